@@ -1,0 +1,173 @@
+/*
+ * qng.h - C ABI of libqng, a GB300 (sm_103a) library for the quantum natural gradient of a
+ * P-parameter unitary ansatz, after T. Jones, "Efficient classical calculation of the Quantum
+ * Natural Gradient" (arXiv:2011.02991).
+ *
+ * What the library computes, for a circuit U(theta) = W U_P(theta_P) ... U_1(theta_1) acting on
+ * |in> = |0...0> and a Hamiltonian H = sum_k c_k sigma_k of Pauli strings:
+ *   - the Fubini-Study metric g = Re G, G_ij = <d_i psi|d_j psi> - <d_i psi|psi><psi|d_j psi>
+ *     (Eq. 4), evaluated through the paper's recurrences: T_i = <psi_i|dU_i|psi_{i-1}>
+ *     (Eq. t_recurrent_def), L_ij = prod[dU_i psi_{i-1}, phi_{i+1,j}] (Eq. L_recurrent_def),
+ *     L_ii = 1/4 a priori (Eq. L_diag_when_single_pauli) and G_ij = L_ij - T_i^* T_j
+ *     (Eq. g_t_L_def), organised as Algorithm 1 (Sec. 3);
+ *   - the energy <E> = <psi|H|psi> and its gradient d<E>/d theta_i (Eq. 2);
+ *   - the natural-gradient step dtheta solving (g + lambda I) dtheta = -dt grad<E> (Eq. 3 with a
+ *     Tikhonov term lambda added to every diagonal entry).
+ *
+ * Conventions
+ *   - Parametric gates are R_sigma(theta) = exp(-i theta sigma / 2), sigma in {X, Y, Z}; the k-th
+ *     parametric gate of a circuit must carry param == k (one unique parameter per gate, Sec. 2).
+ *   - Fixed gates between parametric gates k-1 and k belong to U_k = R_k F_k; fixed gates after
+ *     the last parametric gate form W (part of psi, so of <E>, but cancelling in G).
+ *   - Qubit q is bit q of an amplitude index (q = 0 is the least significant bit).
+ *   - All theta and result arrays are float64. Unless a name ends in _host, pointers are DEVICE
+ *     pointers, read and written asynchronously on the context's CUDA stream: results are valid
+ *     once that stream has reached the end of the call (qng_sync waits for it).
+ *   - Batched contexts concatenate instance b's parameters at param_offset[b] (theta, grad,
+ *     dtheta) and its P_b x P_b row-major metric at metric_offset[b]; energies are one per instance.
+ *   - Memory: the caller owns every device buffer. The library never calls cudaMalloc: it works in
+ *     a caller-provided workspace of qng_workspace_size() bytes (qng_set_workspace). The context
+ *     itself holds only host copies of the descriptions passed to qng_create*.
+ *   - Errors: every call returns a qng_status. Argument errors are found on the host and returned
+ *     before anything is launched. Errors found on the device (a non-positive pivot in the solve)
+ *     are recorded in a status word in the workspace and returned by the next qng_sync.
+ *   - Thread safety: a context may be used by one host thread at a time; calls on one context
+ *     are ordered by its stream. Distinct contexts are independent.
+ */
+#ifndef QNG_H
+#define QNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qng_ctx qng_ctx;
+
+typedef enum {
+    QNG_OK = 0,
+    QNG_ERR_ARG = 1,         /* invalid argument (qubit range, parameter numbering, sizes, NaN theta ...) */
+    QNG_ERR_OOM = 2,         /* host allocation failed */
+    QNG_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    QNG_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    QNG_ERR_NOT_SPD = 5,     /* g + lambda I had a non-positive pivot in the Cholesky factorisation */
+    QNG_ERR_WORKSPACE = 6,   /* no workspace set, or the one set is too small or misaligned */
+    QNG_ERR_UNSUPPORTED = 7  /* a valid request this build does not handle (e.g. too many qubits) */
+} qng_status;
+
+/* gate kinds (qng_gate.kind) */
+enum {
+    QNG_GATE_RX = 0,   /* exp(-i theta X / 2) on q0                     */
+    QNG_GATE_RY = 1,   /* exp(-i theta Y / 2) on q0                     */
+    QNG_GATE_RZ = 2,   /* exp(-i theta Z / 2) on q0                     */
+    QNG_GATE_CZ = 3,   /* controlled-Z on (q0, q1)                      */
+    QNG_GATE_CNOT = 4, /* controlled-X, control q0, target q1           */
+    QNG_GATE_X = 5,    /* Pauli X on q0                                 */
+    QNG_GATE_Y = 6,    /* Pauli Y on q0                                 */
+    QNG_GATE_Z = 7,    /* Pauli Z on q0                                 */
+    QNG_GATE_H = 8     /* Hadamard on q0                                */
+};
+
+/* amplitude precisions */
+enum {
+    QNG_C64 = 0,  /* complex64 amplitudes; float64 accumulation of inner products, assembly and solve */
+    QNG_C128 = 1  /* complex128 amplitudes, float64 arithmetic throughout                            */
+};
+
+/* One gate: param is the index of its angle in theta for RX/RY/RZ and -1 for fixed gates;
+ * q1 is -1 for one-qubit gates. */
+typedef struct {
+    int32_t kind;
+    int32_t q0;
+    int32_t q1;
+    int32_t param;
+} qng_gate;
+
+/* One Pauli string c * sigma: bit q of xmask / zmask set means an X / Z factor on qubit q, both
+ * set means Y (sigma |k> = i^{#Y} (-1)^{popcount(k & zmask)} |k ^ xmask>), neither means identity. */
+typedef struct {
+    double coeff;
+    uint64_t xmask;
+    uint64_t zmask;
+} qng_pauli;
+
+/* Create a single-instance context. gates[0..n_gates-1] and terms[0..n_terms-1] are host arrays,
+ * copied. n_qubits in 1..30; precision QNG_C64 or QNG_C128. On success *out owns the copies. */
+qng_status qng_create(int n_qubits, const qng_gate *gates, int n_gates, const qng_pauli *terms, int n_terms,
+                      int precision, qng_ctx **out);
+
+/* Create a context of `count` independent instances (the batched form). Instance b has n_qubits[b]
+ * qubits, the n_gates[b] gates that follow those of instances 0..b-1 in `gates`, and likewise
+ * n_terms[b] terms of `terms`. Each instance is validated as in qng_create. Batched contexts take
+ * instances of at most 16 qubits. */
+qng_status qng_create_batch(int count, const int32_t *n_qubits, const qng_gate *gates, const int32_t *n_gates,
+                            const qng_pauli *terms, const int32_t *n_terms, int precision, qng_ctx **out);
+
+/* Sizes of a context: number of instances, sum of P_b, sum of P_b^2. Any pointer may be NULL. */
+qng_status qng_get_sizes(const qng_ctx *ctx, int32_t *count, int64_t *total_params, int64_t *total_metric);
+
+/* Host arrays of count+1 offsets: param_offset[b] = sum_{c<b} P_c, metric_offset[b] = sum_{c<b} P_c^2.
+ * Either pointer may be NULL. */
+qng_status qng_get_offsets(const qng_ctx *ctx, int64_t *param_offset, int64_t *metric_offset);
+
+/* Bytes of device workspace the context needs (a multiple of 256). */
+qng_status qng_workspace_size(const qng_ctx *ctx, size_t *bytes);
+
+/* Hand the context a device workspace (256-byte aligned, >= qng_workspace_size bytes, owned by
+ * the caller and kept alive while the context uses it) and the CUDA stream (cudaStream_t, may be
+ * NULL for the legacy default stream) every later call is ordered on. Uploads the circuit tables
+ * into the workspace with asynchronous copies on that stream. */
+qng_status qng_set_workspace(qng_ctx *ctx, void *workspace, size_t bytes, void *stream);
+
+/* Change the stream later calls are ordered on (the workspace stays). */
+qng_status qng_set_stream(qng_ctx *ctx, void *stream);
+
+/* Metric only (Algorithm 1 and Eq. g_t_L_def): g (device, sum P_b^2 float64, row-major per
+ * instance) = Re G. sigma_opt (device, sum P_b, may be NULL) receives <psi_k|sigma_k|psi_k>, the
+ * Pauli expectation right after rotation k, so T_k = -(i/2) sigma_opt[k]. */
+qng_status qng_metric(qng_ctx *ctx, const double *theta, double *g, double *sigma_opt);
+
+/* Energy <E> (device, one float64 per instance) and gradient d<E>/d theta (device, sum P_b). */
+qng_status qng_gradient(qng_ctx *ctx, const double *theta, double *grad, double *energy);
+
+/* Energy only. */
+qng_status qng_energy(qng_ctx *ctx, const double *theta, double *energy);
+
+/* Reverse-mode backward of <E>(theta): grad_theta = grad_out * d<E>/d theta, with grad_out a
+ * DEVICE pointer to one float64 per instance (the upstream gradient). Adjoint (reverse) sweep. */
+qng_status qng_energy_backward(qng_ctx *ctx, const double *theta, const double *grad_out, double *grad_theta);
+
+/* One natural-gradient step: dtheta (device, sum P_b) solves (g + lambda I) dtheta = -dt grad<E>
+ * (Eq. 3) by a float64 Cholesky factorisation. g_opt, grad_opt, energy_opt (device, may be NULL)
+ * also receive the metric, the gradient and the energy. lambda >= 0; a non-positive pivot sets
+ * QNG_ERR_NOT_SPD, reported by qng_sync. */
+qng_status qng_step(qng_ctx *ctx, const double *theta, double dt, double lambda, double *dtheta, double *g_opt,
+                    double *grad_opt, double *energy_opt);
+
+/* qng_step with HOST buffers: copies theta_host in, runs the step, copies the results out and
+ * waits for the stream. Pageable or pinned host memory; g_host, grad_host, energy_host may be NULL. */
+qng_status qng_step_host(qng_ctx *ctx, const double *theta_host, double dt, double lambda, double *dtheta_host,
+                         double *g_host, double *grad_host, double *energy_host);
+
+/* Wait for the context's stream, then return (and clear) the device-side status word. */
+qng_status qng_sync(qng_ctx *ctx);
+
+/* Launch-shape controls (used by the autotuner; 0 leaves a value on automatic):
+ * cluster_log2 = log2 of CTAs per state (0..4), threads = CTA size (64..1024, a multiple of 32).
+ * For batched contexts the settings apply to the instances with n_qubits >= min_qubits. */
+qng_status qng_set_tuning(qng_ctx *ctx, int min_qubits, int cluster_log2, int threads);
+
+/* Number of kernel launches the last compute call issued (for accounting). */
+qng_status qng_last_launch_count(const qng_ctx *ctx, int64_t *launches);
+
+void qng_destroy(qng_ctx *ctx);
+
+const char *qng_status_string(qng_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QNG_H */

@@ -1,0 +1,566 @@
+// Host side of the C ABI declared in include/qng.h: argument validation, the device tables,
+// the workspace layout, launch grouping and the entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qng_internal.h"
+
+using namespace qng;
+
+namespace {
+
+struct HostInst {
+    int n = 0, P = 0;
+    std::vector<qng_gate> gates;
+    std::vector<qng_pauli> terms;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool is_rot(int k) { return k == QNG_GATE_RX || k == QNG_GATE_RY || k == QNG_GATE_RZ; }
+bool is_fixed(int k) { return k >= QNG_GATE_CZ && k <= QNG_GATE_H; }
+bool is_two_qubit(int k) { return k == QNG_GATE_CZ || k == QNG_GATE_CNOT; }
+
+qng_status validate(int n, const qng_gate *gates, int n_gates, const qng_pauli *terms, int n_terms, HostInst &out) {
+    if (n < 1 || n > kMaxQubits || n_gates < 0 || n_terms < 0) return QNG_ERR_ARG;
+    if ((n_gates > 0 && !gates) || (n_terms > 0 && !terms)) return QNG_ERR_ARG;
+    out.n = n;
+    out.P = 0;
+    for (int g = 0; g < n_gates; ++g) {
+        const qng_gate &x = gates[g];
+        if (x.q0 < 0 || x.q0 >= n) return QNG_ERR_ARG;
+        if (is_rot(x.kind)) {
+            if (x.param != out.P) return QNG_ERR_ARG;  // one unique parameter per gate, in circuit order
+            out.P++;
+        } else if (is_fixed(x.kind)) {
+            if (x.param != -1) return QNG_ERR_ARG;
+            if (is_two_qubit(x.kind) && (x.q1 < 0 || x.q1 >= n || x.q1 == x.q0)) return QNG_ERR_ARG;
+        } else {
+            return QNG_ERR_ARG;
+        }
+    }
+    const uint64_t full = (n == 64) ? ~0ull : ((1ull << n) - 1);
+    for (int t = 0; t < n_terms; ++t) {
+        if (!std::isfinite(terms[t].coeff)) return QNG_ERR_ARG;
+        if ((terms[t].xmask & ~full) || (terms[t].zmask & ~full)) return QNG_ERR_ARG;
+    }
+    out.gates.assign(gates, gates + n_gates);
+    out.terms.assign(terms, terms + n_terms);
+    return QNG_OK;
+}
+
+}  // namespace
+
+struct qng_ctx {
+    int precision = QNG_C128;
+    int count = 0;
+    std::vector<HostInst> inst;
+    // device-table images (host copies, uploaded by qng_set_workspace)
+    std::vector<DevInst> t_inst;
+    std::vector<DevParam> t_param;
+    std::vector<DevFixed> t_fixed;
+    std::vector<DevDiag> t_diag;
+    std::vector<DevTerm> t_term;
+    std::vector<DevWork> t_work;
+    std::vector<int32_t> t_group_inst;
+    std::vector<Group> groups;
+    int64_t total_params = 0, total_metric = 0;
+    int max_P = 0;
+    std::vector<int64_t> param_off, metric_off;
+    // workspace layout (byte offsets)
+    size_t o_status = 0, o_inst = 0, o_param = 0, o_fixed = 0, o_diag = 0, o_term = 0, o_work = 0, o_ginst = 0;
+    size_t o_coef = 0, o_sigma = 0, o_scale = 0, o_L = 0, o_grad = 0, o_energy = 0, o_chol = 0, o_ckpt = 0, o_eta = 0;
+    size_t o_io_theta = 0, o_io_dtheta = 0, o_io_g = 0, o_io_grad = 0, o_io_energy = 0;
+    size_t ws_bytes = 0;
+    unsigned char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    bool prepared = false;
+    // tuning
+    int tune_min_qubits = 0, tune_cl = -1, tune_threads = 0;
+    int64_t last_launches = 0;
+
+    Work work() const {
+        Work w;
+        w.status = reinterpret_cast<int32_t *>(ws + o_status);
+        w.inst = reinterpret_cast<const DevInst *>(ws + o_inst);
+        w.param = reinterpret_cast<const DevParam *>(ws + o_param);
+        w.fixed = reinterpret_cast<const DevFixed *>(ws + o_fixed);
+        w.diag = reinterpret_cast<const DevDiag *>(ws + o_diag);
+        w.term = reinterpret_cast<const DevTerm *>(ws + o_term);
+        w.work = reinterpret_cast<const DevWork *>(ws + o_work);
+        w.group_inst = reinterpret_cast<const int32_t *>(ws + o_ginst);
+        w.coef = reinterpret_cast<DevCoef *>(ws + o_coef);
+        w.sigma = reinterpret_cast<double *>(ws + o_sigma);
+        w.scale = reinterpret_cast<double *>(ws + o_scale);
+        w.L = reinterpret_cast<double *>(ws + o_L);
+        w.gradraw = reinterpret_cast<double *>(ws + o_grad);
+        w.energy = reinterpret_cast<double *>(ws + o_energy);
+        w.chol = reinterpret_cast<double *>(ws + o_chol);
+        w.ckpt = ws + o_ckpt;
+        w.eta = ws + o_eta;
+        return w;
+    }
+};
+
+namespace {
+
+size_t amp_bytes(int precision) { return precision == QNG_C128 ? 16 : 8; }
+
+int default_cl(int n, int precision) {
+    const int base = precision == QNG_C128 ? 9 : 11;
+    return std::max(0, std::min(kMaxClusterLog2, n - base));
+}
+
+int default_threads(int nl) {
+    const uint32_t Nl = 1u << nl;
+    if (Nl <= 256) return 64;
+    if (Nl <= 1024) return 128;
+    return 256;
+}
+
+// Build the device-table images, the launch groups and the workspace layout.
+qng_status plan(qng_ctx *c) {
+    c->t_inst.clear(); c->t_param.clear(); c->t_fixed.clear(); c->t_diag.clear(); c->t_term.clear();
+    c->t_work.clear(); c->t_group_inst.clear(); c->groups.clear();
+    c->param_off.assign(c->count + 1, 0);
+    c->metric_off.assign(c->count + 1, 0);
+    const size_t ab = amp_bytes(c->precision);
+    int64_t ckpt_amps = 0, eta_amps = 0, scale_n = 0;
+    c->max_P = 0;
+    for (int b = 0; b < c->count; ++b) {
+        const HostInst &h = c->inst[b];
+        DevInst d = {};
+        d.n = h.n;
+        d.P = h.P;
+        d.nterms = (int32_t)h.terms.size();
+        d.param_off = c->param_off[b];
+        d.metric_off = c->metric_off[b];
+        c->param_off[b + 1] = c->param_off[b] + h.P;
+        c->metric_off[b + 1] = c->metric_off[b] + (int64_t)h.P * h.P;
+        d.ckpt_off = ckpt_amps;
+        ckpt_amps += (int64_t)(h.P + 1) << h.n;
+        d.eta_off = eta_amps;
+        eta_amps += 1ll << h.n;
+        d.scale_off = scale_n;
+        scale_n += h.P + 2;
+        d.param_tab = (int32_t)c->t_param.size();
+        d.term_off = (int32_t)c->t_term.size();
+        c->max_P = std::max(c->max_P, h.P);
+        // parameters with their preceding fixed gates
+        std::vector<const qng_gate *> pending;
+        auto flush_into = [&](DevParam &p) {
+            p.fix_begin = (int32_t)c->t_fixed.size();
+            p.fix_count = (int32_t)pending.size();
+            bool all_diag = true;
+            for (const qng_gate *g : pending) {
+                c->t_fixed.push_back(DevFixed{g->kind, g->q0, g->q1, 0});
+                if (g->kind != QNG_GATE_CZ && g->kind != QNG_GATE_Z) all_diag = false;
+            }
+            p.zmask = 0;
+            if (all_diag) {
+                uint64_t shift_mask[64] = {0};
+                for (const qng_gate *g : pending) {
+                    if (g->kind == QNG_GATE_Z) {
+                        p.zmask ^= 1ull << g->q0;
+                    } else {
+                        const int u = std::min(g->q0, g->q1), v = std::max(g->q0, g->q1);
+                        shift_mask[v - u] ^= 1ull << u;
+                    }
+                }
+                p.diag_begin = (int32_t)c->t_diag.size();
+                for (int s = 1; s < 64; ++s)
+                    if (shift_mask[s]) c->t_diag.push_back(DevDiag{s, 0, shift_mask[s]});
+                p.diag_count = (int32_t)c->t_diag.size() - p.diag_begin;
+            } else {
+                p.diag_begin = 0;
+                p.diag_count = -1;
+            }
+            pending.clear();
+        };
+        for (const qng_gate &g : h.gates) {
+            if (is_rot(g.kind)) {
+                DevParam p = {};
+                p.axis = g.kind == QNG_GATE_RX ? kAxisX : (g.kind == QNG_GATE_RY ? kAxisY : kAxisZ);
+                p.q = g.q0;
+                flush_into(p);
+                c->t_param.push_back(p);
+            } else {
+                pending.push_back(&g);
+            }
+        }
+        d.w_begin = (int32_t)c->t_fixed.size();
+        d.w_count = (int32_t)pending.size();
+        for (const qng_gate *g : pending) c->t_fixed.push_back(DevFixed{g->kind, g->q0, g->q1, 0});
+        for (const qng_pauli &t : h.terms) {
+            DevTerm dt = {};
+            dt.coeff = t.coeff;
+            dt.x = t.xmask;
+            dt.z = t.zmask;
+            dt.ny = __builtin_popcountll(t.xmask & t.zmask) & 3;
+            c->t_term.push_back(dt);
+        }
+        c->t_inst.push_back(d);
+    }
+    c->total_params = c->param_off[c->count];
+    c->total_metric = c->metric_off[c->count];
+
+    // groups: instances sharing (cluster size, CTA size)
+    std::vector<std::pair<int, int>> shape(c->count);
+    for (int b = 0; b < c->count; ++b) {
+        const int n = c->inst[b].n;
+        int cl = default_cl(n, c->precision);
+        if (c->tune_cl >= 0 && n >= c->tune_min_qubits) cl = c->tune_cl;
+        cl = std::max(0, std::min(cl, std::min(kMaxClusterLog2, n - 1)));
+        int th = default_threads(n - cl);
+        if (c->tune_threads > 0 && n >= c->tune_min_qubits) th = c->tune_threads;
+        shape[b] = {cl, th};
+        c->t_inst[b].cl = cl;
+    }
+    std::vector<std::pair<int, int>> keys(shape);
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    for (const auto &key : keys) {
+        Group g;
+        g.cl = key.first;
+        g.threads = key.second;
+        g.first_inst = (int)c->t_group_inst.size();
+        std::vector<DevWork> items;
+        for (int b = 0; b < c->count; ++b) {
+            if (shape[b] != key) continue;
+            c->t_group_inst.push_back(b);
+            g.max_n = std::max(g.max_n, c->inst[b].n);
+            g.max_P = std::max(g.max_P, c->inst[b].P);
+            if (c->inst[b].P > 0)
+                for (int j = 0; j <= c->inst[b].P; ++j) items.push_back(DevWork{b, j});
+        }
+        g.num_inst = (int)c->t_group_inst.size() - g.first_inst;
+        // longest first: steps x amplitudes (column j has j steps, the gradient column P)
+        auto cost = [&](const DevWork &w) { return (double)std::max(w.col, 1) * (double)(1ll << c->inst[w.inst].n); };
+        std::stable_sort(items.begin(), items.end(), [&](const DevWork &a, const DevWork &b) { return cost(a) > cost(b); });
+        g.first_work = (int)c->t_work.size();
+        c->t_work.insert(c->t_work.end(), items.begin(), items.end());
+        g.num_work = (int)items.size();
+        g.first_grad = (int)c->t_work.size();
+        for (const DevWork &w : items) if (w.col == c->inst[w.inst].P) c->t_work.push_back(w);
+        g.num_grad = (int)c->t_work.size() - g.first_grad;
+        g.first_met = (int)c->t_work.size();
+        for (const DevWork &w : items) if (w.col < c->inst[w.inst].P) c->t_work.push_back(w);
+        g.num_met = (int)c->t_work.size() - g.first_met;
+        const size_t Nl = size_t(1) << (g.max_n - g.cl);
+        const int nw = g.threads / 32;
+        const size_t state = Nl * ab * (g.cl ? 3 : 1);
+        g.smem_fwd = state + 64 * sizeof(double);
+        g.smem_col = state + (size_t)(g.max_P + 1) * nw * sizeof(double) + (size_t)(g.max_P + 1) * sizeof(double);
+        if (g.smem_col > 227 * 1024 || g.smem_fwd > 227 * 1024) return QNG_ERR_UNSUPPORTED;
+        c->groups.push_back(g);
+    }
+
+    // workspace layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = align256(off); off = o + std::max<size_t>(bytes, 1); return o; };
+    c->o_status = take(256);
+    c->o_inst = take(sizeof(DevInst) * c->t_inst.size());
+    c->o_param = take(sizeof(DevParam) * c->t_param.size());
+    c->o_fixed = take(sizeof(DevFixed) * c->t_fixed.size());
+    c->o_diag = take(sizeof(DevDiag) * c->t_diag.size());
+    c->o_term = take(sizeof(DevTerm) * c->t_term.size());
+    c->o_work = take(sizeof(DevWork) * c->t_work.size());
+    c->o_ginst = take(sizeof(int32_t) * c->t_group_inst.size());
+    c->o_coef = take(sizeof(DevCoef) * c->total_params);
+    c->o_sigma = take(sizeof(double) * c->total_params);
+    c->o_scale = take(sizeof(double) * scale_n);
+    c->o_L = take(sizeof(double) * c->total_metric);
+    c->o_grad = take(sizeof(double) * c->total_params);
+    c->o_energy = take(sizeof(double) * c->count);
+    c->o_chol = take(sizeof(double) * c->total_metric);
+    c->o_io_theta = take(sizeof(double) * c->total_params);
+    c->o_io_dtheta = take(sizeof(double) * c->total_params);
+    c->o_io_g = take(sizeof(double) * c->total_metric);
+    c->o_io_grad = take(sizeof(double) * c->total_params);
+    c->o_io_energy = take(sizeof(double) * c->count);
+    c->o_ckpt = take(ab * (size_t)ckpt_amps);
+    c->o_eta = take(ab * (size_t)eta_amps);
+    c->ws_bytes = align256(off);
+    c->prepared = false;
+    return QNG_OK;
+}
+
+qng_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return QNG_OK;
+    std::fprintf(stderr, "libqng: CUDA error %s\n", cudaGetErrorString(e));
+    return QNG_ERR_CUDA;
+}
+
+qng_status upload(qng_ctx *c) {
+    auto put = [&](size_t o, const void *src, size_t bytes) -> cudaError_t {
+        if (bytes == 0) return cudaSuccess;
+        return cudaMemcpyAsync(c->ws + o, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    };
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->ws + c->o_status, 0, 256, c->stream)) != cudaSuccess) return cuda_status(e);
+    if ((e = put(c->o_inst, c->t_inst.data(), sizeof(DevInst) * c->t_inst.size())) != cudaSuccess) return cuda_status(e);
+    if ((e = put(c->o_param, c->t_param.data(), sizeof(DevParam) * c->t_param.size())) != cudaSuccess) return cuda_status(e);
+    if ((e = put(c->o_fixed, c->t_fixed.data(), sizeof(DevFixed) * c->t_fixed.size())) != cudaSuccess) return cuda_status(e);
+    if ((e = put(c->o_diag, c->t_diag.data(), sizeof(DevDiag) * c->t_diag.size())) != cudaSuccess) return cuda_status(e);
+    if ((e = put(c->o_term, c->t_term.data(), sizeof(DevTerm) * c->t_term.size())) != cudaSuccess) return cuda_status(e);
+    if ((e = put(c->o_work, c->t_work.data(), sizeof(DevWork) * c->t_work.size())) != cudaSuccess) return cuda_status(e);
+    if ((e = put(c->o_ginst, c->t_group_inst.data(), sizeof(int32_t) * c->t_group_inst.size())) != cudaSuccess)
+        return cuda_status(e);
+    // host tables must stay valid until the copies ran: pageable-memory copies are staged
+    // synchronously with respect to the host, so returning here is safe
+    size_t sf = 0, sc = 0;
+    for (const Group &g : c->groups) { sf = std::max(sf, g.smem_fwd); sc = std::max(sc, g.smem_col); }
+    if ((e = prepare_kernels(c->precision, sf, sc)) != cudaSuccess) return cuda_status(e);
+    c->prepared = true;
+    return QNG_OK;
+}
+
+qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
+    if (!c) return QNG_ERR_ARG;
+    if (!c->ws || !c->prepared) return QNG_ERR_WORKSPACE;
+    if (!args.theta && c->total_params > 0) return QNG_ERR_ARG;
+    const Work w = c->work();
+    int64_t launches = 0;
+    cudaError_t e = launch_coef(w, args.theta, c->total_params, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    launches += c->total_params > 0;
+    const bool need_cols = jobs & (kJobMetric | kJobGradient | kJobSolve);
+    const bool want_eta = jobs & (kJobGradient | kJobSolve);
+    for (const Group &g : c->groups) {
+        if ((e = launch_forward(w, g, c->precision, want_eta, c->stream)) != cudaSuccess) return cuda_status(e);
+        launches += g.num_inst > 0;
+    }
+    if (need_cols) {
+        const int wm = (jobs & (kJobMetric | kJobSolve)) ? 1 : 0;
+        const int wg = (jobs & (kJobGradient | kJobSolve)) ? 1 : 0;
+        for (const Group &g : c->groups) {
+            if ((e = launch_columns(w, g, c->precision, wm, wg, c->stream)) != cudaSuccess) return cuda_status(e);
+            launches += (wm && wg ? g.num_work : (wm ? g.num_met : g.num_grad)) > 0;
+        }
+    }
+    LaunchArgs a = args;
+    a.jobs = jobs;
+    if ((e = launch_finish(w, c->count, c->max_P, a, c->stream)) != cudaSuccess) return cuda_status(e);
+    launches += 1;
+    c->last_launches = launches;
+    return QNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qng_status qng_create(int n_qubits, const qng_gate *gates, int n_gates, const qng_pauli *terms, int n_terms,
+                      int precision, qng_ctx **out) {
+    const int32_t nq = n_qubits, ng = n_gates, nt = n_terms;
+    return qng_create_batch(1, &nq, gates, &ng, terms, &nt, precision, out);
+}
+
+qng_status qng_create_batch(int count, const int32_t *n_qubits, const qng_gate *gates, const int32_t *n_gates,
+                            const qng_pauli *terms, const int32_t *n_terms, int precision, qng_ctx **out) {
+    if (!out) return QNG_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || !n_qubits || !n_gates || !n_terms) return QNG_ERR_ARG;
+    if (precision != QNG_C64 && precision != QNG_C128) return QNG_ERR_ARG;
+    qng_ctx *c = new (std::nothrow) qng_ctx;
+    if (!c) return QNG_ERR_OOM;
+    c->precision = precision;
+    c->count = count;
+    try {
+        c->inst.resize(count);
+    } catch (...) {
+        delete c;
+        return QNG_ERR_OOM;
+    }
+    int64_t go = 0, to = 0;
+    for (int b = 0; b < count; ++b) {
+        qng_status s = validate(n_qubits[b], gates ? gates + go : nullptr, n_gates[b], terms ? terms + to : nullptr,
+                                n_terms[b], c->inst[b]);
+        if (s != QNG_OK) { delete c; return s; }
+        go += n_gates[b];
+        to += n_terms[b];
+        if (c->inst[b].n > kMaxQubitsSmall) { delete c; return QNG_ERR_UNSUPPORTED; }
+    }
+    qng_status s = plan(c);
+    if (s != QNG_OK) { delete c; return s; }
+    *out = c;
+    return QNG_OK;
+}
+
+qng_status qng_get_sizes(const qng_ctx *c, int32_t *count, int64_t *total_params, int64_t *total_metric) {
+    if (!c) return QNG_ERR_ARG;
+    if (count) *count = c->count;
+    if (total_params) *total_params = c->total_params;
+    if (total_metric) *total_metric = c->total_metric;
+    return QNG_OK;
+}
+
+qng_status qng_get_offsets(const qng_ctx *c, int64_t *param_offset, int64_t *metric_offset) {
+    if (!c) return QNG_ERR_ARG;
+    if (param_offset) std::copy(c->param_off.begin(), c->param_off.end(), param_offset);
+    if (metric_offset) std::copy(c->metric_off.begin(), c->metric_off.end(), metric_offset);
+    return QNG_OK;
+}
+
+qng_status qng_workspace_size(const qng_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return QNG_ERR_ARG;
+    *bytes = c->ws_bytes;
+    return QNG_OK;
+}
+
+qng_status qng_set_workspace(qng_ctx *c, void *workspace, size_t bytes, void *stream) {
+    if (!c) return QNG_ERR_ARG;
+    if (!workspace || bytes < c->ws_bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return QNG_ERR_WORKSPACE;
+    c->ws = static_cast<unsigned char *>(workspace);
+    c->stream = static_cast<cudaStream_t>(stream);
+    return upload(c);
+}
+
+qng_status qng_set_stream(qng_ctx *c, void *stream) {
+    if (!c) return QNG_ERR_ARG;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return QNG_OK;
+}
+
+qng_status qng_set_tuning(qng_ctx *c, int min_qubits, int cluster_log2, int threads) {
+    if (!c) return QNG_ERR_ARG;
+    if (cluster_log2 < -1 || cluster_log2 > kMaxClusterLog2) return QNG_ERR_ARG;
+    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32)) return QNG_ERR_ARG;
+    const int old_min = c->tune_min_qubits, old_cl = c->tune_cl, old_th = c->tune_threads;
+    c->tune_min_qubits = min_qubits;
+    c->tune_cl = cluster_log2 == 0 && threads == 0 && min_qubits == 0 ? -1 : cluster_log2;
+    c->tune_threads = threads;
+    const size_t old_bytes = c->ws_bytes;
+    qng_status s = plan(c);
+    if (s != QNG_OK || c->ws_bytes > old_bytes) {
+        c->tune_min_qubits = old_min; c->tune_cl = old_cl; c->tune_threads = old_th;
+        plan(c);
+        if (c->ws) upload(c);
+        return s != QNG_OK ? s : QNG_ERR_WORKSPACE;
+    }
+    if (c->ws) return upload(c);
+    return QNG_OK;
+}
+
+qng_status qng_metric(qng_ctx *c, const double *theta, double *g, double *sigma_opt) {
+    if (!c || !g) return QNG_ERR_ARG;
+    LaunchArgs a = {};
+    a.theta = theta;
+    a.g_out = g;
+    a.sigma_out = sigma_opt;
+    return run(c, kJobMetric, a);
+}
+
+qng_status qng_gradient(qng_ctx *c, const double *theta, double *grad, double *energy) {
+    if (!c || !grad) return QNG_ERR_ARG;
+    LaunchArgs a = {};
+    a.theta = theta;
+    a.grad_out = grad;
+    a.energy_out = energy;
+    return run(c, kJobGradient | kJobEnergy, a);
+}
+
+qng_status qng_energy(qng_ctx *c, const double *theta, double *energy) {
+    if (!c || !energy) return QNG_ERR_ARG;
+    LaunchArgs a = {};
+    a.theta = theta;
+    a.energy_out = energy;
+    return run(c, kJobEnergy, a);
+}
+
+qng_status qng_energy_backward(qng_ctx *c, const double *theta, const double *grad_out, double *grad_theta) {
+    if (!c || !grad_out || !grad_theta) return QNG_ERR_ARG;
+    LaunchArgs a = {};
+    a.theta = theta;
+    a.grad_out = grad_theta;
+    a.grad_scale = grad_out;
+    return run(c, kJobGradient, a);
+}
+
+qng_status qng_step(qng_ctx *c, const double *theta, double dt, double lambda, double *dtheta, double *g_opt,
+                    double *grad_opt, double *energy_opt) {
+    if (!c || !dtheta) return QNG_ERR_ARG;
+    if (!std::isfinite(dt) || !std::isfinite(lambda) || lambda < 0) return QNG_ERR_ARG;
+    LaunchArgs a = {};
+    a.theta = theta;
+    a.dtheta_out = dtheta;
+    a.g_out = g_opt;
+    a.grad_out = grad_opt;
+    a.energy_out = energy_opt;
+    a.dt = dt;
+    a.lambda = lambda;
+    return run(c, kJobSolve | kJobGradient | kJobEnergy | kJobMetric, a);
+}
+
+qng_status qng_step_host(qng_ctx *c, const double *theta_host, double dt, double lambda, double *dtheta_host,
+                         double *g_host, double *grad_host, double *energy_host) {
+    if (!c || !dtheta_host || (!theta_host && c->total_params > 0)) return QNG_ERR_ARG;
+    if (!c->ws || !c->prepared) return QNG_ERR_WORKSPACE;
+    double *th = reinterpret_cast<double *>(c->ws + c->o_io_theta);
+    double *dth = reinterpret_cast<double *>(c->ws + c->o_io_dtheta);
+    double *g = reinterpret_cast<double *>(c->ws + c->o_io_g);
+    double *gr = reinterpret_cast<double *>(c->ws + c->o_io_grad);
+    double *en = reinterpret_cast<double *>(c->ws + c->o_io_energy);
+    const size_t pb = sizeof(double) * c->total_params, mb = sizeof(double) * c->total_metric;
+    cudaError_t e;
+    if (pb && (e = cudaMemcpyAsync(th, theta_host, pb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_status(e);
+    qng_status s = qng_step(c, th, dt, lambda, dth, g_host ? g : nullptr, grad_host ? gr : nullptr,
+                            energy_host ? en : nullptr);
+    if (s != QNG_OK) return s;
+    if (pb && (e = cudaMemcpyAsync(dtheta_host, dth, pb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return cuda_status(e);
+    if (g_host && mb && (e = cudaMemcpyAsync(g_host, g, mb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return cuda_status(e);
+    if (grad_host && pb && (e = cudaMemcpyAsync(grad_host, gr, pb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return cuda_status(e);
+    if (energy_host &&
+        (e = cudaMemcpyAsync(energy_host, en, sizeof(double) * c->count, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return cuda_status(e);
+    return qng_sync(c);
+}
+
+qng_status qng_sync(qng_ctx *c) {
+    if (!c) return QNG_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!c->ws) return QNG_OK;
+    int32_t st = 0;
+    if ((e = cudaMemcpyAsync(&st, c->ws + c->o_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_status(e);
+    if (st != 0) {
+        if ((e = cudaMemsetAsync(c->ws + c->o_status, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_status(e);
+        return static_cast<qng_status>(st);
+    }
+    return QNG_OK;
+}
+
+qng_status qng_last_launch_count(const qng_ctx *c, int64_t *launches) {
+    if (!c || !launches) return QNG_ERR_ARG;
+    *launches = c->last_launches;
+    return QNG_OK;
+}
+
+void qng_destroy(qng_ctx *c) { delete c; }
+
+const char *qng_status_string(qng_status s) {
+    switch (s) {
+    case QNG_OK: return "ok";
+    case QNG_ERR_ARG: return "invalid argument";
+    case QNG_ERR_OOM: return "host allocation failed";
+    case QNG_ERR_CUDA: return "CUDA error";
+    case QNG_ERR_TIMEOUT: return "device wait timed out";
+    case QNG_ERR_NOT_SPD: return "g + lambda I is not positive definite";
+    case QNG_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case QNG_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

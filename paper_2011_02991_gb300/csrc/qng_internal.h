@@ -1,0 +1,149 @@
+// Internal declarations shared by the host API (qng_api.cu) and the kernels (qng_kernels.cu).
+// Device-visible tables live in the caller's workspace; every offset below is in elements.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/qng.h"
+
+namespace qng {
+
+constexpr int kMaxQubits = 30;         // any single instance
+constexpr int kMaxQubitsSmall = 16;    // instances run by the on-chip (cluster-resident) path
+constexpr int kMaxClusterLog2 = 4;     // 16 CTAs per cluster (non-portable size, opt-in)
+constexpr int kAxisX = 0, kAxisY = 1, kAxisZ = 2;
+
+// One parametric gate k of an instance: U_k = R_k F_k with R_k = exp(-i theta_k sigma / 2).
+struct DevParam {
+    int32_t axis;       // kAxisX / kAxisY / kAxisZ
+    int32_t q;          // target qubit
+    int32_t fix_begin;  // F_k: fixed gates [fix_begin, fix_begin + fix_count) of the fixed table, circuit order
+    int32_t fix_count;
+    int32_t diag_begin; // if F_k is all CZ / Z: its sign as (shift, mask) pairs [diag_begin, +diag_count)
+    int32_t diag_count; //   of the diag table, plus zmask; diag_count = -1 when F_k is not all diagonal
+    uint64_t zmask;     //   single-qubit Z factors of F_k
+};
+
+struct DevFixed {
+    int32_t kind;  // QNG_GATE_CZ, CNOT, X, Y, Z, H
+    int32_t q0;
+    int32_t q1;
+    int32_t pad;
+};
+
+// sign(k) of a set of CZ gates = (-1)^(sum over pairs of popcount(k & (k >> shift) & mask))
+struct DevDiag {
+    int32_t shift;
+    int32_t pad;
+    uint64_t mask;
+};
+
+struct DevTerm {
+    double coeff;
+    uint64_t x;
+    uint64_t z;
+    int32_t ny;   // number of Y factors mod 4
+    int32_t pad;
+};
+
+// Per-instance descriptor.
+struct DevInst {
+    int32_t n, P;
+    int32_t cl;             // log2 of CTAs per cluster used for this instance's chains
+    int32_t nterms;
+    int64_t param_off;      // theta, coef, sigma, grad, dtheta (P entries)
+    int64_t metric_off;     // g, L, cholesky scratch (P*P entries)
+    int64_t ckpt_off;       // checkpoints Psi[0..P] (amplitude units; (P+1) * 2^n)
+    int64_t eta_off;        // adjoint seed eta (2^n amplitudes)
+    int64_t scale_off;      // P + 2 scale factors: Psi[0..P], eta
+    int32_t param_tab;      // first DevParam of the instance
+    int32_t w_begin;        // trailing fixed gates W in the fixed table
+    int32_t w_count;
+    int32_t term_off;       // first DevTerm
+};
+
+struct DevWork {
+    int32_t inst;
+    int32_t col;  // 0..P-1: metric column; P: gradient (adjoint) column
+};
+
+// Coefficients of parameter k (float64): c = cos(theta/2), s = sin(theta/2), and the scaled
+// form of the adjoint rotation R^dag = c I + i s sigma = f (I + i t sigma) (|c| >= |s|) or
+// f (t I + i sigma) (|c| < |s|).
+struct DevCoef {
+    double c, s, t, f;
+    int32_t caseB;
+    int32_t pad;
+};
+
+// Pointers into the workspace.
+struct Work {
+    int32_t *status;          // device status word
+    const DevInst *inst;
+    const DevParam *param;
+    const DevFixed *fixed;
+    const DevDiag *diag;
+    const DevTerm *term;
+    const DevWork *work;      // work items, all groups, each group contiguous
+    const int32_t *group_inst;// instances of each group, contiguous per group
+    DevCoef *coef;
+    double *sigma;            // <psi_k|sigma_k|psi_k>
+    double *scale;            // checkpoint and eta scale factors
+    double *L;                // (1/4) Re L_ij, i < j, per instance P*P
+    double *gradraw;          // d<E>/d theta
+    double *energy;           // <E>
+    double *chol;             // P*P per instance
+    void *ckpt;               // checkpoint amplitudes
+    void *eta;                // adjoint seeds
+};
+
+// A launch group: instances sharing one cluster size and CTA shape.
+struct Group {
+    int cl = 0;
+    int threads = 128;
+    int max_n = 0;
+    int max_P = 0;
+    int first_inst = 0;   // into group_inst
+    int num_inst = 0;
+    int first_work = 0;   // into work: metric + gradient columns, sorted by decreasing length
+    int num_work = 0;
+    int first_grad = 0;   // gradient columns only
+    int num_grad = 0;
+    int first_met = 0;    // metric columns only, sorted by decreasing length
+    int num_met = 0;
+    size_t smem_fwd = 0;
+    size_t smem_col = 0;
+};
+
+enum Job : int {
+    kJobMetric = 1,
+    kJobGradient = 2,
+    kJobEnergy = 4,
+    kJobSolve = 8,
+};
+
+struct LaunchArgs {
+    const double *theta;
+    double *g_out;        // may be null
+    double *sigma_out;    // may be null
+    double *grad_out;     // may be null
+    double *energy_out;   // may be null
+    double *dtheta_out;   // may be null
+    const double *grad_scale;  // device, one per instance (energy backward), may be null
+    double dt, lambda;
+    int jobs;
+};
+
+// Kernel-side launchers (qng_kernels.cu). Return cudaSuccess or the launch error.
+cudaError_t launch_coef(const Work &w, const double *theta, int64_t total_params, cudaStream_t st);
+cudaError_t launch_forward(const Work &w, const Group &g, int precision, int want_eta, cudaStream_t st);
+cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
+                           cudaStream_t st);
+cudaError_t launch_finish(const Work &w, int count, int max_P, const LaunchArgs &a, cudaStream_t st);
+cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col);
+
+}  // namespace qng

@@ -1,0 +1,737 @@
+// sm_103a kernels of the on-chip path: every state vector of an instance lives in the shared
+// memory of one thread-block cluster (2^cl CTAs, each holding 2^(n-cl) amplitudes), so the
+// O(P^2) recurrence of Algorithm 1 runs without touching HBM except to read checkpoints.
+//
+//   k_coef     per-parameter cos/sin of theta/2 and the scaled rotation form
+//   k_forward  psi_k = U_k ... U_1 |0> for every k (checkpoints), W psi, H W psi, <E>, and the
+//              adjoint seed eta = W^dag H W psi (Sec. 2: psi_i and T_i; Eq. 2 for <E>)
+//   k_columns  one cluster per column j of L: phi walks down from dU_j psi_{j-1} by one adjoint
+//              gate per element, L_ij = prod[dU_i psi_{i-1}, phi_{i+1,j}] (Eq. L_recurrent_def,
+//              the inner loop of Algorithm 1); the extra column P walks eta down the same way
+//              and yields d<E>/d theta_i (reverse sweep)
+//   k_finish   G_ij = L_ij - T_i^* T_j (Eq. g_t_L_def), g = Re G, and the float64 Cholesky solve
+//              of (g + lambda I) dtheta = -dt grad<E> (Eq. 3)
+//
+// Notation used throughout (0-based parameters k = 0..P-1):
+//   Psi[k]    the state after U_{k-1} (Psi[0] = |0>), stored as a checkpoint;
+//   R_k^dag = c + i s sigma_k, R_k = c - i s sigma_k, with c = cos(theta_k/2), s = sin(theta_k/2);
+//   dU_k Psi[k] = (-i/2) sigma_k Psi[k+1], hence L_ij = (1/4) <Psi[i+1]| sigma_i |b_ij> with
+//   b_ij = U_{i+1}^dag ... U_j^dag sigma_j Psi[j+1], and T_k = -(i/2) <Psi[k+1]|sigma_k|Psi[k+1]>.
+// Complex128 amplitudes are kept as (scalar factor) x (vector): a rotation becomes one FMA per
+// real component (see DevCoef), halving the float64 work on a part whose float64 rate is 1/64 of
+// its float32 rate; the factors are applied to each inner product.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "qng_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace qng {
+
+template <typename R> struct CX;
+template <> struct CX<double> { using T = double2; };
+template <> struct CX<float> { using T = float2; };
+
+__device__ __forceinline__ uint32_t ins0(uint32_t p, int q) {
+    return ((p >> q) << (q + 1)) | (p & ((1u << q) - 1u));
+}
+
+// (-1)^parity of an all-diagonal fixed block F (CZ and Z gates) at basis index k
+__device__ __forceinline__ int diag_parity(uint64_t k, const DevParam &pd, const DevDiag *dt) {
+    int par = __popcll(k & pd.zmask);
+    for (int e = 0; e < pd.diag_count; ++e) {
+        const DevDiag d = dt[pd.diag_begin + e];
+        par += __popcll(k & (k >> d.shift) & d.mask);
+    }
+    return par & 1;
+}
+
+template <typename T2> __device__ __forceinline__ T2 neg_if(T2 v, int p) {
+    if (p) { v.x = -v.x; v.y = -v.y; }
+    return v;
+}
+
+// (i sigma x)_beta for the pair component with bit value beta, own value xm, partner value xo
+template <typename T2> __device__ __forceinline__ T2 i_sigma(int axis, int beta, T2 xm, T2 xo) {
+    T2 v;
+    if (axis == kAxisX) {          // i x_other
+        v.x = -xo.y; v.y = xo.x;
+    } else if (axis == kAxisY) {   // beta=0: i(-i x1) = x1 ; beta=1: i(i x0) = -x0
+        if (beta) { v.x = -xo.x; v.y = -xo.y; } else { v = xo; }
+    } else {                       // beta=0: i x0 ; beta=1: -i x1
+        if (beta) { v.x = xm.y; v.y = -xm.x; } else { v.x = -xm.y; v.y = xm.x; }
+    }
+    return v;
+}
+
+// (sigma x)_beta
+template <typename T2> __device__ __forceinline__ T2 sigma_of(int axis, int beta, T2 xm, T2 xo) {
+    T2 v;
+    if (axis == kAxisX) {
+        v = xo;
+    } else if (axis == kAxisY) {   // beta=0: -i x1 ; beta=1: i x0
+        if (beta) { v.x = -xo.y; v.y = xo.x; } else { v.x = xo.y; v.y = -xo.x; }
+    } else {
+        v = beta ? T2{-xm.x, -xm.y} : xm;
+    }
+    return v;
+}
+
+// Rotation y = c x + i s' sigma x in one of three forms (see DevCoef).
+template <typename R> struct Rot {
+    R c, s, t;
+    int caseB;
+    __device__ __forceinline__ typename CX<R>::T apply(typename CX<R>::T x, typename CX<R>::T v) const {
+        typename CX<R>::T y;
+        if (std::is_same<R, double>::value) {
+            if (caseB) { y.x = fma(t, x.x, v.x); y.y = fma(t, x.y, v.y); }
+            else       { y.x = fma(t, v.x, x.x); y.y = fma(t, v.y, x.y); }
+        } else {
+            y.x = fma(s, v.x, c * x.x); y.y = fma(s, v.y, c * x.y);
+        }
+        return y;
+    }
+};
+
+// adjoint (R^dag) or forward (R) coefficients of parameter k; f receives the scale factor
+template <typename R> __device__ __forceinline__ Rot<R> make_rot(const DevCoef &co, bool adjoint, double &f) {
+    Rot<R> r;
+    const double sg = adjoint ? 1.0 : -1.0;
+    r.c = (R)co.c;
+    r.s = (R)(sg * co.s);
+    r.t = (R)(sg * co.t);
+    r.caseB = co.caseB;
+    f = co.caseB ? sg * co.f : co.f;
+    return r;
+}
+
+template <typename RA> __device__ __forceinline__ RA warp_sum(RA v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------------------------------
+// Cluster-resident state: CTA `rank` holds amplitudes [rank * Nl, (rank + 1) * Nl) in buf.
+// Qubits >= nl are distributed; a pair on such a qubit has its halves in two CTAs at the same
+// local index. A distributed op pushes the CTA's half into the partner's receive buffer (two
+// buffers used alternately), then one cluster barrier, then each CTA writes its own half.
+// Every CTA of a cluster runs the same op sequence, so the barriers match.
+template <typename R> struct Eng {
+    using cx = typename CX<R>::T;
+    cx *buf, *rv0, *rv1;
+    int n, nl, cl, rank, phase;
+    uint32_t Nl;
+    uint64_t base;  // global index of buf[0]
+
+    __device__ void csync() const {
+        if (cl) cg::this_cluster().sync(); else __syncthreads();
+    }
+
+    // push my slice to the partner across distributed qubit q; returns my receive buffer
+    __device__ cx *exchange(int q) {
+        const int db = q - nl;
+        const int partner = rank ^ (1 << db);
+        cx *mine = phase ? rv1 : rv0;
+        cx *remote = cg::this_cluster().map_shared_rank(mine, partner);
+        for (uint32_t l = threadIdx.x; l < Nl; l += blockDim.x) remote[l] = buf[l];
+        cg::this_cluster().sync();
+        phase ^= 1;
+        return mine;
+    }
+
+    // one fixed gate (all are self-adjoint); scale absorbs the 1/sqrt2 of H in float64
+    __device__ void fixed_gate(const DevFixed g, double &scale) {
+        const int kind = g.kind;
+        if (kind == QNG_GATE_CZ || kind == QNG_GATE_Z) {
+            const uint64_t m = (kind == QNG_GATE_CZ) ? ((1ull << g.q0) | (1ull << g.q1)) : (1ull << g.q0);
+            for (uint32_t l = threadIdx.x; l < Nl; l += blockDim.x) {
+                const uint64_t k = base | l;
+                if ((k & m) == m) { cx x = buf[l]; x.x = -x.x; x.y = -x.y; buf[l] = x; }
+            }
+            __syncthreads();
+            return;
+        }
+        const int q = (kind == QNG_GATE_CNOT) ? g.q1 : g.q0;
+        const uint64_t cm = (kind == QNG_GATE_CNOT) ? (1ull << g.q0) : 0ull;
+        const bool kScaled = std::is_same<R, double>::value;
+        const R hs = kScaled ? (R)1 : (R)0.70710678118654752440;
+        if (q < nl) {
+            const uint32_t bit = 1u << q, half = Nl >> 1;
+            for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+                const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
+                cx x0 = buf[l0], x1 = buf[l1], y0, y1;
+                if (kind == QNG_GATE_CNOT) {
+                    if ((base | l0) & cm) { y0 = x1; y1 = x0; } else { y0 = x0; y1 = x1; }
+                } else if (kind == QNG_GATE_X) {
+                    y0 = x1; y1 = x0;
+                } else if (kind == QNG_GATE_Y) {
+                    y0.x = x1.y; y0.y = -x1.x; y1.x = -x0.y; y1.y = x0.x;
+                } else {  // H
+                    y0.x = (x0.x + x1.x) * hs; y0.y = (x0.y + x1.y) * hs;
+                    y1.x = (x0.x - x1.x) * hs; y1.y = (x0.y - x1.y) * hs;
+                }
+                buf[l0] = y0; buf[l1] = y1;
+            }
+            __syncthreads();
+        } else {
+            const cx *rv = exchange(q);
+            const int beta = (rank >> (q - nl)) & 1;
+            for (uint32_t l = threadIdx.x; l < Nl; l += blockDim.x) {
+                const cx xm = buf[l], xo = rv[l];
+                cx y;
+                if (kind == QNG_GATE_CNOT) {
+                    y = ((base | l) & cm) ? xo : xm;
+                } else if (kind == QNG_GATE_X) {
+                    y = xo;
+                } else if (kind == QNG_GATE_Y) {
+                    y = beta ? cx{-xo.y, xo.x} : cx{xo.y, -xo.x};
+                } else {  // H: y0 = x0 + x1, y1 = x0 - x1
+                    y = beta ? cx{(xo.x - xm.x) * hs, (xo.y - xm.y) * hs} : cx{(xm.x + xo.x) * hs, (xm.y + xo.y) * hs};
+                }
+                buf[l] = y;
+            }
+            __syncthreads();
+        }
+        if (kind == QNG_GATE_H && kScaled) scale *= 0.70710678118654752440;
+    }
+
+    // keep the float64 scale factor far from underflow: fold 2^-200 into the vector (exact)
+    __device__ void maybe_renorm(double &scale) {
+        if constexpr (std::is_same<R, double>::value) {
+            const double lim = 0x1p-200;
+            if (fabs(scale) < lim) {
+                for (uint32_t l = threadIdx.x; l < Nl; l += blockDim.x) {
+                    cx x = buf[l];
+                    x.x *= lim; x.y *= lim;
+                    buf[l] = x;
+                }
+                scale *= 0x1p200;
+                __syncthreads();
+            }
+        }
+    }
+};
+
+template <typename R> __device__ __forceinline__ Eng<R> make_eng(unsigned char *smem, int n, int cl) {
+    Eng<R> e;
+    using cx = typename CX<R>::T;
+    e.n = n;
+    e.cl = cl;
+    e.nl = n - cl;
+    e.Nl = 1u << e.nl;
+    e.rank = cl ? (int)cg::this_cluster().block_rank() : 0;
+    e.base = (uint64_t)e.rank << e.nl;
+    e.buf = reinterpret_cast<cx *>(smem);
+    e.rv0 = e.buf + e.Nl;
+    e.rv1 = e.rv0 + e.Nl;
+    e.phase = 0;
+    return e;
+}
+
+// Sum a per-thread double over the CTA, then over the cluster; the result lands in rank 0's
+// thread 0. red must hold blockDim/32 doubles of shared memory.
+__device__ double cluster_sum(double v, double *red, int cl) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (cl) cg::this_cluster().sync();
+    double tot = 0.0;
+    if (threadIdx.x == 0 && (!cl || cg::this_cluster().block_rank() == 0)) {
+        const int C = 1 << cl;
+        for (int r = 0; r < C; ++r) {
+            const double *rr = cl ? cg::this_cluster().map_shared_rank(red, r) : red;
+            for (int w = 0; w < nw; ++w) tot += rr[w];
+        }
+    }
+    if (cl) cg::this_cluster().sync();
+    return tot;
+}
+
+// ------------------------------------------------------------------------------------------
+__global__ void k_coef(const double *theta, DevCoef *coef, int64_t total, int32_t *status) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const double th = theta[k];
+    if (!isfinite(th)) atomicCAS(status, 0, (int)QNG_ERR_ARG);
+    double s, c;
+    sincos(0.5 * th, &s, &c);
+    DevCoef co;
+    co.c = c;
+    co.s = s;
+    if (fabs(c) >= fabs(s)) { co.caseB = 0; co.f = c; co.t = s / c; }
+    else                    { co.caseB = 1; co.f = s; co.t = c / s; }
+    co.pad = 0;
+    coef[k] = co;
+}
+
+// ------------------------------------------------------------------------------------------
+// k_forward: one cluster per instance of the group.
+template <typename R>
+__global__ void __launch_bounds__(1024) k_forward(Work w, int group_first, int cl, int want_eta) {
+    using cx = typename CX<R>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevInst in = w.inst[w.group_inst[group_first + (blockIdx.x >> cl)]];
+    Eng<R> e = make_eng<R>(smem, in.n, cl);
+    double *red = reinterpret_cast<double *>(e.buf + (cl ? 3 : 1) * e.Nl);
+    const uint64_t N = 1ull << in.n;
+    cx *ckpt = reinterpret_cast<cx *>(w.ckpt) + in.ckpt_off;
+    double *scales = w.scale + in.scale_off;
+
+    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+        cx z = {0, 0};
+        if ((e.base | l) == 0) z.x = 1;
+        e.buf[l] = z;
+        ckpt[e.base | l] = z;
+    }
+    double scale = 1.0;
+    if (e.rank == 0 && threadIdx.x == 0) scales[0] = 1.0;
+    __syncthreads();
+
+    for (int k = 0; k < in.P; ++k) {
+        const DevParam pk = w.param[in.param_tab + k];
+        if (pk.diag_count < 0)
+            for (int f = 0; f < pk.fix_count; ++f) e.fixed_gate(w.fixed[pk.fix_begin + f], scale);
+        const bool pre = pk.diag_count > 0 || pk.zmask != 0;
+        double fs;
+        const Rot<R> rot = make_rot<R>(w.coef[in.param_off + k], false, fs);
+        cx *out = ckpt + (uint64_t)(k + 1) * N;
+        const int q = pk.q, axis = pk.axis;
+        if (axis == kAxisZ) {
+            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+                const uint64_t kk = e.base | l;
+                cx x = e.buf[l];
+                if (pre) x = neg_if(x, diag_parity(kk, pk, w.diag));
+                const int beta = (int)((kk >> q) & 1);
+                const cx y = rot.apply(x, i_sigma(axis, beta, x, x));
+                e.buf[l] = y;
+                out[kk] = y;
+            }
+            __syncthreads();
+        } else if (q < e.nl) {
+            const uint32_t bit = 1u << q, half = e.Nl >> 1;
+            for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+                const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
+                cx x0 = e.buf[l0], x1 = e.buf[l1];
+                if (pre) {
+                    x0 = neg_if(x0, diag_parity(e.base | l0, pk, w.diag));
+                    x1 = neg_if(x1, diag_parity(e.base | l1, pk, w.diag));
+                }
+                const cx y0 = rot.apply(x0, i_sigma(axis, 0, x0, x1));
+                const cx y1 = rot.apply(x1, i_sigma(axis, 1, x1, x0));
+                e.buf[l0] = y0; e.buf[l1] = y1;
+                out[e.base | l0] = y0; out[e.base | l1] = y1;
+            }
+            __syncthreads();
+        } else {
+            const cx *rv = e.exchange(q);
+            const int beta = (e.rank >> (q - e.nl)) & 1;
+            const uint64_t m = 1ull << q;
+            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+                const uint64_t kk = e.base | l;
+                cx xm = e.buf[l], xo = rv[l];
+                if (pre) {
+                    xm = neg_if(xm, diag_parity(kk, pk, w.diag));
+                    xo = neg_if(xo, diag_parity(kk ^ m, pk, w.diag));
+                }
+                const cx y = rot.apply(xm, i_sigma(axis, beta, xm, xo));
+                e.buf[l] = y;
+                out[kk] = y;
+            }
+            __syncthreads();
+        }
+        if (std::is_same<R, double>::value) scale *= fs;
+        e.maybe_renorm(scale);
+        if (e.rank == 0 && threadIdx.x == 0) scales[k + 1] = scale;
+    }
+
+    // trailing fixed gates W, then H W psi, <E> and eta = W^dag H W psi
+    for (int f = 0; f < in.w_count; ++f) e.fixed_gate(w.fixed[in.w_begin + f], scale);
+    cx *eta = reinterpret_cast<cx *>(w.eta) + in.eta_off;
+    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) eta[e.base | l] = e.buf[l];
+    __syncthreads();
+    e.csync();  // W psi visible to the whole cluster through global memory
+    double epart = 0.0;
+    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+        const uint64_t kk = e.base | l;
+        double hr = 0.0, hi = 0.0;
+        for (int t = 0; t < in.nterms; ++t) {
+            const DevTerm tm = w.term[in.term_off + t];
+            const uint64_t src = kk ^ tm.x;
+            const cx v = __ldcg(eta + src);
+            const int ph = (tm.ny + 2 * (__popcll(src & tm.z) & 1)) & 3;
+            const double vr = (double)v.x, vi = (double)v.y;
+            // i^ph * coeff * v
+            if (ph == 0)      { hr = fma(tm.coeff, vr, hr);  hi = fma(tm.coeff, vi, hi); }
+            else if (ph == 1) { hr = fma(-tm.coeff, vi, hr); hi = fma(tm.coeff, vr, hi); }
+            else if (ph == 2) { hr = fma(-tm.coeff, vr, hr); hi = fma(-tm.coeff, vi, hi); }
+            else              { hr = fma(tm.coeff, vi, hr);  hi = fma(-tm.coeff, vr, hi); }
+        }
+        const cx x = e.buf[l];
+        epart += (double)x.x * hr + (double)x.y * hi;
+        e.buf[l] = cx{(R)hr, (R)hi};
+    }
+    __syncthreads();
+    const double esum = cluster_sum(epart, red, cl);  // also orders the reads of eta before the writes below
+    if (e.rank == 0 && threadIdx.x == 0) w.energy[w.group_inst[group_first + (blockIdx.x >> cl)]] = esum * scale * scale;
+    if (want_eta) {
+        for (int f = in.w_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[in.w_begin + f], scale);
+        for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) eta[e.base | l] = e.buf[l];
+        if (e.rank == 0 && threadIdx.x == 0) scales[in.P + 1] = scale;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// k_columns: one cluster per work item (instance, column).
+template <typename R>
+__global__ void __launch_bounds__(1024) k_columns(Work w, int work_first, int cl, int max_P) {
+    using cx = typename CX<R>::T;
+    using RA = R;  // per-thread partial sums; float64 from the warp level on
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevWork wk = w.work[work_first + (blockIdx.x >> cl)];
+    const DevInst in = w.inst[wk.inst];
+    Eng<R> e = make_eng<R>(smem, in.n, cl);
+    const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double *red = reinterpret_cast<double *>(e.buf + (cl ? 3 : 1) * e.Nl);  // [(max_P + 1) * nw]
+    double *fac = red + (size_t)(max_P + 1) * nw;                              // [max_P + 1]
+    const uint64_t N = 1ull << in.n;
+    const cx *ckpt = reinterpret_cast<const cx *>(w.ckpt) + in.ckpt_off;
+    const double *scales = w.scale + in.scale_off;
+    const int P = in.P;
+    const bool grad_col = (wk.col == P);
+
+    double scale_b;
+    int nsteps, i0;
+    if (!grad_col) {
+        // b = F_j^dag sigma_j F_j Psi[j] = U_j^dag sigma_j Psi[j+1]; e_j = <Psi[j]|b>
+        const int j = wk.col;
+        const DevParam pj = w.param[in.param_tab + j];
+        const cx *psi = ckpt + (uint64_t)j * N;
+        scale_b = scales[j];
+        double escale = 1.0;  // scale of F_j Psi[j] relative to Psi[j] (float64 form with H gates)
+        RA ep = 0;
+        if (pj.diag_count >= 0) {
+            const uint64_t m = (pj.axis == kAxisZ) ? 0ull : (1ull << pj.q);
+            const bool diag = pj.diag_count > 0 || pj.zmask != 0;
+            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+                const uint64_t kk = e.base | l, kp = kk ^ m;
+                const int beta = (int)((kk >> pj.q) & 1);
+                const cx xo = psi[kp];
+                const cx xm = m ? psi[kk] : xo;
+                cx v = sigma_of(pj.axis, beta, xo, xo);  // (sigma y)[kk] from y[kp]
+                if (diag) v = neg_if(v, diag_parity(kk, pj, w.diag) ^ diag_parity(kp, pj, w.diag));
+                e.buf[l] = v;
+                ep += xm.x * v.x + xm.y * v.y;
+            }
+            __syncthreads();
+        } else {
+            // general F_j: load Psi[j], apply F_j, take e_j and apply sigma_j, then undo F_j
+            double sF = 1.0;
+            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) e.buf[l] = psi[e.base | l];
+            __syncthreads();
+            for (int f = 0; f < pj.fix_count; ++f) e.fixed_gate(w.fixed[pj.fix_begin + f], sF);
+            escale = sF;
+            const int q = pj.q, axis = pj.axis;
+            if (axis == kAxisZ) {
+                for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+                    const uint64_t kk = e.base | l;
+                    const cx x = e.buf[l];
+                    const cx v = sigma_of(axis, (int)((kk >> q) & 1), x, x);
+                    ep += x.x * v.x + x.y * v.y;
+                    e.buf[l] = v;
+                }
+                __syncthreads();
+            } else if (q < e.nl) {
+                const uint32_t bit = 1u << q, half = e.Nl >> 1;
+                for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+                    const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
+                    const cx x0 = e.buf[l0], x1 = e.buf[l1];
+                    const cx v0 = sigma_of(axis, 0, x0, x1), v1 = sigma_of(axis, 1, x1, x0);
+                    ep += x0.x * v0.x + x0.y * v0.y + x1.x * v1.x + x1.y * v1.y;
+                    e.buf[l0] = v0; e.buf[l1] = v1;
+                }
+                __syncthreads();
+            } else {
+                const cx *rv = e.exchange(q);
+                const int beta = (e.rank >> (q - e.nl)) & 1;
+                for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+                    const cx xm = e.buf[l];
+                    const cx v = sigma_of(axis, beta, xm, rv[l]);
+                    ep += xm.x * v.x + xm.y * v.y;
+                    e.buf[l] = v;
+                }
+                __syncthreads();
+            }
+            for (int f = pj.fix_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[pj.fix_begin + f], sF);
+            scale_b *= sF;
+        }
+        const double epw = warp_sum((double)ep);
+        if (lane == 0) red[(size_t)max_P * nw + wid] = epw;
+        if (threadIdx.x == 0) fac[max_P] = scales[j] * escale * scales[j] * escale;
+        nsteps = j;
+        i0 = j - 1;
+    } else {
+        const cx *eta = reinterpret_cast<const cx *>(w.eta) + in.eta_off;
+        for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) e.buf[l] = eta[e.base | l];
+        scale_b = scales[P + 1];
+        nsteps = P;
+        i0 = P - 1;
+        __syncthreads();
+    }
+
+    const bool want_im = grad_col;
+    for (int s = 0; s < nsteps; ++s) {
+        const int i = i0 - s;
+        const DevParam pi = w.param[in.param_tab + i];
+        const cx *a = ckpt + (uint64_t)(i + 1) * N;
+        if (threadIdx.x == 0) fac[s] = scales[i + 1] * scale_b;
+        const bool rot_on = (i > 0);
+        double fs = 1.0;
+        const Rot<R> rot = make_rot<R>(w.coef[in.param_off + i], true, fs);
+        const bool post = rot_on && (pi.diag_count > 0 || pi.zmask != 0);
+        const int q = pi.q, axis = pi.axis;
+        RA part = 0;
+        if (axis == kAxisZ) {
+            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+                const uint64_t kk = e.base | l;
+                const int beta = (int)((kk >> q) & 1);
+                const cx x = e.buf[l];
+                const cx av = a[kk];
+                const cx sb = sigma_of(axis, beta, x, x);
+                part += want_im ? (av.x * sb.y - av.y * sb.x) : (av.x * sb.x + av.y * sb.y);
+                if (rot_on) {
+                    cx y = rot.apply(x, i_sigma(axis, beta, x, x));
+                    if (post) y = neg_if(y, diag_parity(kk, pi, w.diag));
+                    e.buf[l] = y;
+                }
+            }
+            __syncthreads();
+        } else if (q < e.nl) {
+            const uint32_t bit = 1u << q, half = e.Nl >> 1;
+            for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+                const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
+                const cx x0 = e.buf[l0], x1 = e.buf[l1];
+                const cx a0 = a[e.base | l0], a1 = a[e.base | l1];
+                const cx s0 = sigma_of(axis, 0, x0, x1), s1 = sigma_of(axis, 1, x1, x0);
+                if (want_im) part += (a0.x * s0.y - a0.y * s0.x) + (a1.x * s1.y - a1.y * s1.x);
+                else         part += (a0.x * s0.x + a0.y * s0.y) + (a1.x * s1.x + a1.y * s1.y);
+                if (rot_on) {
+                    cx y0 = rot.apply(x0, i_sigma(axis, 0, x0, x1));
+                    cx y1 = rot.apply(x1, i_sigma(axis, 1, x1, x0));
+                    if (post) {
+                        y0 = neg_if(y0, diag_parity(e.base | l0, pi, w.diag));
+                        y1 = neg_if(y1, diag_parity(e.base | l1, pi, w.diag));
+                    }
+                    e.buf[l0] = y0; e.buf[l1] = y1;
+                }
+            }
+            __syncthreads();
+        } else {
+            const cx *rv = e.exchange(q);
+            const int beta = (e.rank >> (q - e.nl)) & 1;
+            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+                const uint64_t kk = e.base | l;
+                const cx xm = e.buf[l], xo = rv[l];
+                const cx av = a[kk];
+                const cx sb = sigma_of(axis, beta, xm, xo);
+                part += want_im ? (av.x * sb.y - av.y * sb.x) : (av.x * sb.x + av.y * sb.y);
+                if (rot_on) {
+                    cx y = rot.apply(xm, i_sigma(axis, beta, xm, xo));
+                    if (post) y = neg_if(y, diag_parity(kk, pi, w.diag));
+                    e.buf[l] = y;
+                }
+            }
+            __syncthreads();
+        }
+        if (rot_on) {
+            if (std::is_same<R, double>::value) scale_b *= fs;
+            if (pi.diag_count < 0)
+                for (int f = pi.fix_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[pi.fix_begin + f], scale_b);
+            e.maybe_renorm(scale_b);
+        }
+        const double pw = (double)warp_sum(part);
+        if (lane == 0) red[(size_t)s * nw + wid] = pw;
+    }
+
+    // reduce the per-warp partial sums over the cluster (rank 0) and write the results
+    __syncthreads();
+    if (cl) cg::this_cluster().sync();
+    if (e.rank == 0) {
+        const int C = 1 << cl;
+        const int rows = grad_col ? nsteps : nsteps + 1;
+        for (int s = threadIdx.x; s < rows; s += blockDim.x) {
+            const int row = (s < nsteps) ? s : max_P;
+            double tot = 0.0;
+            for (int r = 0; r < C; ++r) {
+                const double *rr = cl ? cg::this_cluster().map_shared_rank(red, r) : red;
+                for (int ww = 0; ww < nw; ++ww) tot += rr[(size_t)row * nw + ww];
+            }
+            tot *= fac[row];
+            if (grad_col) {
+                w.gradraw[in.param_off + (i0 - s)] = -tot;
+            } else if (s < nsteps) {
+                w.L[in.metric_off + (int64_t)(i0 - s) * P + wk.col] = 0.25 * tot;
+            } else {
+                w.sigma[in.param_off + wk.col] = tot;
+            }
+        }
+    }
+    if (cl) cg::this_cluster().sync();
+}
+
+// ------------------------------------------------------------------------------------------
+// k_finish: one CTA per instance. Assembly of g (Eq. g_t_L_def with L_ii = 1/4 and
+// T_k = -(i/2) sigma_k), outputs, and the Cholesky solve of (g + lambda I) dtheta = -dt grad.
+__global__ void __launch_bounds__(512) k_finish(Work w, LaunchArgs a) {
+    __shared__ double sh[2];
+    __shared__ int bad;
+    const int b = blockIdx.x;
+    const DevInst in = w.inst[b];
+    const int P = in.P;
+    const double *sg = w.sigma + in.param_off;
+    const double *L = w.L + in.metric_off;
+    const bool metric = a.jobs & (kJobMetric | kJobSolve);
+    double *A = w.chol + in.metric_off;
+    if (metric) {
+        for (int64_t idx = threadIdx.x; idx < (int64_t)P * P; idx += blockDim.x) {
+            const int i = (int)(idx / P), j = (int)(idx % P);
+            double v;
+            if (i == j) v = 0.25 * (1.0 - sg[i] * sg[i]);
+            else if (i < j) v = L[(int64_t)i * P + j] - 0.25 * sg[i] * sg[j];
+            else v = L[(int64_t)j * P + i] - 0.25 * sg[i] * sg[j];
+            if (a.g_out) a.g_out[in.metric_off + idx] = v;
+            if (a.jobs & kJobSolve) A[idx] = v + (i == j ? a.lambda : 0.0);
+        }
+        if (a.sigma_out)
+            for (int k = threadIdx.x; k < P; k += blockDim.x) a.sigma_out[in.param_off + k] = sg[k];
+    }
+    if (a.jobs & kJobGradient) {
+        const double gs = a.grad_scale ? a.grad_scale[b] : 1.0;
+        if (a.grad_out)
+            for (int k = threadIdx.x; k < P; k += blockDim.x) a.grad_out[in.param_off + k] = gs * w.gradraw[in.param_off + k];
+    }
+    if ((a.jobs & (kJobGradient | kJobEnergy)) && a.energy_out && threadIdx.x == 0) a.energy_out[b] = w.energy[b];
+    if (!(a.jobs & kJobSolve) || P == 0) return;
+    __syncthreads();
+    // right-looking Cholesky, lower triangle, in place
+    if (threadIdx.x == 0) bad = 0;
+    for (int k = 0; k < P; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = A[(int64_t)k * P + k];
+            if (!(d > 0.0)) { bad = 1; atomicCAS(w.status, 0, (int)QNG_ERR_NOT_SPD); }
+            const double r = sqrt(d);
+            A[(int64_t)k * P + k] = r;
+            sh[0] = 1.0 / r;
+        }
+        __syncthreads();
+        if (bad) return;
+        const double inv = sh[0];
+        for (int i = k + 1 + threadIdx.x; i < P; i += blockDim.x) A[(int64_t)i * P + k] *= inv;
+        __syncthreads();
+        const int m = P - k - 1;
+        for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
+            const int i = k + 1 + (int)(t / m), j = k + 1 + (int)(t % m);
+            if (j <= i) A[(int64_t)i * P + j] -= A[(int64_t)i * P + k] * A[(int64_t)j * P + k];
+        }
+        __syncthreads();
+    }
+    // forward substitution L y = -dt grad, then L^T x = y (x in dtheta)
+    double *x = a.dtheta_out + in.param_off;
+    const double *gr = w.gradraw + in.param_off;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) x[k] = -a.dt * gr[k];
+    __syncthreads();
+    for (int k = 0; k < P; ++k) {
+        if (threadIdx.x == 0) { x[k] /= A[(int64_t)k * P + k]; sh[1] = x[k]; }
+        __syncthreads();
+        const double xk = sh[1];
+        for (int i = k + 1 + threadIdx.x; i < P; i += blockDim.x) x[i] -= A[(int64_t)i * P + k] * xk;
+        __syncthreads();
+    }
+    for (int k = P - 1; k >= 0; --k) {
+        if (threadIdx.x == 0) { x[k] /= A[(int64_t)k * P + k]; sh[1] = x[k]; }
+        __syncthreads();
+        const double xk = sh[1];
+        for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] -= A[(int64_t)k * P + i] * xk;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// launchers
+template <typename K>
+static cudaError_t launch_cluster(K kern, int grid, int threads, size_t smem, int cl, cudaStream_t st,
+                                  Work w, int a0, int a1, int a2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (cl > 0) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1u << cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, w, a0, a1, a2);
+}
+
+template <typename K> static cudaError_t set_attrs(K kern, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+// smem_fwd / smem_col: the largest dynamic shared memory any group launches the kernels with
+cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col) {
+    cudaError_t e;
+    if (precision == QNG_C128) {
+        if ((e = set_attrs(k_forward<double>, smem_fwd)) != cudaSuccess) return e;
+        return set_attrs(k_columns<double>, smem_col);
+    }
+    if ((e = set_attrs(k_forward<float>, smem_fwd)) != cudaSuccess) return e;
+    return set_attrs(k_columns<float>, smem_col);
+}
+
+cudaError_t launch_coef(const Work &w, const double *theta, int64_t total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    const int t = 256;
+    k_coef<<<(unsigned)((total + t - 1) / t), t, 0, st>>>(theta, w.coef, total, w.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const Work &w, const Group &g, int precision, int want_eta, cudaStream_t st) {
+    if (g.num_inst == 0) return cudaSuccess;
+    const int grid = g.num_inst << g.cl;
+    if (precision == QNG_C128)
+        return launch_cluster(k_forward<double>, grid, g.threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
+    return launch_cluster(k_forward<float>, grid, g.threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
+}
+
+cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
+                           cudaStream_t st) {
+    int first, num;
+    if (with_metric && with_grad) { first = g.first_work; num = g.num_work; }
+    else if (with_metric)         { first = g.first_met; num = g.num_met; }
+    else                          { first = g.first_grad; num = g.num_grad; }
+    if (num == 0) return cudaSuccess;
+    const int grid = num << g.cl;
+    if (precision == QNG_C128)
+        return launch_cluster(k_columns<double>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P);
+    return launch_cluster(k_columns<float>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P);
+}
+
+cudaError_t launch_finish(const Work &w, int count, int max_P, const LaunchArgs &a, cudaStream_t st) {
+    const int t = max_P >= 128 ? 512 : 128;
+    k_finish<<<count, t, 0, st>>>(w, a);
+    return cudaGetLastError();
+}
+
+}  // namespace qng

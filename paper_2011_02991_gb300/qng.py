@@ -1,0 +1,280 @@
+"""Python binding of libqng (argument marshalling only; every step runs in the CUDA kernels).
+
+The ``qng_*`` functions mirror the C ABI of ``include/qng.h`` one to one. ``Context`` wraps them
+for PyTorch users: PyTorch provides the device workspace and the stream, the library does the
+work. There is no CPU fallback: without a built ``libqng.so`` or without a CUDA device every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from . import workloads as W
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libqng.so")
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "host allocation failed", 3: "CUDA error", 4: "device wait timed out",
+          5: "g + lambda I is not positive definite", 6: "workspace missing, too small or misaligned",
+          7: "unsupported request"}
+QNG_OK, QNG_ERR_ARG, QNG_ERR_OOM, QNG_ERR_CUDA, QNG_ERR_TIMEOUT, QNG_ERR_NOT_SPD, QNG_ERR_WORKSPACE, QNG_ERR_UNSUPPORTED = range(8)
+
+
+class QngError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, 'unknown status')} ({status})")
+        self.status = status
+
+
+class qng_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("q0", ctypes.c_int32), ("q1", ctypes.c_int32), ("param", ctypes.c_int32)]
+
+
+class qng_pauli(ctypes.Structure):
+    _fields_ = [("coeff", ctypes.c_double), ("xmask", ctypes.c_uint64), ("zmask", ctypes.c_uint64)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+SYMBOLS = {
+    "qng_create": [ctypes.c_int, ctypes.POINTER(qng_gate), ctypes.c_int, ctypes.POINTER(qng_pauli), ctypes.c_int,
+                   ctypes.c_int, ctypes.POINTER(_vp)],
+    "qng_create_batch": [ctypes.c_int, _i32p, ctypes.POINTER(qng_gate), _i32p, ctypes.POINTER(qng_pauli), _i32p,
+                         ctypes.c_int, ctypes.POINTER(_vp)],
+    "qng_get_sizes": [_vp, _i32p, _i64p, _i64p],
+    "qng_get_offsets": [_vp, _i64p, _i64p],
+    "qng_workspace_size": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+    "qng_set_workspace": [_vp, _vp, ctypes.c_size_t, _vp],
+    "qng_set_stream": [_vp, _vp],
+    "qng_metric": [_vp, _vp, _vp, _vp],
+    "qng_gradient": [_vp, _vp, _vp, _vp],
+    "qng_energy": [_vp, _vp, _vp],
+    "qng_energy_backward": [_vp, _vp, _vp, _vp],
+    "qng_step": [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp],
+    "qng_step_host": [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp],
+    "qng_sync": [_vp],
+    "qng_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "qng_last_launch_count": [_vp, _i64p],
+    "qng_destroy": [_vp],
+    "qng_status_string": [ctypes.c_int],
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libqng.so (built by ``paper_2011_02991_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libqng.so not built ({path}); run paper_2011_02991_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        for name, args in SYMBOLS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name == "qng_status_string" else (None if name == "qng_destroy" else ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def _chk(status: int, where: str):
+    if status != QNG_OK:
+        raise QngError(status, where)
+
+
+def _gates_array(circuit: W.Circuit):
+    g = np.ascontiguousarray(circuit.gates, dtype=np.int32)
+    arr = (qng_gate * max(len(g), 1))()
+    ctypes.memmove(arr, g.ctypes.data, g.nbytes)
+    return arr, len(g)
+
+
+def _terms_array(ham: W.Hamiltonian):
+    T = ham.num_terms
+    arr = (qng_pauli * max(T, 1))()
+    for t in range(T):
+        arr[t].coeff = float(ham.coeffs[t])
+        arr[t].xmask = int(ham.xmask[t])
+        arr[t].zmask = int(ham.zmask[t])
+    return arr, T
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Context:
+    """A libqng context over one or more instances, with a torch-allocated workspace.
+
+    ``problems`` is a Problem or a list of Problems (a batch). theta and the per-parameter outputs
+    are concatenated over instances; metrics are concatenated P_b x P_b blocks.
+    """
+
+    def __init__(self, problems, precision: int | None = None, device=None, stream: torch.cuda.Stream | None = None):
+        L = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqng needs a CUDA device")
+        self.problems = [problems] if isinstance(problems, W.Problem) else list(problems)
+        self.precision = self.problems[0].precision if precision is None else precision
+        self.device = torch.device(device if device is not None else "cuda")
+        self._h = _vp()
+        if len(self.problems) == 1:
+            p = self.problems[0]
+            ga, ng = _gates_array(p.circuit)
+            ta, nt = _terms_array(p.hamiltonian)
+            _chk(L.qng_create(p.n, ga, ng, ta, nt, self.precision, ctypes.byref(self._h)), "qng_create")
+        else:
+            rows = [np.ascontiguousarray(p.circuit.gates, dtype=np.int32) for p in self.problems]
+            allg = np.concatenate(rows) if rows else np.zeros((0, 4), np.int32)
+            ga = (qng_gate * max(len(allg), 1))()
+            ctypes.memmove(ga, allg.ctypes.data, allg.nbytes)
+            nq = np.array([p.n for p in self.problems], dtype=np.int32)
+            ngs = np.array([len(r) for r in rows], dtype=np.int32)
+            nts = np.array([p.hamiltonian.num_terms for p in self.problems], dtype=np.int32)
+            ta = (qng_pauli * max(int(nts.sum()), 1))()
+            k = 0
+            for p in self.problems:
+                h = p.hamiltonian
+                for t in range(h.num_terms):
+                    ta[k].coeff = float(h.coeffs[t]); ta[k].xmask = int(h.xmask[t]); ta[k].zmask = int(h.zmask[t])
+                    k += 1
+            _chk(L.qng_create_batch(len(self.problems), nq.ctypes.data_as(_i32p), ga, ngs.ctypes.data_as(_i32p), ta,
+                                    nts.ctypes.data_as(_i32p), self.precision, ctypes.byref(self._h)), "qng_create_batch")
+        cnt = ctypes.c_int32()
+        tp, tm = ctypes.c_int64(), ctypes.c_int64()
+        _chk(L.qng_get_sizes(self._h, ctypes.byref(cnt), ctypes.byref(tp), ctypes.byref(tm)), "qng_get_sizes")
+        self.count, self.total_params, self.total_metric = cnt.value, tp.value, tm.value
+        po = np.zeros(self.count + 1, dtype=np.int64)
+        mo = np.zeros(self.count + 1, dtype=np.int64)
+        _chk(L.qng_get_offsets(self._h, po.ctypes.data_as(_i64p), mo.ctypes.data_as(_i64p)), "qng_get_offsets")
+        self.param_offsets, self.metric_offsets = po, mo
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._alloc_workspace()
+
+    def _alloc_workspace(self):
+        L = load()
+        nb = ctypes.c_size_t()
+        _chk(L.qng_workspace_size(self._h, ctypes.byref(nb)), "qng_workspace_size")
+        self.workspace = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
+        _chk(L.qng_set_workspace(self._h, _ptr(self.workspace), self.workspace.numel(),
+                                 ctypes.c_void_p(self.stream.cuda_stream)), "qng_set_workspace")
+
+    # -- helpers -----------------------------------------------------------------------------
+    def _f64(self, n):
+        return torch.empty(int(n), dtype=torch.float64, device=self.device)
+
+    def _theta(self, theta):
+        if not isinstance(theta, torch.Tensor):
+            theta = torch.as_tensor(np.asarray(theta, dtype=np.float64))
+        theta = theta.to(device=self.device, dtype=torch.float64).contiguous()
+        if theta.numel() != self.total_params:
+            raise ValueError(f"theta has {theta.numel()} entries, expected {self.total_params}")
+        return theta
+
+    def split_params(self, v: torch.Tensor):
+        return [v[self.param_offsets[b]:self.param_offsets[b + 1]] for b in range(self.count)]
+
+    def split_metric(self, g: torch.Tensor):
+        out = []
+        for b in range(self.count):
+            P = int(self.param_offsets[b + 1] - self.param_offsets[b])
+            out.append(g[self.metric_offsets[b]:self.metric_offsets[b + 1]].view(P, P))
+        return out
+
+    def theta0(self):
+        return torch.as_tensor(np.concatenate([p.theta for p in self.problems]), dtype=torch.float64, device=self.device)
+
+    # -- entry points --------------------------------------------------------------------------
+    def metric(self, theta, want_sigma: bool = False):
+        theta = self._theta(theta)
+        g = self._f64(self.total_metric)
+        sg = self._f64(self.total_params) if want_sigma else None
+        _chk(load().qng_metric(self._h, _ptr(theta), _ptr(g), _ptr(sg)), "qng_metric")
+        return (g, sg) if want_sigma else g
+
+    def gradient(self, theta):
+        theta = self._theta(theta)
+        gr, en = self._f64(self.total_params), self._f64(self.count)
+        _chk(load().qng_gradient(self._h, _ptr(theta), _ptr(gr), _ptr(en)), "qng_gradient")
+        return gr, en
+
+    def energy(self, theta):
+        theta = self._theta(theta)
+        en = self._f64(self.count)
+        _chk(load().qng_energy(self._h, _ptr(theta), _ptr(en)), "qng_energy")
+        return en
+
+    def energy_backward(self, theta, grad_out):
+        theta = self._theta(theta)
+        go = grad_out.to(device=self.device, dtype=torch.float64).contiguous()
+        gt = self._f64(self.total_params)
+        _chk(load().qng_energy_backward(self._h, _ptr(theta), _ptr(go), _ptr(gt)), "qng_energy_backward")
+        return gt
+
+    def step(self, theta, dt: float = 0.1, lam: float = 1e-3, outputs: dict | None = None):
+        """One QNG step; returns dict(dtheta, g, grad, energy) of device tensors."""
+        theta = self._theta(theta)
+        o = outputs if outputs is not None else {
+            "dtheta": self._f64(self.total_params), "g": self._f64(self.total_metric),
+            "grad": self._f64(self.total_params), "energy": self._f64(self.count)}
+        _chk(load().qng_step(self._h, _ptr(theta), float(dt), float(lam), _ptr(o["dtheta"]), _ptr(o.get("g")),
+                             _ptr(o.get("grad")), _ptr(o.get("energy"))), "qng_step")
+        return o
+
+    def step_host(self, theta_host: np.ndarray, dt: float = 0.1, lam: float = 1e-3, out: dict | None = None,
+                  want_all: bool = True):
+        """qng_step_host: host (numpy, ideally pinned) buffers in and out; waits for completion."""
+        th = np.ascontiguousarray(theta_host, dtype=np.float64)
+        o = out if out is not None else {"dtheta": np.empty(self.total_params), "g": np.empty(self.total_metric),
+                                         "grad": np.empty(self.total_params), "energy": np.empty(self.count)}
+        p = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+        _chk(load().qng_step_host(self._h, p(th), float(dt), float(lam), p(o["dtheta"]),
+                                  p(o.get("g")) if want_all else None, p(o.get("grad")) if want_all else None,
+                                  p(o.get("energy")) if want_all else None), "qng_step_host")
+        return o
+
+    def sync(self):
+        _chk(load().qng_sync(self._h), "qng_sync")
+
+    def set_tuning(self, min_qubits: int, cluster_log2: int, threads: int):
+        _chk(load().qng_set_tuning(self._h, min_qubits, cluster_log2, threads), "qng_set_tuning")
+
+    def last_launch_count(self) -> int:
+        v = ctypes.c_int64()
+        _chk(load().qng_last_launch_count(self._h, ctypes.byref(v)), "qng_last_launch_count")
+        return int(v.value)
+
+    def close(self):
+        if self._h:
+            load().qng_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Energy(torch.autograd.Function):
+    """<E>(theta) with the reverse-sweep (adjoint) backward of libqng."""
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, qctx: Context):
+        ctx.qctx = qctx
+        ctx.save_for_backward(theta)
+        return qctx.energy(theta)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (theta,) = ctx.saved_tensors
+        return ctx.qctx.energy_backward(theta, grad_out), None
+
+
+def energy(theta: torch.Tensor, qctx: Context) -> torch.Tensor:
+    return Energy.apply(theta, qctx)

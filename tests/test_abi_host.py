@@ -1,0 +1,115 @@
+"""CPU-only checks of the C ABI: the library loads, exports every declared symbol, and its host
+logic (validation, sizes, offsets, workspace layout) behaves. No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2011_02991_gb300 import build as B
+from paper_2011_02991_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    from paper_2011_02991_gb300 import qng
+    return qng.load()
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(qng_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "qng_create" in names and "qng_step" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def _create(lib, n, gates, terms=(), precision=W.C128):
+    from paper_2011_02991_gb300 import qng
+    ga = (qng.qng_gate * max(len(gates), 1))(*[qng.qng_gate(*g) for g in gates])
+    ta = (qng.qng_pauli * max(len(terms), 1))(*[qng.qng_pauli(*t) for t in terms])
+    h = ctypes.c_void_p()
+    st = lib.qng_create(n, ga, len(gates), ta, len(terms), precision, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("gates,n,expect", [
+    ([(W.RY, 0, -1, 0)], 1, 0),
+    ([(W.RY, 1, -1, 0)], 1, 1),            # qubit out of range
+    ([(W.RY, 0, -1, 1)], 1, 1),            # parameters must be numbered in circuit order
+    ([(W.CZ, 0, 0, -1)], 2, 1),            # two-qubit gate on one qubit
+    ([(W.CZ, 0, 1, 0)], 2, 1),             # fixed gate with a parameter
+    ([(42, 0, -1, -1)], 2, 1),             # unknown kind
+    ([(W.RX, 0, -1, 0), (W.H, 1, -1, -1), (W.RZ, 1, -1, 1)], 2, 0),
+    ([], 3, 0),                            # no gates at all
+    ([(W.RY, 0, -1, 0)], 17, 7),           # beyond the on-chip path of this build
+])
+def test_validation(lib, gates, n, expect):
+    st, h = _create(lib, n, gates)
+    assert st == expect
+    if st == 0:
+        lib.qng_destroy(h)
+
+
+def test_pauli_validation(lib):
+    st, h = _create(lib, 2, [(W.RY, 0, -1, 0)], [(1.0, 0b100, 0)])
+    assert st == 1
+    st, h = _create(lib, 2, [(W.RY, 0, -1, 0)], [(float("nan"), 1, 0)])
+    assert st == 1
+
+
+def test_sizes_offsets_workspace(lib):
+    from paper_2011_02991_gb300 import qng
+    probs = W.config_batch(count=5)
+    rows = [np.ascontiguousarray(p.circuit.gates, dtype=np.int32) for p in probs]
+    allg = np.concatenate(rows)
+    ga = (qng.qng_gate * len(allg))()
+    ctypes.memmove(ga, allg.ctypes.data, allg.nbytes)
+    terms = [(float(c), int(x), int(z)) for p in probs for c, x, z in
+             zip(p.hamiltonian.coeffs, p.hamiltonian.xmask, p.hamiltonian.zmask)]
+    ta = (qng.qng_pauli * len(terms))(*[qng.qng_pauli(*t) for t in terms])
+    nq = np.array([p.n for p in probs], dtype=np.int32)
+    ng = np.array([len(r) for r in rows], dtype=np.int32)
+    nt = np.array([p.hamiltonian.num_terms for p in probs], dtype=np.int32)
+    h = ctypes.c_void_p()
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    assert lib.qng_create_batch(5, nq.ctypes.data_as(i32), ga, ng.ctypes.data_as(i32), ta, nt.ctypes.data_as(i32),
+                                W.C64, ctypes.byref(h)) == 0
+    cnt, tp, tm = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    assert lib.qng_get_sizes(h, ctypes.byref(cnt), ctypes.byref(tp), ctypes.byref(tm)) == 0
+    Ps = [p.P for p in probs]
+    assert cnt.value == 5 and tp.value == sum(Ps) and tm.value == sum(P * P for P in Ps)
+    po = np.zeros(6, dtype=np.int64)
+    mo = np.zeros(6, dtype=np.int64)
+    i64 = ctypes.POINTER(ctypes.c_int64)
+    assert lib.qng_get_offsets(h, po.ctypes.data_as(i64), mo.ctypes.data_as(i64)) == 0
+    assert list(po) == list(np.concatenate([[0], np.cumsum(Ps)]))
+    assert list(mo) == list(np.concatenate([[0], np.cumsum([P * P for P in Ps])]))
+    nb = ctypes.c_size_t()
+    assert lib.qng_workspace_size(h, ctypes.byref(nb)) == 0
+    # checkpoints dominate: (P+1) 2^n complex64 amplitudes per instance
+    assert nb.value >= sum((p.P + 1) * (1 << p.n) * 8 for p in probs)
+    assert nb.value % 256 == 0
+    # compute calls without a workspace are refused on the host
+    theta = ctypes.c_void_p(0)
+    assert lib.qng_metric(h, theta, ctypes.c_void_p(8), None) == 6
+    assert lib.qng_set_workspace(h, ctypes.c_void_p(0x1000 + 8), nb.value, None) == 6  # misaligned
+    assert lib.qng_set_workspace(h, ctypes.c_void_p(0x1000), nb.value - 256, None) == 6  # too small
+    lib.qng_destroy(h)
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.qng_status_string(s)

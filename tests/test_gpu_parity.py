@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerance: relative max-abs error err(x) = max_k |x_k - x_k^o| / max_k |x_k^o|, at most 1e-10 for
+complex128 paths and 2e-4 for complex64 paths, applied separately to g, grad<E>, dtheta and <E>.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2011_02991_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {W.C128: 1e-10, W.C64: 2e-4}
+
+
+def rel(got, ref):
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)) if ref.size else 0.0
+
+
+@pytest.fixture(scope="module")
+def qng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_02991_gb300 import build as B
+    B.build()
+    from paper_2011_02991_gb300 import qng as Q
+    return Q
+
+
+def check_problem(qng, oracle, p, precision, tuning=None, tol=None):
+    ctx = qng.Context(p, precision=precision)
+    if tuning is not None:
+        ctx.set_tuning(*tuning)
+    out = ctx.step(ctx.theta0(), p.dt, p.lam)
+    g_s, sig = ctx.metric(ctx.theta0(), want_sigma=True)
+    ctx.sync()
+    ref = oracle.qng_step(p)
+    t = TOL[precision] if tol is None else tol
+    errs = {
+        "g": rel(out["g"].cpu(), ref["g"]),
+        "grad": rel(out["grad"].cpu(), ref["grad"]),
+        "dtheta": rel(out["dtheta"].cpu(), ref["dtheta"]),
+        "E": rel(out["energy"].cpu(), [ref["E"]]),
+        "g_metric_call": rel(g_s.cpu(), ref["g"]),
+        "sigma": rel(sig.cpu(), -2.0 * ref["T"].imag),  # T_k = -(i/2) sigma_k
+    }
+    bad = {k: v for k, v in errs.items() if not v <= t}
+    assert not bad, f"{p.name} precision={precision} tuning={tuning}: {bad} (tol {t})"
+    return errs
+
+
+def test_config_tfim4_c128(qng, oracle):
+    check_problem(qng, oracle, W.config_tfim4(), W.C128)
+
+
+@pytest.mark.parametrize("precision", [W.C128, W.C64])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_circuits_all_gate_kinds(qng, oracle, seed, precision):
+    """Every gate kind (Rx/Ry/Rz, CZ, CNOT, X, Y, Z, H), fixed gates before, between and after."""
+    p = W.random_problem(6, 60, 12, 500 + seed, precision)
+    check_problem(qng, oracle, p, precision)
+
+
+@pytest.mark.parametrize("cl", [0, 1, 2, 3])
+@pytest.mark.parametrize("precision", [W.C128, W.C64])
+def test_cluster_distribution(qng, oracle, cl, precision):
+    """The same circuit with the state split over 1, 2, 4, 8 CTAs (distributed top qubits)."""
+    p = W.random_problem(7, 70, 10, 900, precision)
+    check_problem(qng, oracle, p, precision, tuning=(0, cl, 64))
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+def test_cta_sizes(qng, oracle, threads):
+    p = W.random_problem(8, 50, 8, 77, W.C128)
+    check_problem(qng, oracle, p, W.C128, tuning=(0, 1, threads))
+
+
+def test_config_rand12_c128_full(qng, oracle):
+    """The 12-qubit, P = 192 workload, every entry against the oracle."""
+    check_problem(qng, oracle, W.config_rand12(), W.C128)
+
+
+def test_config_rand12_c64_full(qng, oracle):
+    check_problem(qng, oracle, W.config_rand12(precision=W.C64), W.C64)
+
+
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+def test_batch_subset_every_instance(qng, oracle, precision):
+    probs = [p for p in W.config_batch(count=24, precision=precision)]
+    ctx = qng.Context(probs, precision=precision)
+    out = ctx.step(ctx.theta0(), 0.1, 1e-3)
+    ctx.sync()
+    gs, grads, dths = ctx.split_metric(out["g"]), ctx.split_params(out["grad"]), ctx.split_params(out["dtheta"])
+    for b, p in enumerate(probs):
+        ref = oracle.qng_step(p)
+        t = TOL[precision]
+        assert rel(gs[b].cpu(), ref["g"]) <= t, (b, p.name)
+        assert rel(grads[b].cpu(), ref["grad"]) <= t, (b, p.name)
+        assert rel(dths[b].cpu(), ref["dtheta"]) <= t, (b, p.name)
+        assert rel(out["energy"][b:b + 1].cpu(), [ref["E"]]) <= t, (b, p.name)
+
+
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+def test_batch256_sampled_instances(qng, oracle, precision):
+    """The full 256-instance batch in one launch per group; 12 instances checked against the oracle."""
+    probs = W.config_batch(precision=precision)
+    ctx = qng.Context(probs, precision=precision)
+    out = ctx.step(ctx.theta0(), 0.1, 1e-3)
+    ctx.sync()
+    gs, grads, dths = ctx.split_metric(out["g"]), ctx.split_params(out["grad"]), ctx.split_params(out["dtheta"])
+    rng = np.random.default_rng(5)
+    pick = sorted(set(rng.choice(len(probs), 10, replace=False).tolist())
+                  | {int(np.argmax([p.n * 1000 + p.P for p in probs])), int(np.argmin([p.P for p in probs]))})
+    t = TOL[precision]
+    for b in pick:
+        p = probs[b]
+        ref = oracle.qng_step(p)
+        assert rel(gs[b].cpu(), ref["g"]) <= t, (b, p.name)
+        assert rel(grads[b].cpu(), ref["grad"]) <= t, (b, p.name)
+        assert rel(dths[b].cpu(), ref["dtheta"]) <= t, (b, p.name)
+
+
+def test_energy_autograd_backward(qng, oracle):
+    p = W.random_problem(9, 80, 15, 1234, W.C128)
+    ctx = qng.Context(p)
+    theta = ctx.theta0().requires_grad_(True)
+    E = qng.energy(theta, ctx)
+    (3.0 * E.sum()).backward()
+    grad_ref, E_ref = oracle.gradient(p.circuit, p.hamiltonian, p.theta)
+    assert rel(E.detach().cpu(), [E_ref]) <= 1e-10
+    assert rel(theta.grad.cpu() / 3.0, grad_ref) <= 1e-10
+
+
+def test_gradient_vs_parameter_shift_on_gpu(qng):
+    """d<E>/d theta from the reverse sweep equals the parameter-shift rule on GPU energies."""
+    p = W.random_problem(7, 40, 10, 4321, W.C128)
+    ctx = qng.Context(p)
+    th = ctx.theta0()
+    grad, _ = ctx.gradient(th)
+    shifts = []
+    for k in range(p.P):
+        tp, tm = th.clone(), th.clone()
+        tp[k] += np.pi / 2
+        tm[k] -= np.pi / 2
+        shifts.append(0.5 * (ctx.energy(tp) - ctx.energy(tm)).item())
+    assert rel(grad.cpu(), shifts) <= 1e-10
+
+
+def test_edge_cases(qng, oracle):
+    # only fixed gates: P = 0, energy only
+    c = W.Circuit(3, np.array([[W.H, 0, -1, -1], [W.CNOT, 0, 1, -1], [W.X, 2, -1, -1]], dtype=np.int32))
+    ham = W.tfim_chain(3, 1.0, 0.5)
+    p = W.Problem("fixed_only", c, ham, np.zeros(0))
+    ctx = qng.Context(p)
+    E = ctx.energy(torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert rel(E.cpu(), [oracle.energy(c, ham, np.zeros(0))]) <= 1e-12
+    # one qubit, one parameter
+    c = W.Circuit(1, np.array([[W.RY, 0, -1, 0]], dtype=np.int32))
+    p = W.Problem("one", c, W.hamiltonian_from_terms([(0.7, {0: "Z"}), (0.3, {0: "X"})]), np.array([0.9]))
+    check_problem(qng, oracle, p, W.C128)
+    # trailing fixed gates with H (W is part of psi and of <E>) and leading fixed gates
+    base = W.config_tfim4()
+    extra = np.array([[W.H, 0, -1, -1], [W.CNOT, 0, 3, -1], [W.Y, 2, -1, -1]], dtype=np.int32)
+    lead = np.array([[W.H, 1, -1, -1], [W.CZ, 1, 2, -1]], dtype=np.int32)
+    c2 = W.Circuit(4, np.concatenate([lead, base.circuit.gates, extra]))
+    check_problem(qng, oracle, W.Problem("lead_trail", c2, base.hamiltonian, base.theta), W.C128)
+
+
+def test_not_spd_reported(qng):
+    """lambda = 0 with a singular metric (Rz first on |0> gives g_00 = 0) reports QNG_ERR_NOT_SPD."""
+    c = W.Circuit(2, np.array([[W.RZ, 0, -1, 0], [W.RY, 1, -1, 1]], dtype=np.int32))
+    p = W.Problem("singular", c, W.tfim_chain(2), np.array([0.3, 0.4]))
+    ctx = qng.Context(p)
+    ctx.step(ctx.theta0(), 0.1, 0.0)
+    with pytest.raises(qng.QngError) as e:
+        ctx.sync()
+    assert e.value.status == qng.QNG_ERR_NOT_SPD
+    ctx.sync()  # the status word is cleared after being reported
+    ctx.step(ctx.theta0(), 0.1, 1e-3)
+    ctx.sync()
+
+
+def test_nonfinite_theta_reported(qng):
+    p = W.config_tfim4()
+    ctx = qng.Context(p)
+    th = ctx.theta0()
+    th[3] = float("nan")
+    ctx.metric(th)
+    with pytest.raises(qng.QngError) as e:
+        ctx.sync()
+    assert e.value.status == qng.QNG_ERR_ARG
+
+
+def test_step_host_matches_device(qng, oracle):
+    p = W.config_rand12()
+    ctx = qng.Context(p)
+    dev = ctx.step(ctx.theta0(), p.dt, p.lam)
+    ctx.sync()
+    host = ctx.step_host(p.theta, p.dt, p.lam)
+    np.testing.assert_array_equal(host["dtheta"], dev["dtheta"].cpu().numpy())
+    np.testing.assert_array_equal(host["g"], dev["g"].cpu().numpy())
+
+
+def test_deterministic(qng):
+    p = W.config_rand12()
+    ctx = qng.Context(p)
+    a = ctx.step(ctx.theta0(), p.dt, p.lam)
+    a = {k: v.clone() for k, v in a.items()}
+    b = ctx.step(ctx.theta0(), p.dt, p.lam)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k

@@ -155,9 +155,17 @@ qng_status qng_step_host(qng_ctx *ctx, const double *theta_host, double dt, doub
 qng_status qng_sync(qng_ctx *ctx);
 
 /* Launch-shape controls (used by the autotuner; 0 leaves a value on automatic):
- * cluster_log2 = log2 of CTAs per state (0..4), threads = CTA size (64..1024, a multiple of 32).
+ * cluster_log2 = log2 of CTAs per state (0..3), threads = CTA size (64..1024, a multiple of 32).
  * For batched contexts the settings apply to the instances with n_qubits >= min_qubits. */
 qng_status qng_set_tuning(qng_ctx *ctx, int min_qubits, int cluster_log2, int threads);
+
+/* Kernel timing with CUDA events recorded on the context's stream around every launch.
+ * qng_profile(ctx, 1) starts recording, qng_profile(ctx, 0) stops. qng_profile_read waits for the
+ * stream, then returns per kernel class (0 coefficients, 1 checkpoints/forward, 2 recurrence
+ * columns, 3 assembly and solve) the summed milliseconds and the launch counts since the last read. */
+#define QNG_KERNEL_CLASSES 4
+qng_status qng_profile(qng_ctx *ctx, int enable);
+qng_status qng_profile_read(qng_ctx *ctx, double *ms, int64_t *launches);
 
 /* Number of kernel launches the last compute call issued (for accounting). */
 qng_status qng_last_launch_count(const qng_ctx *ctx, int64_t *launches);

@@ -82,6 +82,24 @@ struct qng_ctx {
     // tuning
     int tune_min_qubits = 0, tune_cl = -1, tune_threads = 0;
     int64_t last_launches = 0;
+    // kernel timing (qng_profile)
+    bool profiling = false;
+    struct Mark { int cls; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> spare;
+    double prof_ms[QNG_KERNEL_CLASSES] = {0, 0, 0, 0};
+    int64_t prof_n[QNG_KERNEL_CLASSES] = {0, 0, 0, 0};
+
+    ~qng_ctx() {
+        for (auto &m : marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+        for (auto e : spare) cudaEventDestroy(e);
+    }
+    cudaEvent_t take_event() {
+        if (!spare.empty()) { cudaEvent_t e = spare.back(); spare.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
 
     Work work() const {
         Work w;
@@ -319,32 +337,53 @@ qng_status upload(qng_ctx *c) {
     return QNG_OK;
 }
 
+// Record events around a launch when profiling (class cls), then launch.
+template <class F> cudaError_t timed(qng_ctx *c, int cls, F &&launch) {
+    if (!c->profiling) return launch();
+    cudaEvent_t a = c->take_event(), b = c->take_event();
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(a, c->stream);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+    if (e != cudaSuccess) { c->spare.push_back(a); c->spare.push_back(b); return e; }
+    c->marks.push_back({cls, a, b});
+    return cudaSuccess;
+}
+
 qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
     if (!c) return QNG_ERR_ARG;
     if (!c->ws || !c->prepared) return QNG_ERR_WORKSPACE;
     if (!args.theta && c->total_params > 0) return QNG_ERR_ARG;
     const Work w = c->work();
     int64_t launches = 0;
-    cudaError_t e = launch_coef(w, args.theta, c->total_params, c->stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    launches += c->total_params > 0;
+    cudaError_t e = cudaSuccess;
+    if (c->total_params > 0) {
+        e = timed(c, 0, [&] { return launch_coef(w, args.theta, c->total_params, c->stream); });
+        if (e != cudaSuccess) return cuda_status(e);
+        launches += 1;
+    }
     const bool need_cols = jobs & (kJobMetric | kJobGradient | kJobSolve);
     const bool want_eta = jobs & (kJobGradient | kJobSolve);
     for (const Group &g : c->groups) {
-        if ((e = launch_forward(w, g, c->precision, want_eta, c->stream)) != cudaSuccess) return cuda_status(e);
-        launches += g.num_inst > 0;
+        if (g.num_inst == 0) continue;
+        e = timed(c, 1, [&] { return launch_forward(w, g, c->precision, want_eta, c->stream); });
+        if (e != cudaSuccess) return cuda_status(e);
+        launches += 1;
     }
     if (need_cols) {
         const int wm = (jobs & (kJobMetric | kJobSolve)) ? 1 : 0;
         const int wg = (jobs & (kJobGradient | kJobSolve)) ? 1 : 0;
         for (const Group &g : c->groups) {
-            if ((e = launch_columns(w, g, c->precision, wm, wg, c->stream)) != cudaSuccess) return cuda_status(e);
-            launches += (wm && wg ? g.num_work : (wm ? g.num_met : g.num_grad)) > 0;
+            if ((wm && wg ? g.num_work : (wm ? g.num_met : g.num_grad)) == 0) continue;
+            e = timed(c, 2, [&] { return launch_columns(w, g, c->precision, wm, wg, c->stream); });
+            if (e != cudaSuccess) return cuda_status(e);
+            launches += 1;
         }
     }
     LaunchArgs a = args;
     a.jobs = jobs;
-    if ((e = launch_finish(w, c->count, c->max_P, a, c->stream)) != cudaSuccess) return cuda_status(e);
+    e = timed(c, 3, [&] { return launch_finish(w, c->count, c->max_P, a, c->stream); });
+    if (e != cudaSuccess) return cuda_status(e);
     launches += 1;
     c->last_launches = launches;
     return QNG_OK;
@@ -537,6 +576,34 @@ qng_status qng_sync(qng_ctx *c) {
         if ((e = cudaMemsetAsync(c->ws + c->o_status, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return cuda_status(e);
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_status(e);
         return static_cast<qng_status>(st);
+    }
+    return QNG_OK;
+}
+
+qng_status qng_profile(qng_ctx *c, int enable) {
+    if (!c) return QNG_ERR_ARG;
+    c->profiling = enable != 0;
+    return QNG_OK;
+}
+
+qng_status qng_profile_read(qng_ctx *c, double *ms, int64_t *launches) {
+    if (!c) return QNG_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (auto &m : c->marks) {
+        float t = 0.f;
+        if ((e = cudaEventElapsedTime(&t, m.a, m.b)) != cudaSuccess) return cuda_status(e);
+        c->prof_ms[m.cls] += t;
+        c->prof_n[m.cls] += 1;
+        c->spare.push_back(m.a);
+        c->spare.push_back(m.b);
+    }
+    c->marks.clear();
+    for (int k = 0; k < QNG_KERNEL_CLASSES; ++k) {
+        if (ms) ms[k] = c->prof_ms[k];
+        if (launches) launches[k] = c->prof_n[k];
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
     }
     return QNG_OK;
 }

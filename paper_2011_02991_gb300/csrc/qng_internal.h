@@ -14,7 +14,7 @@ namespace qng {
 
 constexpr int kMaxQubits = 30;         // any single instance
 constexpr int kMaxQubitsSmall = 16;    // instances run by the on-chip (cluster-resident) path
-constexpr int kMaxClusterLog2 = 4;     // 16 CTAs per cluster (non-portable size, opt-in)
+constexpr int kMaxClusterLog2 = 3;     // 8 CTAs per cluster (the portable maximum)
 constexpr int kAxisX = 0, kAxisY = 1, kAxisZ = 2;
 
 // One parametric gate k of an instance: U_k = R_k F_k with R_k = exp(-i theta_k sigma / 2).

@@ -62,6 +62,8 @@ SYMBOLS = {
     "qng_sync": [_vp],
     "qng_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "qng_last_launch_count": [_vp, _i64p],
+    "qng_profile": [_vp, ctypes.c_int],
+    "qng_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), _i64p],
     "qng_destroy": [_vp],
     "qng_status_string": [ctypes.c_int],
 }
@@ -243,6 +245,18 @@ class Context:
 
     def set_tuning(self, min_qubits: int, cluster_log2: int, threads: int):
         _chk(load().qng_set_tuning(self._h, min_qubits, cluster_log2, threads), "qng_set_tuning")
+
+    KERNEL_CLASSES = ("coef", "forward", "columns", "finish")
+
+    def profile(self, enable: bool):
+        _chk(load().qng_profile(self._h, int(bool(enable))), "qng_profile")
+
+    def profile_read(self) -> dict:
+        """Per kernel class: (milliseconds, launches) since the last read; waits for the stream."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        _chk(load().qng_profile_read(self._h, ms, n), "qng_profile_read")
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
 
     def last_launch_count(self) -> int:
         v = ctypes.c_int64()

@@ -170,6 +170,25 @@ qng_status qng_profile_read(qng_ctx *ctx, double *ms, int64_t *launches);
 /* Number of kernel launches the last compute call issued (for accounting). */
 qng_status qng_last_launch_count(const qng_ctx *ctx, int64_t *launches);
 
+/* Metric without any allocation, for callers that cannot allocate device memory: programs whose
+ * GPU memory is owned by a host application's own pool (plugins, embedded solvers) or that must
+ * not pay cudaMalloc's implicit synchronisation, and callers that cannot keep a workspace alive
+ * between calls. The paper has no counterpart; this is a packaging of qng_metric.
+ *   Inputs and outputs are as in qng_metric for ONE instance (n_qubits <= 16, at most 1024 gates
+ *   and 320 parameters): theta (device, P float64), g (device, P*P float64), stream (cudaStream_t
+ *   or NULL). Every other buffer lives in one static device array of QNG_NOALLOC_SCRATCH_BYTES
+ *   bytes that each GPU loading the library holds until the process exits.
+ *   Returns QNG_ERR_WORKSPACE when the instance needs more than that array (for example 12 qubits
+ *   at complex128 fit with P <= 240), QNG_ERR_ARG for an invalid circuit, QNG_ERR_CUDA for a
+ *   failed CUDA call. Device-side conditions (a non-finite theta) are not reported.
+ *   All calls on a device share the array, which keeps the last call's contents: calls whose work
+ *   overlaps on the GPU race and must be ordered by the caller. The first call on each device
+ *   looks up the array's address (with that device current); make it before any stream capture.
+ *   No cudaMalloc, cudaFree or other allocating routine is called. */
+#define QNG_NOALLOC_SCRATCH_BYTES (16u << 20)
+qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, int n_gates, int precision, const double *theta,
+                              double *g, void *stream);
+
 void qng_destroy(qng_ctx *ctx);
 
 const char *qng_status_string(qng_status s);

@@ -350,6 +350,14 @@ template <class F> cudaError_t timed(qng_ctx *c, int cls, F &&launch) {
     return cudaSuccess;
 }
 
+// cluster size of the distributed solve (-1: the single-CTA finish kernel is used)
+int solve_cluster_log2(int max_P) {
+    if (max_P < 48) return -1;
+    for (int cl = 3; cl >= 0; --cl)
+        if (solve_smem_bytes(max_P, cl) <= 200 * 1024) return cl;
+    return -1;
+}
+
 qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
     if (!c) return QNG_ERR_ARG;
     if (!c->ws || !c->prepared) return QNG_ERR_WORKSPACE;
@@ -382,7 +390,11 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
     }
     LaunchArgs a = args;
     a.jobs = jobs;
-    e = timed(c, 3, [&] { return launch_finish(w, c->count, c->max_P, a, c->stream); });
+    const int scl = solve_cluster_log2(c->max_P);
+    if ((jobs & kJobSolve) && scl >= 0)
+        e = timed(c, 3, [&] { return launch_solve(w, c->count, c->max_P, scl, a, c->stream); });
+    else
+        e = timed(c, 3, [&] { return launch_finish(w, c->count, c->max_P, a, c->stream); });
     if (e != cudaSuccess) return cuda_status(e);
     launches += 1;
     c->last_launches = launches;

@@ -144,6 +144,8 @@ cudaError_t launch_forward(const Work &w, const Group &g, int precision, int wan
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
                            cudaStream_t st);
 cudaError_t launch_finish(const Work &w, int count, int max_P, const LaunchArgs &a, cudaStream_t st);
+cudaError_t launch_solve(const Work &w, int count, int max_P, int cl, const LaunchArgs &a, cudaStream_t st);
+size_t solve_smem_bytes(int P, int cl);
 cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col);
 
 }  // namespace qng

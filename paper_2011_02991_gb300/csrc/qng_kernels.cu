@@ -253,6 +253,207 @@ __device__ double cluster_sum(double v, double *red, int cl) {
     return tot;
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Compile-time Pauli axis and bit value: every sign below folds into an FMA operand or is a
+// sign-bit flip on the integer pipe, so a pair costs only its essential float64 FMAs.
+__device__ __forceinline__ double flip(double v, int p) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(p & 1) << 63));
+}
+__device__ __forceinline__ float flip(float v, int p) { return __int_as_float(__float_as_int(v) ^ ((p & 1) << 31)); }
+template <typename T2> __device__ __forceinline__ T2 flip2(T2 v, int p) {
+    v.x = flip(v.x, p);
+    v.y = flip(v.y, p);
+    return v;
+}
+
+// (i sigma x)_BETA and (sigma x)_BETA from own value xm and partner value xo
+template <int AX, int BETA, typename T2> __device__ __forceinline__ T2 isig(T2 xm, T2 xo) {
+    if constexpr (AX == kAxisX) return T2{-xo.y, xo.x};
+    else if constexpr (AX == kAxisY) return BETA ? T2{-xo.x, -xo.y} : xo;
+    else return BETA ? T2{xm.y, -xm.x} : T2{-xm.y, xm.x};
+}
+template <int AX, int BETA, typename T2> __device__ __forceinline__ T2 sig(T2 xm, T2 xo) {
+    if constexpr (AX == kAxisX) return xo;
+    else if constexpr (AX == kAxisY) return BETA ? T2{-xo.y, xo.x} : T2{xo.y, -xo.x};
+    else return BETA ? T2{-xm.x, -xm.y} : xm;
+}
+// part += Re(conj(a) s) (IM = 0) or Im(conj(a) s) (IM = 1)
+template <int IM, typename RA, typename T2> __device__ __forceinline__ RA ipacc(RA part, T2 a, T2 s) {
+    if constexpr (IM) return fma(a.x, s.y, fma(-a.y, s.x, part));
+    else return fma(a.x, s.x, fma(a.y, s.y, part));
+}
+
+// One fused step of a column on a local X/Y qubit: inner product with sigma on the pairs,
+// then the adjoint rotation R^dag on the same pairs, then the diagonal fixed block F^dag.
+template <typename R, int AX, int IM>
+__device__ __forceinline__ R col_pairs(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on, const Rot<R> &rot,
+                                       bool post, const DevParam &pi, const DevDiag *dt) {
+    using cx = typename CX<R>::T;
+    R part = 0;
+    const uint32_t bit = 1u << q, half = e.Nl >> 1;
+    for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+        const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
+        const cx x0 = e.buf[l0], x1 = e.buf[l1];
+        const cx a0 = a[e.base | l0], a1 = a[e.base | l1];
+        part = ipacc<IM>(part, a0, sig<AX, 0>(x0, x1));
+        part = ipacc<IM>(part, a1, sig<AX, 1>(x1, x0));
+        if (rot_on) {
+            cx y0 = rot.apply(x0, isig<AX, 0>(x0, x1));
+            cx y1 = rot.apply(x1, isig<AX, 1>(x1, x0));
+            if (post) {
+                y0 = flip2(y0, diag_parity(e.base | l0, pi, dt));
+                y1 = flip2(y1, diag_parity(e.base | l1, pi, dt));
+            }
+            e.buf[l0] = y0;
+            e.buf[l1] = y1;
+        }
+    }
+    return part;
+}
+
+// The same step on a distributed X/Y qubit, this CTA holding the BETA half of every pair.
+template <typename R, int AX, int IM, int BETA>
+__device__ __forceinline__ R col_dist(Eng<R> &e, const typename CX<R>::T *rv, const typename CX<R>::T *a, bool rot_on,
+                                      const Rot<R> &rot, bool post, const DevParam &pi, const DevDiag *dt) {
+    using cx = typename CX<R>::T;
+    R part = 0;
+    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+        const uint64_t kk = e.base | l;
+        const cx xm = e.buf[l], xo = rv[l];
+        part = ipacc<IM>(part, a[kk], sig<AX, BETA>(xm, xo));
+        if (rot_on) {
+            cx y = rot.apply(xm, isig<AX, BETA>(xm, xo));
+            if (post) y = flip2(y, diag_parity(kk, pi, dt));
+            e.buf[l] = y;
+        }
+    }
+    return part;
+}
+
+// The same step for a Z rotation (diagonal: any qubit, no pairing).
+template <typename R, int IM>
+__device__ __forceinline__ R col_diag(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on, const Rot<R> &rot,
+                                      bool post, const DevParam &pi, const DevDiag *dt) {
+    using cx = typename CX<R>::T;
+    R part = 0;
+    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+        const uint64_t kk = e.base | l;
+        const int beta = (int)((kk >> q) & 1);
+        const cx x = e.buf[l];
+        part = ipacc<IM>(part, flip2(a[kk], beta), x);  // (Z x)_beta = (-1)^beta x
+        if (rot_on) {
+            const cx v = {flip(x.y, beta ^ 1), flip(x.x, beta)};  // (i Z x)_beta
+            cx y = rot.apply(x, v);
+            if (post) y = flip2(y, diag_parity(kk, pi, dt));
+            e.buf[l] = y;
+        }
+    }
+    return part;
+}
+
+template <typename R, int IM>
+__device__ __forceinline__ R col_step(Eng<R> &e, const typename CX<R>::T *a, const DevParam &pi, bool rot_on,
+                                      const Rot<R> &rot, bool post, const DevDiag *dt) {
+    R part;
+    if (pi.axis == kAxisZ) {
+        part = col_diag<R, IM>(e, a, pi.q, rot_on, rot, post, pi, dt);
+    } else if (pi.q < e.nl) {
+        part = (pi.axis == kAxisX) ? col_pairs<R, kAxisX, IM>(e, a, pi.q, rot_on, rot, post, pi, dt)
+                                   : col_pairs<R, kAxisY, IM>(e, a, pi.q, rot_on, rot, post, pi, dt);
+    } else {
+        const typename CX<R>::T *rv = e.exchange(pi.q);
+        const int beta = (e.rank >> (pi.q - e.nl)) & 1;
+        if (pi.axis == kAxisX)
+            part = beta ? col_dist<R, kAxisX, IM, 1>(e, rv, a, rot_on, rot, post, pi, dt)
+                        : col_dist<R, kAxisX, IM, 0>(e, rv, a, rot_on, rot, post, pi, dt);
+        else
+            part = beta ? col_dist<R, kAxisY, IM, 1>(e, rv, a, rot_on, rot, post, pi, dt)
+                        : col_dist<R, kAxisY, IM, 0>(e, rv, a, rot_on, rot, post, pi, dt);
+    }
+    __syncthreads();
+    return part;
+}
+
+// Forward rotation R_k with the diagonal fixed block F_k applied to the inputs (pre), writing
+// both the shared-memory state and the checkpoint out.
+template <typename R, int AX>
+__device__ __forceinline__ void fwd_pairs(Eng<R> &e, typename CX<R>::T *out, int q, const Rot<R> &rot, bool pre,
+                                          const DevParam &pk, const DevDiag *dt) {
+    using cx = typename CX<R>::T;
+    const uint32_t bit = 1u << q, half = e.Nl >> 1;
+    for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+        const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
+        cx x0 = e.buf[l0], x1 = e.buf[l1];
+        if (pre) {
+            x0 = flip2(x0, diag_parity(e.base | l0, pk, dt));
+            x1 = flip2(x1, diag_parity(e.base | l1, pk, dt));
+        }
+        const cx y0 = rot.apply(x0, isig<AX, 0>(x0, x1));
+        const cx y1 = rot.apply(x1, isig<AX, 1>(x1, x0));
+        e.buf[l0] = y0;
+        e.buf[l1] = y1;
+        out[e.base | l0] = y0;
+        out[e.base | l1] = y1;
+    }
+}
+
+template <typename R, int AX, int BETA>
+__device__ __forceinline__ void fwd_dist(Eng<R> &e, const typename CX<R>::T *rv, typename CX<R>::T *out, int q,
+                                         const Rot<R> &rot, bool pre, const DevParam &pk, const DevDiag *dt) {
+    using cx = typename CX<R>::T;
+    const uint64_t m = 1ull << q;
+    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+        const uint64_t kk = e.base | l;
+        cx xm = e.buf[l], xo = rv[l];
+        if (pre) {
+            xm = flip2(xm, diag_parity(kk, pk, dt));
+            xo = flip2(xo, diag_parity(kk ^ m, pk, dt));
+        }
+        const cx y = rot.apply(xm, isig<AX, BETA>(xm, xo));
+        e.buf[l] = y;
+        out[kk] = y;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void fwd_diag(Eng<R> &e, typename CX<R>::T *out, int q, const Rot<R> &rot, bool pre,
+                                         const DevParam &pk, const DevDiag *dt) {
+    using cx = typename CX<R>::T;
+    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+        const uint64_t kk = e.base | l;
+        cx x = e.buf[l];
+        if (pre) x = flip2(x, diag_parity(kk, pk, dt));
+        const int beta = (int)((kk >> q) & 1);
+        const cx v = {flip(x.y, beta ^ 1), flip(x.x, beta)};
+        const cx y = rot.apply(x, v);
+        e.buf[l] = y;
+        out[kk] = y;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void fwd_step(Eng<R> &e, typename CX<R>::T *out, const DevParam &pk, const Rot<R> &rot,
+                                         bool pre, const DevDiag *dt) {
+    if (pk.axis == kAxisZ) {
+        fwd_diag<R>(e, out, pk.q, rot, pre, pk, dt);
+    } else if (pk.q < e.nl) {
+        if (pk.axis == kAxisX) fwd_pairs<R, kAxisX>(e, out, pk.q, rot, pre, pk, dt);
+        else fwd_pairs<R, kAxisY>(e, out, pk.q, rot, pre, pk, dt);
+    } else {
+        const typename CX<R>::T *rv = e.exchange(pk.q);
+        const int beta = (e.rank >> (pk.q - e.nl)) & 1;
+        if (pk.axis == kAxisX) {
+            if (beta) fwd_dist<R, kAxisX, 1>(e, rv, out, pk.q, rot, pre, pk, dt);
+            else fwd_dist<R, kAxisX, 0>(e, rv, out, pk.q, rot, pre, pk, dt);
+        } else {
+            if (beta) fwd_dist<R, kAxisY, 1>(e, rv, out, pk.q, rot, pre, pk, dt);
+            else fwd_dist<R, kAxisY, 0>(e, rv, out, pk.q, rot, pre, pk, dt);
+        }
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------------------------------
 __global__ void k_coef(const double *theta, DevCoef *coef, int64_t total, int32_t *status) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,50 +502,7 @@ __global__ void __launch_bounds__(1024) k_forward(Work w, int group_first, int c
         double fs;
         const Rot<R> rot = make_rot<R>(w.coef[in.param_off + k], false, fs);
         cx *out = ckpt + (uint64_t)(k + 1) * N;
-        const int q = pk.q, axis = pk.axis;
-        if (axis == kAxisZ) {
-            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
-                const uint64_t kk = e.base | l;
-                cx x = e.buf[l];
-                if (pre) x = neg_if(x, diag_parity(kk, pk, w.diag));
-                const int beta = (int)((kk >> q) & 1);
-                const cx y = rot.apply(x, i_sigma(axis, beta, x, x));
-                e.buf[l] = y;
-                out[kk] = y;
-            }
-            __syncthreads();
-        } else if (q < e.nl) {
-            const uint32_t bit = 1u << q, half = e.Nl >> 1;
-            for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
-                const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
-                cx x0 = e.buf[l0], x1 = e.buf[l1];
-                if (pre) {
-                    x0 = neg_if(x0, diag_parity(e.base | l0, pk, w.diag));
-                    x1 = neg_if(x1, diag_parity(e.base | l1, pk, w.diag));
-                }
-                const cx y0 = rot.apply(x0, i_sigma(axis, 0, x0, x1));
-                const cx y1 = rot.apply(x1, i_sigma(axis, 1, x1, x0));
-                e.buf[l0] = y0; e.buf[l1] = y1;
-                out[e.base | l0] = y0; out[e.base | l1] = y1;
-            }
-            __syncthreads();
-        } else {
-            const cx *rv = e.exchange(q);
-            const int beta = (e.rank >> (q - e.nl)) & 1;
-            const uint64_t m = 1ull << q;
-            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
-                const uint64_t kk = e.base | l;
-                cx xm = e.buf[l], xo = rv[l];
-                if (pre) {
-                    xm = neg_if(xm, diag_parity(kk, pk, w.diag));
-                    xo = neg_if(xo, diag_parity(kk ^ m, pk, w.diag));
-                }
-                const cx y = rot.apply(xm, i_sigma(axis, beta, xm, xo));
-                e.buf[l] = y;
-                out[kk] = y;
-            }
-            __syncthreads();
-        }
+        fwd_step<R>(e, out, pk, rot, pre, w.diag);
         if (std::is_same<R, double>::value) scale *= fs;
         e.maybe_renorm(scale);
         if (e.rank == 0 && threadIdx.x == 0) scales[k + 1] = scale;
@@ -494,60 +652,8 @@ __global__ void __launch_bounds__(1024) k_columns(Work w, int work_first, int cl
         double fs = 1.0;
         const Rot<R> rot = make_rot<R>(w.coef[in.param_off + i], true, fs);
         const bool post = rot_on && (pi.diag_count > 0 || pi.zmask != 0);
-        const int q = pi.q, axis = pi.axis;
-        RA part = 0;
-        if (axis == kAxisZ) {
-            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
-                const uint64_t kk = e.base | l;
-                const int beta = (int)((kk >> q) & 1);
-                const cx x = e.buf[l];
-                const cx av = a[kk];
-                const cx sb = sigma_of(axis, beta, x, x);
-                part += want_im ? (av.x * sb.y - av.y * sb.x) : (av.x * sb.x + av.y * sb.y);
-                if (rot_on) {
-                    cx y = rot.apply(x, i_sigma(axis, beta, x, x));
-                    if (post) y = neg_if(y, diag_parity(kk, pi, w.diag));
-                    e.buf[l] = y;
-                }
-            }
-            __syncthreads();
-        } else if (q < e.nl) {
-            const uint32_t bit = 1u << q, half = e.Nl >> 1;
-            for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
-                const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
-                const cx x0 = e.buf[l0], x1 = e.buf[l1];
-                const cx a0 = a[e.base | l0], a1 = a[e.base | l1];
-                const cx s0 = sigma_of(axis, 0, x0, x1), s1 = sigma_of(axis, 1, x1, x0);
-                if (want_im) part += (a0.x * s0.y - a0.y * s0.x) + (a1.x * s1.y - a1.y * s1.x);
-                else         part += (a0.x * s0.x + a0.y * s0.y) + (a1.x * s1.x + a1.y * s1.y);
-                if (rot_on) {
-                    cx y0 = rot.apply(x0, i_sigma(axis, 0, x0, x1));
-                    cx y1 = rot.apply(x1, i_sigma(axis, 1, x1, x0));
-                    if (post) {
-                        y0 = neg_if(y0, diag_parity(e.base | l0, pi, w.diag));
-                        y1 = neg_if(y1, diag_parity(e.base | l1, pi, w.diag));
-                    }
-                    e.buf[l0] = y0; e.buf[l1] = y1;
-                }
-            }
-            __syncthreads();
-        } else {
-            const cx *rv = e.exchange(q);
-            const int beta = (e.rank >> (q - e.nl)) & 1;
-            for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
-                const uint64_t kk = e.base | l;
-                const cx xm = e.buf[l], xo = rv[l];
-                const cx av = a[kk];
-                const cx sb = sigma_of(axis, beta, xm, xo);
-                part += want_im ? (av.x * sb.y - av.y * sb.x) : (av.x * sb.x + av.y * sb.y);
-                if (rot_on) {
-                    cx y = rot.apply(xm, i_sigma(axis, beta, xm, xo));
-                    if (post) y = neg_if(y, diag_parity(kk, pi, w.diag));
-                    e.buf[l] = y;
-                }
-            }
-            __syncthreads();
-        }
+        const RA part = want_im ? col_step<R, 1>(e, a, pi, rot_on, rot, post, w.diag)
+                                : col_step<R, 0>(e, a, pi, rot_on, rot, post, w.diag);
         if (rot_on) {
             if (std::is_same<R, double>::value) scale_b *= fs;
             if (pi.diag_count < 0)
@@ -662,6 +768,216 @@ __global__ void __launch_bounds__(512) k_finish(Work w, LaunchArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
+// k_solve: one cluster of 2^cl CTAs per instance. Assembly of g (Eq. g_t_L_def), then the float64
+// Cholesky factorisation of A = g + lambda I and the solve of A dtheta = -dt grad (Eq. 3), with the
+// rows of A spread over the cluster (row i lives in CTA i mod C) in shared memory.
+// Blocked right-looking factorisation, block width kNb: every CTA factors the kNb x kNb diagonal
+// block itself (fetched through distributed shared memory), computes the panel entries of its own
+// rows, then updates its own trailing rows with the panel gathered from all CTAs. The forward
+// substitution L y = b rides along block by block; the back substitution L^T x = y runs block by
+// block from the end with one cluster reduction per block. Three cluster barriers per block.
+constexpr int kNb = 16;
+
+struct SolveSmem {
+    double *A;      // [R][P] own rows
+    double *PLt;    // [kNb][P] panel of the current block, transposed (column c, row j)
+    double *D;      // [kNb][kNb] diagonal block, factored in place
+    double *ys;     // [P] y (forward substitution), then x
+    double *part;   // [2][kNb] per-CTA partial sums of the back substitution
+    double *b;      // [R] own entries of the right-hand side
+    double *invd;   // [kNb] reciprocals of the diagonal block's pivots
+    int *flag;
+};
+
+__device__ __forceinline__ SolveSmem solve_smem(unsigned char *smem, int R, int P) {
+    SolveSmem s;
+    s.A = reinterpret_cast<double *>(smem);
+    s.PLt = s.A + (size_t)R * P;
+    s.D = s.PLt + (size_t)kNb * P;
+    s.ys = s.D + kNb * kNb;
+    s.part = s.ys + P;
+    s.b = s.part + 2 * kNb;
+    s.invd = s.b + R;
+    s.flag = reinterpret_cast<int *>(s.invd + kNb);
+    return s;
+}
+
+__global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int C = 1 << cl;
+    const int b = blockIdx.x >> cl;
+    const int rank = cl ? (int)cg::this_cluster().block_rank() : 0;
+    const DevInst in = w.inst[b];
+    const int P = in.P;
+    const int R = (P + C - 1) / C;  // rows per CTA (upper bound)
+    SolveSmem sm = solve_smem(smem, R, P);
+    const double *sg = w.sigma + in.param_off;
+    const double *L = w.L + in.metric_off;
+    const double *gr = w.gradraw + in.param_off;
+    auto csync = [&]() { if (cl) cg::this_cluster().sync(); else __syncthreads(); };
+    auto remote = [&](double *p, int r) -> double * { return cl ? cg::this_cluster().map_shared_rank(p, r) : p; };
+
+    // assembly of own rows; g_out, grad_out and energy_out
+    const int nown = (rank < P) ? (P - 1 - rank) / C + 1 : 0;
+    for (int t = threadIdx.x; t < nown * P; t += blockDim.x) {
+        const int il = t / P, j = t % P, i = il * C + rank;
+        double v;
+        if (i == j) v = 0.25 * (1.0 - sg[i] * sg[i]);
+        else if (i < j) v = L[(int64_t)i * P + j] - 0.25 * sg[i] * sg[j];
+        else v = L[(int64_t)j * P + i] - 0.25 * sg[i] * sg[j];
+        if (a.g_out) a.g_out[in.metric_off + (int64_t)i * P + j] = v;
+        sm.A[(size_t)il * P + j] = v + (i == j ? a.lambda : 0.0);
+    }
+    for (int il = threadIdx.x; il < nown; il += blockDim.x) sm.b[il] = -a.dt * gr[il * C + rank];
+    if (rank == 0) {
+        if (a.grad_out)
+            for (int k = threadIdx.x; k < P; k += blockDim.x) a.grad_out[in.param_off + k] = gr[k];
+        if (a.sigma_out)
+            for (int k = threadIdx.x; k < P; k += blockDim.x) a.sigma_out[in.param_off + k] = sg[k];
+        if (a.energy_out && threadIdx.x == 0) a.energy_out[b] = w.energy[b];
+    }
+    if (threadIdx.x == 0) *sm.flag = 0;
+    __syncthreads();
+    csync();
+
+    const int nblk = (P + kNb - 1) / kNb;
+    bool failed = false;
+    for (int kb = 0; kb < nblk && !failed; ++kb) {
+        const int c0 = kb * kNb, nb = min(kNb, P - c0), t0 = c0 + nb;
+        // (1) diagonal block and the matching entries of b, fetched from their owners
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+            const int r = t / nb, c = t % nb, i = c0 + r;
+            sm.D[r * kNb + c] = (c <= r) ? remote(sm.A, i % C)[(size_t)(i / C) * P + c0 + c] : 0.0;
+        }
+        for (int r = threadIdx.x; r < nb; r += blockDim.x) sm.ys[c0 + r] = remote(sm.b, (c0 + r) % C)[(c0 + r) / C];
+        __syncthreads();
+        // (2) factor the diagonal block and solve its part of L y = b (warp 0, lanes in parallel)
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            for (int k = 0; k < nb; ++k) {
+                const double d = sm.D[k * kNb + k];
+                if (!(d > 0.0)) { if (lane == 0) *sm.flag = 1; break; }
+                const double rd = sqrt(d), inv = 1.0 / rd;
+                __syncwarp();
+                for (int r = k + 1 + lane; r < nb; r += 32) sm.D[r * kNb + k] *= inv;
+                if (lane == 0) { sm.D[k * kNb + k] = rd; sm.invd[k] = inv; }
+                __syncwarp();
+                for (int t = lane; t < nb * nb; t += 32) {
+                    const int r = t / nb, c = t % nb;
+                    if (c > k && c <= r) sm.D[r * kNb + c] = fma(-sm.D[r * kNb + k], sm.D[c * kNb + k], sm.D[r * kNb + c]);
+                }
+                __syncwarp();
+            }
+            __syncwarp();
+            if (!*sm.flag) {
+                for (int c = 0; c < nb; ++c) {  // column-oriented forward substitution
+                    if (lane == 0) sm.ys[c0 + c] *= sm.invd[c];
+                    __syncwarp();
+                    const double yc = sm.ys[c0 + c];
+                    for (int r = c + 1 + lane; r < nb; r += 32) sm.ys[c0 + r] = fma(-sm.D[r * kNb + c], yc, sm.ys[c0 + r]);
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+        if (*sm.flag) { failed = true; break; }  // every CTA factors the same block: all stop together
+        // (3) own rows: the diagonal block's rows take L, rows below become panel rows
+        for (int il = threadIdx.x; il < nown; il += blockDim.x) {
+            const int i = il * C + rank;
+            double *row = sm.A + (size_t)il * P;
+            if (i >= c0 && i < t0) {
+                for (int c = 0; c <= i - c0; ++c) row[c0 + c] = sm.D[(i - c0) * kNb + c];
+            } else if (i >= t0) {
+                double bi = sm.b[il];
+                for (int c = 0; c < nb; ++c) {
+                    double v = row[c0 + c];
+                    for (int c2 = 0; c2 < c; ++c2) v = fma(-row[c0 + c2], sm.D[c * kNb + c2], v);
+                    v *= sm.invd[c];
+                    row[c0 + c] = v;
+                    bi = fma(-v, sm.ys[c0 + c], bi);
+                }
+                sm.b[il] = bi;
+            }
+        }
+        __syncthreads();
+        csync();
+        // (4) gather the panel rows j >= t0 from every CTA (transposed into PLt[c][j - t0])
+        const int m = P - t0;
+        for (int t = threadIdx.x; t < m * nb; t += blockDim.x) {
+            const int jj = t / nb, c = t % nb, j = t0 + jj;
+            sm.PLt[(size_t)c * P + jj] = remote(sm.A, j % C)[(size_t)(j / C) * P + c0 + c];
+        }
+        __syncthreads();
+        // (5) trailing update of own rows: A_ij -= sum_c L_ic L_jc for t0 <= j <= i
+        for (int t = threadIdx.x; t < nown * m; t += blockDim.x) {
+            const int il = t / m, jj = t % m, i = il * C + rank, j = t0 + jj;
+            if (i < t0 || j > i) continue;
+            double v = sm.A[(size_t)il * P + j];
+            const int ii = i - t0;
+#pragma unroll 4
+            for (int c = 0; c < nb; ++c) v -= sm.PLt[(size_t)c * P + ii] * sm.PLt[(size_t)c * P + jj];
+            sm.A[(size_t)il * P + j] = v;
+        }
+        __syncthreads();
+        csync();
+    }
+    if (failed) {
+        if (rank == 0 && threadIdx.x == 0) atomicCAS(w.status, 0, (int)QNG_ERR_NOT_SPD);
+        csync();
+        return;
+    }
+    // back substitution L^T x = y, last block first; ys turns into x block by block
+    for (int kb = nblk - 1; kb >= 0; --kb) {
+        const int c0 = kb * kNb, nb = min(kNb, P - c0), t0 = c0 + nb;
+        double *part = sm.part + (kb & 1) * kNb;
+        // partial sums over own rows below the block: sum_i L_{i, c0+c} x_i
+        if (threadIdx.x < 32) {
+            for (int c = 0; c < nb; ++c) {
+                double v = 0.0;
+                for (int il = threadIdx.x; il < nown; il += 32) {
+                    const int i = il * C + rank;
+                    if (i >= t0) v += sm.A[(size_t)il * P + c0 + c] * sm.ys[i];
+                }
+                v = warp_sum(v);
+                if (threadIdx.x == 0) part[c] = v;
+            }
+        }
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {  // the diagonal block of L again
+            const int r = t / nb, c = t % nb, i = c0 + r;
+            sm.D[r * kNb + c] = (c <= r) ? remote(sm.A, i % C)[(size_t)(i / C) * P + c0 + c] : 0.0;
+        }
+        __syncthreads();
+        csync();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            if (lane < nb) {
+                double sacc = 0.0;
+                for (int r = 0; r < C; ++r) sacc += remote(part, r)[lane];
+                sm.ys[c0 + lane] -= sacc;
+                sm.invd[lane] = 1.0 / sm.D[lane * kNb + lane];
+            }
+            __syncwarp();
+            for (int c = nb - 1; c >= 0; --c) {  // column-oriented back substitution with L_d^T
+                if (lane == 0) sm.ys[c0 + c] *= sm.invd[c];
+                __syncwarp();
+                const double xc = sm.ys[c0 + c];
+                if (lane < c) sm.ys[c0 + lane] = fma(-sm.D[c * kNb + lane], xc, sm.ys[c0 + lane]);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+    if (rank == 0)
+        for (int k = threadIdx.x; k < P; k += blockDim.x) a.dtheta_out[in.param_off + k] = sm.ys[k];
+    csync();  // keep every CTA's shared memory alive until all remote reads are done
+}
+
+size_t solve_smem_bytes(int P, int cl) {
+    const int C = 1 << cl, R = (P + C - 1) / C;
+    return sizeof(double) * ((size_t)R * P + (size_t)kNb * P + kNb * kNb + P + 2 * kNb + R + kNb) + 16;
+}
+
+// ------------------------------------------------------------------------------------------
 // launchers
 template <typename K>
 static cudaError_t launch_cluster(K kern, int grid, int threads, size_t smem, int cl, cudaStream_t st,
@@ -726,6 +1042,27 @@ cudaError_t launch_columns(const Work &w, const Group &g, int precision, int wit
     if (precision == QNG_C128)
         return launch_cluster(k_columns<double>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P);
     return launch_cluster(k_columns<float>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P);
+}
+
+cudaError_t launch_solve(const Work &w, int count, int max_P, int cl, const LaunchArgs &a, cudaStream_t st) {
+    const size_t smem = solve_smem_bytes(max_P, cl);
+    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)count << cl);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (cl > 0) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1u << cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, k_solve, w, a, cl);
 }
 
 cudaError_t launch_finish(const Work &w, int count, int max_P, const LaunchArgs &a, cudaStream_t st) {

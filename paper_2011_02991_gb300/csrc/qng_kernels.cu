@@ -115,6 +115,27 @@ template <typename RA> __device__ __forceinline__ RA warp_sum(RA v) {
     return v;
 }
 
+// Warp sums of 8 values at once: a[k] of every lane is summed over the warp; the lane returns the
+// sum of a[(lane >> 2) & 7]. 9 additions and 18 shuffles for 8 sums instead of 40 and 80.
+template <typename RA> __device__ __forceinline__ RA warp_sum8(const RA (&a)[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    RA t[4], u[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const RA mine = b4 ? a[4 + k] : a[k], other = b4 ? a[k] : a[4 + k];
+        t[k] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const RA mine = b3 ? t[2 + k] : t[k], other = b3 ? t[k] : t[2 + k];
+        u[k] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+    }
+    RA v = (b2 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, b2 ? u[0] : u[1], 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
 // ------------------------------------------------------------------------------------------
 // Cluster-resident state: CTA `rank` holds amplitudes [rank * Nl, (rank + 1) * Nl) in buf.
 // Qubits >= nl are distributed; a pair on such a qubit has its halves in two CTAs at the same
@@ -204,7 +225,8 @@ template <typename R> struct Eng {
     __device__ void maybe_renorm(double &scale) {
         if constexpr (std::is_same<R, double>::value) {
             const double lim = 0x1p-200;
-            if (fabs(scale) < lim) {
+            const int ex = (int)((__double_as_longlong(scale) >> 52) & 0x7ff);  // integer test, no float64 op
+            if (ex < 1023 - 200) {
                 for (uint32_t l = threadIdx.x; l < Nl; l += blockDim.x) {
                     cx x = buf[l];
                     x.x *= lim; x.y *= lim;
@@ -230,6 +252,8 @@ template <typename R> __device__ __forceinline__ Eng<R> make_eng(unsigned char *
     e.rv0 = e.buf + e.Nl;
     e.rv1 = e.rv0 + e.Nl;
     e.phase = 0;
+    // distributed shared memory may only be touched once every CTA of the cluster is running
+    if (cl) cg::this_cluster().sync();
     return e;
 }
 
@@ -643,6 +667,8 @@ __global__ void __launch_bounds__(1024) k_columns(Work w, int work_first, int cl
     }
 
     const bool want_im = grad_col;
+    RA acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // acc[k]: this thread's partial sum of step s - k
+    int cnt = 0;
     for (int s = 0; s < nsteps; ++s) {
         const int i = i0 - s;
         const DevParam pi = w.param[in.param_tab + i];
@@ -660,8 +686,17 @@ __global__ void __launch_bounds__(1024) k_columns(Work w, int work_first, int cl
                 for (int f = pi.fix_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[pi.fix_begin + f], scale_b);
             e.maybe_renorm(scale_b);
         }
-        const double pw = (double)warp_sum(part);
-        if (lane == 0) red[(size_t)s * nw + wid] = pw;
+#pragma unroll
+        for (int k = 7; k > 0; --k) acc[k] = acc[k - 1];
+        acc[0] = part;
+        if (++cnt == 8 || s == nsteps - 1) {
+            const int idx = (lane >> 2) & 7;
+            const double pw = (double)warp_sum8(acc, lane);
+            if ((lane & 3) == 0 && idx < cnt) red[(size_t)(s - idx) * nw + wid] = pw;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = 0;
+            cnt = 0;
+        }
     }
 
     // reduce the per-warp partial sums over the cluster (rank 0) and write the results
@@ -769,36 +804,42 @@ __global__ void __launch_bounds__(512) k_finish(Work w, LaunchArgs a) {
 
 // ------------------------------------------------------------------------------------------
 // k_solve: one cluster of 2^cl CTAs per instance. Assembly of g (Eq. g_t_L_def), then the float64
-// Cholesky factorisation of A = g + lambda I and the solve of A dtheta = -dt grad (Eq. 3), with the
-// rows of A spread over the cluster (row i lives in CTA i mod C) in shared memory.
-// Blocked right-looking factorisation, block width kNb: every CTA factors the kNb x kNb diagonal
-// block itself (fetched through distributed shared memory), computes the panel entries of its own
-// rows, then updates its own trailing rows with the panel gathered from all CTAs. The forward
-// substitution L y = b rides along block by block; the back substitution L^T x = y runs block by
-// block from the end with one cluster reduction per block. Three cluster barriers per block.
+// Cholesky factorisation of A = g + lambda I and the solve of A dtheta = -dt grad (Eq. 3). Row i of
+// A lives in the shared memory of CTA i mod C. Blocked right-looking factorisation, block width kNb:
+//   (B) barrier: the diagonal block and its right-hand side have been pushed to every CTA;
+//   (C) every CTA factors the diagonal block itself and solves that block of L y = b;
+//   (D) each CTA turns its own rows below the block into panel rows of L, updates its entries of
+//       b, and pushes its panel rows to every CTA (remote stores only, no remote loads);
+//   (E) barrier: the whole panel is in every CTA;
+//   (F) each CTA updates its own trailing rows, then pushes its rows of the next diagonal block.
+// Single buffers are safe: a buffer is rewritten only after a barrier that every reader reached
+// after its last read. The back substitution L^T x = y runs block by block from the end: partial
+// sums of the own rows are pushed to every CTA (two parity buffers), one barrier per block, and
+// every CTA solves the block with the diagonal blocks of L it kept from (C).
 constexpr int kNb = 16;
 
 struct SolveSmem {
     double *A;      // [R][P] own rows
-    double *PLt;    // [kNb][P] panel of the current block, transposed (column c, row j)
-    double *D;      // [kNb][kNb] diagonal block, factored in place
-    double *ys;     // [P] y (forward substitution), then x
-    double *part;   // [2][kNb] per-CTA partial sums of the back substitution
+    double *PLt;    // [kNb][P] panel of the current block, column-major (column c, row j - t0)
+    double *Ld;     // [nblk][kNb][kNb] factored diagonal blocks (the current one is factored in place)
+    double *ys;     // [P] y, then x
+    double *part;   // [2][C][kNb] pushed partial sums of the back substitution
     double *b;      // [R] own entries of the right-hand side
-    double *invd;   // [kNb] reciprocals of the diagonal block's pivots
+    double *inv;    // [kNb] reciprocal pivots of the current block
     int *flag;
 };
 
-__device__ __forceinline__ SolveSmem solve_smem(unsigned char *smem, int R, int P) {
+__device__ __forceinline__ SolveSmem solve_smem(unsigned char *smem, int R, int P, int C) {
+    const int nblk = (P + kNb - 1) / kNb;
     SolveSmem s;
     s.A = reinterpret_cast<double *>(smem);
     s.PLt = s.A + (size_t)R * P;
-    s.D = s.PLt + (size_t)kNb * P;
-    s.ys = s.D + kNb * kNb;
+    s.Ld = s.PLt + (size_t)kNb * P;
+    s.ys = s.Ld + (size_t)nblk * kNb * kNb;
     s.part = s.ys + P;
-    s.b = s.part + 2 * kNb;
-    s.invd = s.b + R;
-    s.flag = reinterpret_cast<int *>(s.invd + kNb);
+    s.b = s.part + 2 * C * kNb;
+    s.inv = s.b + R;
+    s.flag = reinterpret_cast<int *>(s.inv + kNb);
     return s;
 }
 
@@ -809,16 +850,18 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     const int rank = cl ? (int)cg::this_cluster().block_rank() : 0;
     const DevInst in = w.inst[b];
     const int P = in.P;
-    const int R = (P + C - 1) / C;  // rows per CTA (upper bound)
-    SolveSmem sm = solve_smem(smem, R, P);
+    const int R = (P + C - 1) / C;
+    SolveSmem sm = solve_smem(smem, R, P, C);
     const double *sg = w.sigma + in.param_off;
     const double *L = w.L + in.metric_off;
     const double *gr = w.gradraw + in.param_off;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     auto csync = [&]() { if (cl) cg::this_cluster().sync(); else __syncthreads(); };
-    auto remote = [&](double *p, int r) -> double * { return cl ? cg::this_cluster().map_shared_rank(p, r) : p; };
-
-    // assembly of own rows; g_out, grad_out and energy_out
+    auto rptr = [&](double *p, int r) -> double * { return cl ? cg::this_cluster().map_shared_rank(p, r) : p; };
+    const int nblk = (P + kNb - 1) / kNb;
     const int nown = (rank < P) ? (P - 1 - rank) / C + 1 : 0;
+
+    // assembly of own rows, outputs
     for (int t = threadIdx.x; t < nown * P; t += blockDim.x) {
         const int il = t / P, j = t % P, i = il * C + rank;
         double v;
@@ -838,88 +881,109 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     }
     if (threadIdx.x == 0) *sm.flag = 0;
     __syncthreads();
-    csync();
-
-    const int nblk = (P + kNb - 1) / kNb;
-    bool failed = false;
-    for (int kb = 0; kb < nblk && !failed; ++kb) {
-        const int c0 = kb * kNb, nb = min(kNb, P - c0), t0 = c0 + nb;
-        // (1) diagonal block and the matching entries of b, fetched from their owners
-        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-            const int r = t / nb, c = t % nb, i = c0 + r;
-            sm.D[r * kNb + c] = (c <= r) ? remote(sm.A, i % C)[(size_t)(i / C) * P + c0 + c] : 0.0;
+    csync();  // every CTA is running before any distributed shared memory access
+    // push the first diagonal block (rows 0..nb-1) and its b entries
+    auto push_diag = [&](int kb) {
+        const int c0 = kb * kNb, nb = min(kNb, P - c0);
+        double *dst = sm.Ld + (size_t)kb * kNb * kNb;
+        for (int t = threadIdx.x; t < nb * (nb + 1); t += blockDim.x) {
+            const int r = t / (nb + 1), c = t % (nb + 1), i = c0 + r;
+            if (i % C != rank) continue;
+            const double v = (c < nb) ? ((c <= r) ? sm.A[(size_t)(i / C) * P + c0 + c] : 0.0) : sm.b[i / C];
+            for (int q = 0; q < C; ++q) {
+                if (c < nb) rptr(dst, q)[r * kNb + c] = v;
+                else rptr(sm.ys, q)[i] = v;
+            }
         }
-        for (int r = threadIdx.x; r < nb; r += blockDim.x) sm.ys[c0 + r] = remote(sm.b, (c0 + r) % C)[(c0 + r) / C];
+    };
+    push_diag(0);
+
+    bool failed = false;
+    for (int kb = 0; kb < nblk; ++kb) {
+        const int c0 = kb * kNb, nb = min(kNb, P - c0), t0 = c0 + nb;
+        double *D = sm.Ld + (size_t)kb * kNb * kNb;
         __syncthreads();
-        // (2) factor the diagonal block and solve its part of L y = b (warp 0, lanes in parallel)
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
+        csync();  // (B)
+        // (C) factor the diagonal block in place and solve its part of L y = b (warp 0)
+        if (wid == 0) {
             for (int k = 0; k < nb; ++k) {
-                const double d = sm.D[k * kNb + k];
+                const double d = D[k * kNb + k];
                 if (!(d > 0.0)) { if (lane == 0) *sm.flag = 1; break; }
-                const double rd = sqrt(d), inv = 1.0 / rd;
+                const double iv = rsqrt(d);
                 __syncwarp();
-                for (int r = k + 1 + lane; r < nb; r += 32) sm.D[r * kNb + k] *= inv;
-                if (lane == 0) { sm.D[k * kNb + k] = rd; sm.invd[k] = inv; }
+                if (lane > k && lane < nb) D[lane * kNb + k] *= iv;
+                if (lane == 0) { D[k * kNb + k] = d * iv; sm.inv[k] = iv; }
                 __syncwarp();
                 for (int t = lane; t < nb * nb; t += 32) {
                     const int r = t / nb, c = t % nb;
-                    if (c > k && c <= r) sm.D[r * kNb + c] = fma(-sm.D[r * kNb + k], sm.D[c * kNb + k], sm.D[r * kNb + c]);
+                    if (c > k && c <= r) D[r * kNb + c] = fma(-D[r * kNb + k], D[c * kNb + k], D[r * kNb + c]);
                 }
                 __syncwarp();
             }
             __syncwarp();
             if (!*sm.flag) {
-                for (int c = 0; c < nb; ++c) {  // column-oriented forward substitution
-                    if (lane == 0) sm.ys[c0 + c] *= sm.invd[c];
+                for (int c = 0; c < nb; ++c) {
+                    if (lane == 0) sm.ys[c0 + c] *= sm.inv[c];
                     __syncwarp();
                     const double yc = sm.ys[c0 + c];
-                    for (int r = c + 1 + lane; r < nb; r += 32) sm.ys[c0 + r] = fma(-sm.D[r * kNb + c], yc, sm.ys[c0 + r]);
+                    if (lane > c && lane < nb) sm.ys[c0 + lane] = fma(-D[lane * kNb + c], yc, sm.ys[c0 + lane]);
                     __syncwarp();
                 }
             }
         }
         __syncthreads();
-        if (*sm.flag) { failed = true; break; }  // every CTA factors the same block: all stop together
-        // (3) own rows: the diagonal block's rows take L, rows below become panel rows
+        if (*sm.flag) { failed = true; break; }  // identical in every CTA: all stop together
+        // (D) own rows: diagonal-block rows take L, rows below become panel rows (pushed)
         for (int il = threadIdx.x; il < nown; il += blockDim.x) {
             const int i = il * C + rank;
             double *row = sm.A + (size_t)il * P;
             if (i >= c0 && i < t0) {
-                for (int c = 0; c <= i - c0; ++c) row[c0 + c] = sm.D[(i - c0) * kNb + c];
+                for (int c = 0; c <= i - c0; ++c) row[c0 + c] = D[(i - c0) * kNb + c];
             } else if (i >= t0) {
+                double pr[kNb];
+#pragma unroll
+                for (int c = 0; c < kNb; ++c) pr[c] = (c < nb) ? row[c0 + c] : 0.0;
                 double bi = sm.b[il];
-                for (int c = 0; c < nb; ++c) {
-                    double v = row[c0 + c];
-                    for (int c2 = 0; c2 < c; ++c2) v = fma(-row[c0 + c2], sm.D[c * kNb + c2], v);
-                    v *= sm.invd[c];
-                    row[c0 + c] = v;
-                    bi = fma(-v, sm.ys[c0 + c], bi);
+#pragma unroll
+                for (int c = 0; c < kNb; ++c) {  // right-looking: short dependency chain per column
+                    if (c < nb) {
+                        const double v = pr[c] * sm.inv[c];
+                        pr[c] = v;
+                        bi = fma(-v, sm.ys[c0 + c], bi);
+#pragma unroll
+                        for (int c2 = c + 1; c2 < kNb; ++c2)
+                            if (c2 < nb) pr[c2] = fma(-v, D[c2 * kNb + c], pr[c2]);
+                    }
                 }
                 sm.b[il] = bi;
+                const int jj = i - t0;
+#pragma unroll
+                for (int c = 0; c < kNb; ++c) {
+                    if (c < nb) {
+                        row[c0 + c] = pr[c];
+                        for (int q = 0; q < C; ++q) rptr(sm.PLt, q)[(size_t)c * P + jj] = pr[c];
+                    }
+                }
             }
         }
         __syncthreads();
-        csync();
-        // (4) gather the panel rows j >= t0 from every CTA (transposed into PLt[c][j - t0])
-        const int m = P - t0;
-        for (int t = threadIdx.x; t < m * nb; t += blockDim.x) {
-            const int jj = t / nb, c = t % nb, j = t0 + jj;
-            sm.PLt[(size_t)c * P + jj] = remote(sm.A, j % C)[(size_t)(j / C) * P + c0 + c];
-        }
-        __syncthreads();
-        // (5) trailing update of own rows: A_ij -= sum_c L_ic L_jc for t0 <= j <= i
-        for (int t = threadIdx.x; t < nown * m; t += blockDim.x) {
-            const int il = t / m, jj = t % m, i = il * C + rank, j = t0 + jj;
-            if (i < t0 || j > i) continue;
-            double v = sm.A[(size_t)il * P + j];
+        csync();  // (E)
+        // (F) trailing update of own rows: A_ij -= sum_c L_ic L_jc for t0 <= j <= i
+        for (int il = wid; il < nown; il += nw) {
+            const int i = il * C + rank;
+            if (i < t0) continue;
             const int ii = i - t0;
+            double *row = sm.A + (size_t)il * P;
+            for (int j = t0 + lane; j <= i; j += 32) {
+                const int jj = j - t0;
+                double v = row[j];
 #pragma unroll 4
-            for (int c = 0; c < nb; ++c) v -= sm.PLt[(size_t)c * P + ii] * sm.PLt[(size_t)c * P + jj];
-            sm.A[(size_t)il * P + j] = v;
+                for (int c = 0; c < nb; ++c) v = fma(-sm.PLt[(size_t)c * P + ii], sm.PLt[(size_t)c * P + jj], v);
+                row[j] = v;
+            }
         }
         __syncthreads();
-        csync();
+        if (kb + 1 < nblk) push_diag(kb + 1);
     }
     if (failed) {
         if (rank == 0 && threadIdx.x == 0) atomicCAS(w.status, 0, (int)QNG_ERR_NOT_SPD);
@@ -929,39 +993,34 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     // back substitution L^T x = y, last block first; ys turns into x block by block
     for (int kb = nblk - 1; kb >= 0; --kb) {
         const int c0 = kb * kNb, nb = min(kNb, P - c0), t0 = c0 + nb;
-        double *part = sm.part + (kb & 1) * kNb;
-        // partial sums over own rows below the block: sum_i L_{i, c0+c} x_i
-        if (threadIdx.x < 32) {
+        double *part = sm.part + (kb & 1) * C * kNb;
+        const double *D = sm.Ld + (size_t)kb * kNb * kNb;
+        if (wid == 0) {
             for (int c = 0; c < nb; ++c) {
                 double v = 0.0;
-                for (int il = threadIdx.x; il < nown; il += 32) {
+                for (int il = lane; il < nown; il += 32) {
                     const int i = il * C + rank;
-                    if (i >= t0) v += sm.A[(size_t)il * P + c0 + c] * sm.ys[i];
+                    if (i >= t0) v = fma(sm.A[(size_t)il * P + c0 + c], sm.ys[i], v);
                 }
                 v = warp_sum(v);
-                if (threadIdx.x == 0) part[c] = v;
+                if (lane < C) rptr(part, lane)[rank * kNb + c] = v;
             }
-        }
-        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {  // the diagonal block of L again
-            const int r = t / nb, c = t % nb, i = c0 + r;
-            sm.D[r * kNb + c] = (c <= r) ? remote(sm.A, i % C)[(size_t)(i / C) * P + c0 + c] : 0.0;
         }
         __syncthreads();
         csync();
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
+        if (wid == 0) {
             if (lane < nb) {
                 double sacc = 0.0;
-                for (int r = 0; r < C; ++r) sacc += remote(part, r)[lane];
+                for (int r = 0; r < C; ++r) sacc += part[r * kNb + lane];
                 sm.ys[c0 + lane] -= sacc;
-                sm.invd[lane] = 1.0 / sm.D[lane * kNb + lane];
+                sm.inv[lane] = 1.0 / D[lane * kNb + lane];
             }
             __syncwarp();
-            for (int c = nb - 1; c >= 0; --c) {  // column-oriented back substitution with L_d^T
-                if (lane == 0) sm.ys[c0 + c] *= sm.invd[c];
+            for (int c = nb - 1; c >= 0; --c) {
+                if (lane == 0) sm.ys[c0 + c] *= sm.inv[c];
                 __syncwarp();
                 const double xc = sm.ys[c0 + c];
-                if (lane < c) sm.ys[c0 + lane] = fma(-sm.D[c * kNb + lane], xc, sm.ys[c0 + lane]);
+                if (lane < c) sm.ys[c0 + lane] = fma(-D[c * kNb + lane], xc, sm.ys[c0 + lane]);
                 __syncwarp();
             }
         }
@@ -969,12 +1028,12 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     }
     if (rank == 0)
         for (int k = threadIdx.x; k < P; k += blockDim.x) a.dtheta_out[in.param_off + k] = sm.ys[k];
-    csync();  // keep every CTA's shared memory alive until all remote reads are done
+    csync();
 }
 
 size_t solve_smem_bytes(int P, int cl) {
-    const int C = 1 << cl, R = (P + C - 1) / C;
-    return sizeof(double) * ((size_t)R * P + (size_t)kNb * P + kNb * kNb + P + 2 * kNb + R + kNb) + 16;
+    const int C = 1 << cl, R = (P + C - 1) / C, nblk = (P + kNb - 1) / kNb;
+    return sizeof(double) * ((size_t)R * P + (size_t)kNb * P + (size_t)nblk * kNb * kNb + P + 2 * C * kNb + R + kNb) + 16;
 }
 
 // ------------------------------------------------------------------------------------------

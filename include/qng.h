@@ -94,7 +94,8 @@ typedef struct {
 } qng_pauli;
 
 /* Create a single-instance context. gates[0..n_gates-1] and terms[0..n_terms-1] are host arrays,
- * copied. n_qubits in 1..30; precision QNG_C64 or QNG_C128. On success *out owns the copies. */
+ * copied. n_qubits in 1..30; precision QNG_C64 or QNG_C128. On success *out owns the copies.
+ * Instances of more than 16 qubits run on the streaming path (state vectors in HBM). */
 qng_status qng_create(int n_qubits, const qng_gate *gates, int n_gates, const qng_pauli *terms, int n_terms,
                       int precision, qng_ctx **out);
 
@@ -158,6 +159,13 @@ qng_status qng_sync(qng_ctx *ctx);
  * cluster_log2 = log2 of CTAs per state (0..3), threads = CTA size (64..1024, a multiple of 32).
  * For batched contexts the settings apply to the instances with n_qubits >= min_qubits. */
 qng_status qng_set_tuning(qng_ctx *ctx, int min_qubits, int cluster_log2, int threads);
+
+/* Execution path: 0 automatic (on-chip for n <= 16 qubits, streaming above), 1 on-chip (every
+ * state of an instance in the shared memory of one thread-block cluster, O(P) checkpoints in HBM),
+ * 2 streaming (single instance only: O(1) registers of 2^n amplitudes in HBM, tiled passes). A
+ * change re-plans the context; if the workspace already set is then too small the call returns
+ * QNG_ERR_WORKSPACE and keeps the old path (query qng_workspace_size before setting a workspace). */
+qng_status qng_set_path(qng_ctx *ctx, int path);
 
 /* Kernel timing with CUDA events recorded on the context's stream around every launch.
  * qng_profile(ctx, 1) starts recording, qng_profile(ctx, 0) stops. qng_profile_read waits for the

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "qng_internal.h"
+#include "qng_large.h"
 
 using namespace qng;
 
@@ -81,6 +82,13 @@ struct qng_ctx {
     bool prepared = false;
     // tuning
     int tune_min_qubits = 0, tune_cl = -1, tune_threads = 0;
+    int path = 0;             // 0 automatic, 1 on-chip, 2 streaming
+    // streaming path (one instance, registers in HBM)
+    bool streaming = false;
+    large::Schedule sched;
+    int l_grid = 0;
+    size_t o_reg[large::kRegs] = {0, 0, 0};
+    size_t o_regscale = 0, o_partial = 0, o_slotfac = 0, o_pdesc = 0, o_pops = 0, o_red = 0;
     int64_t last_launches = 0;
     // kernel timing (qng_profile)
     bool profiling = false;
@@ -138,6 +146,51 @@ int default_threads(int nl) {
     if (Nl <= 256) return 64;
     if (Nl <= 1024) return 128;
     return 256;
+}
+
+// Streaming path: schedule of passes and the workspace layout (no checkpoints).
+qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
+    const HostInst &h = c->inst[0];
+    const size_t ab = amp_bytes(c->precision);
+    c->sched = large::Schedule();
+    large::build_schedule(h.gates, h.n, h.P, c->precision, c->sched);
+    const int64_t ntiles = 1ll << (h.n - c->sched.t);
+    c->l_grid = (int)std::min<int64_t>(ntiles, 152 * 2);
+    c->t_inst[0].cl = 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = align256(off); off = o + std::max<size_t>(bytes, 1); return o; };
+    c->o_status = take(256);
+    c->o_inst = take(sizeof(DevInst) * c->t_inst.size());
+    c->o_param = take(sizeof(DevParam) * std::max<size_t>(c->t_param.size(), 1));
+    c->o_fixed = take(sizeof(DevFixed) * std::max<size_t>(c->t_fixed.size(), 1));
+    c->o_diag = take(sizeof(DevDiag) * std::max<size_t>(c->t_diag.size(), 1));
+    c->o_term = take(sizeof(DevTerm) * std::max<size_t>(c->t_term.size(), 1));
+    c->o_work = take(8);
+    c->o_ginst = take(8);
+    c->o_coef = take(sizeof(DevCoef) * c->total_params);
+    c->o_sigma = take(sizeof(double) * c->total_params);
+    c->o_scale = take(sizeof(double) * scale_n);
+    c->o_L = take(sizeof(double) * c->total_metric);
+    c->o_grad = take(sizeof(double) * c->total_params);
+    c->o_energy = take(sizeof(double) * c->count);
+    c->o_chol = take(sizeof(double) * c->total_metric);
+    c->o_io_theta = take(sizeof(double) * c->total_params);
+    c->o_io_dtheta = take(sizeof(double) * c->total_params);
+    c->o_io_g = take(sizeof(double) * c->total_metric);
+    c->o_io_grad = take(sizeof(double) * c->total_params);
+    c->o_io_energy = take(sizeof(double) * c->count);
+    c->o_regscale = take(sizeof(double) * 2 * large::kRegs);
+    c->o_partial = take(sizeof(double) * (size_t)c->sched.max_slots * c->l_grid);
+    c->o_slotfac = take(sizeof(double) * (size_t)c->sched.max_slots);
+    c->o_pdesc = take(sizeof(large::PassDesc) * std::max<size_t>(c->sched.passes.size(), 1));
+    c->o_pops = take(sizeof(large::PassOp) * std::max<size_t>(c->sched.ops.size(), 1));
+    c->o_red = take(sizeof(large::ReduceItem) * std::max<size_t>(c->sched.reds.size(), 1));
+    for (int r = 0; r < large::kRegs; ++r) c->o_reg[r] = take(ab << h.n);
+    c->o_ckpt = c->o_eta = 0;
+    c->ws_bytes = align256(off);
+    c->groups.clear();
+    c->prepared = false;
+    return QNG_OK;
 }
 
 // Build the device-table images, the launch groups and the workspace layout.
@@ -225,6 +278,8 @@ qng_status plan(qng_ctx *c) {
     }
     c->total_params = c->param_off[c->count];
     c->total_metric = c->metric_off[c->count];
+    c->streaming = c->count == 1 && (c->path == 2 || (c->path == 0 && c->inst[0].n > kMaxQubitsSmall));
+    if (c->streaming) return plan_streaming(c, scale_n);
 
     // groups: instances sharing (cluster size, CTA size)
     std::vector<std::pair<int, int>> shape(c->count);
@@ -330,6 +385,27 @@ qng_status upload(qng_ctx *c) {
         return cuda_status(e);
     // host tables must stay valid until the copies ran: pageable-memory copies are staged
     // synchronously with respect to the host, so returning here is safe
+    if (c->streaming) {
+        const large::Schedule &S = c->sched;
+        if ((e = put(c->o_pdesc, S.passes.data(), sizeof(large::PassDesc) * S.passes.size())) != cudaSuccess) return cuda_status(e);
+        if ((e = put(c->o_pops, S.ops.data(), sizeof(large::PassOp) * S.ops.size())) != cudaSuccess) return cuda_status(e);
+        std::vector<large::ReduceItem> items(S.reds.size());
+        for (size_t k = 0; k < S.reds.size(); ++k) {
+            const large::RedSpec &r = S.reds[k];
+            size_t region = r.region == large::kRegionSigma ? c->o_sigma
+                          : r.region == large::kRegionL ? c->o_L
+                          : r.region == large::kRegionGrad ? c->o_grad : c->o_energy;
+            items[k].slot = r.slot;
+            items[k].pad = 0;
+            items[k].mul = r.mul;
+            items[k].dst = reinterpret_cast<double *>(c->ws + region) + r.index;
+        }
+        if ((e = put(c->o_red, items.data(), sizeof(large::ReduceItem) * items.size())) != cudaSuccess) return cuda_status(e);
+        static const double ones[2 * large::kRegs] = {1, 1, 1, 1, 1, 1};
+        if ((e = put(c->o_regscale, ones, sizeof(ones))) != cudaSuccess) return cuda_status(e);
+        c->prepared = true;
+        return QNG_OK;
+    }
     size_t sf = 0, sc = 0;
     for (const Group &g : c->groups) { sf = std::max(sf, g.smem_fwd); sc = std::max(sc, g.smem_col); }
     if ((e = prepare_kernels(c->precision, sf, sc)) != cudaSuccess) return cuda_status(e);
@@ -348,6 +424,52 @@ template <class F> cudaError_t timed(qng_ctx *c, int cls, F &&launch) {
     if (e != cudaSuccess) { c->spare.push_back(a); c->spare.push_back(b); return e; }
     c->marks.push_back({cls, a, b});
     return cudaSuccess;
+}
+
+// The streaming schedule's launches for the requested jobs.
+qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
+    const large::Schedule &S = c->sched;
+    const HostInst &h = c->inst[0];
+    const bool energy = jobs & (kJobEnergy | kJobGradient | kJobSolve);
+    const bool grad = jobs & (kJobGradient | kJobSolve);
+    const bool metric = jobs & (kJobMetric | kJobSolve);
+    large::PassArgs pa = {};
+    pa.ops = reinterpret_cast<const large::PassOp *>(c->ws + c->o_pops);
+    pa.coef = reinterpret_cast<const DevCoef *>(c->ws + c->o_coef);
+    for (int r = 0; r < large::kRegs; ++r) pa.reg[r] = c->ws + c->o_reg[r];
+    pa.regscale = reinterpret_cast<double *>(c->ws + c->o_regscale);
+    pa.partial = reinterpret_cast<double *>(c->ws + c->o_partial);
+    pa.slotfac = reinterpret_cast<double *>(c->ws + c->o_slotfac);
+    const large::PassDesc *descs = reinterpret_cast<const large::PassDesc *>(c->ws + c->o_pdesc);
+    const large::ReduceItem *items = reinterpret_cast<const large::ReduceItem *>(c->ws + c->o_red);
+    const size_t ab = amp_bytes(c->precision);
+    for (const large::Launch &L : S.launches) {
+        const bool want = (L.segment == large::kSegForward || L.segment == large::kSegEnergy) ? energy
+                        : (L.segment == large::kSegAdjoint ? grad : metric);
+        if (!want) continue;
+        cudaError_t e = cudaSuccess;
+        if (L.kind == large::Launch::Pass) {
+            const large::PassDesc &pd = S.passes[L.pass];
+            pa.desc = descs + L.pass;
+            const size_t smem = (size_t)__builtin_popcount(pd.regmask) * (ab << pd.t);
+            e = timed(c, L.segment == large::kSegMetric ? 2 : 1,
+                      [&] { return large::launch_pass(pa, c->precision, c->l_grid, 256, smem, c->stream); });
+        } else if (L.kind == large::Launch::Hpsi) {
+            e = timed(c, 1, [&] {
+                return large::launch_hpsi(c->ws + c->o_reg[large::kRegB], c->ws + c->o_reg[large::kRegA],
+                                          reinterpret_cast<const DevTerm *>(c->ws + c->o_term), (int)h.terms.size(), h.n,
+                                          c->precision, pa.partial, c->l_grid, c->stream);
+            });
+        } else {
+            e = timed(c, L.segment == large::kSegMetric ? 2 : 1, [&] {
+                return large::launch_reduce(pa.partial, pa.slotfac, c->l_grid, items + L.item_begin, L.nitems, L.use_fac,
+                                            c->stream);
+            });
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        ++launches;
+    }
+    return QNG_OK;
 }
 
 // cluster size of the distributed solve (-1: the single-CTA finish kernel is used)
@@ -372,6 +494,10 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
     }
     const bool need_cols = jobs & (kJobMetric | kJobGradient | kJobSolve);
     const bool want_eta = jobs & (kJobGradient | kJobSolve);
+    if (c->streaming) {
+        qng_status st = run_streaming(c, jobs, launches);
+        if (st != QNG_OK) return st;
+    }
     for (const Group &g : c->groups) {
         if (g.num_inst == 0) continue;
         e = timed(c, 1, [&] { return launch_forward(w, g, c->precision, want_eta, c->stream); });
@@ -434,7 +560,7 @@ qng_status qng_create_batch(int count, const int32_t *n_qubits, const qng_gate *
         if (s != QNG_OK) { delete c; return s; }
         go += n_gates[b];
         to += n_terms[b];
-        if (c->inst[b].n > kMaxQubitsSmall) { delete c; return QNG_ERR_UNSUPPORTED; }
+        if (c->inst[b].n > kMaxQubitsSmall && count > 1) { delete c; return QNG_ERR_UNSUPPORTED; }
     }
     qng_status s = plan(c);
     if (s != QNG_OK) { delete c; return s; }
@@ -589,6 +715,24 @@ qng_status qng_sync(qng_ctx *c) {
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_status(e);
         return static_cast<qng_status>(st);
     }
+    return QNG_OK;
+}
+
+qng_status qng_set_path(qng_ctx *c, int path) {
+    if (!c || path < 0 || path > 2) return QNG_ERR_ARG;
+    if (path == 1 && c->count == 1 && c->inst[0].n > kMaxQubitsSmall) return QNG_ERR_UNSUPPORTED;
+    if (path == 2 && c->count != 1) return QNG_ERR_UNSUPPORTED;
+    const int old = c->path;
+    const size_t old_bytes = c->ws_bytes;
+    c->path = path;
+    qng_status s = plan(c);
+    if (s != QNG_OK || (c->ws && c->ws_bytes > old_bytes)) {
+        c->path = old;
+        plan(c);
+        if (c->ws) upload(c);
+        return s != QNG_OK ? s : QNG_ERR_WORKSPACE;
+    }
+    if (c->ws) return upload(c);
     return QNG_OK;
 }
 

@@ -1,0 +1,414 @@
+// sm_103a kernels of the streaming path, for one instance whose state vectors live in HBM
+// (n > 16 qubits, 2^n amplitudes per register). Algorithm 1 keeps O(1) registers (Sec. 3): the
+// rolling state psi, the prefix lambda (here "a") and phi (here "b"). Every kernel launch is one
+// pass over the registers it touches: the state is cut into tiles of 2^t amplitudes (the low
+// kLow qubits, contiguous in memory, plus a window of up to kMaxWin other qubits); a CTA loads a
+// tile of each register into shared memory, runs a short program of operations on it (rotations,
+// fixed gates, sigma, inner products) and writes it back. Operations on qubits outside the tile
+// must be diagonal (Z rotations, CZ, Z, Z-axis inner products); the host forms passes so that all
+// other operations act on tile qubits. Several steps of the recurrence share one pass, so HBM
+// traffic per step is 4 S / (steps per pass) for the two column registers (S = bytes per register).
+//
+// Inner products accumulate per CTA into partial[slot][cta]; the column's reduce kernel sums them
+// in a fixed order. float64 registers use the scaled form of the on-chip path: each register is a
+// float64 factor times a vector, the factors live in a two-entry parity buffer per register
+// (launch p reads entry p&1 and writes entry (p+1)&1), and every inner product records the product
+// of its registers' factors in slotfac[slot].
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "qng_large.h"
+
+namespace qng {
+namespace large {
+
+template <typename R> struct CX2;
+template <> struct CX2<double> { using T = double2; };
+template <> struct CX2<float> { using T = float2; };
+
+__device__ __forceinline__ double lflip(double v, int p) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(p & 1) << 63));
+}
+__device__ __forceinline__ float lflip(float v, int p) { return __int_as_float(__float_as_int(v) ^ ((p & 1) << 31)); }
+template <typename T2> __device__ __forceinline__ T2 lflip2(T2 v, int p) {
+    v.x = lflip(v.x, p);
+    v.y = lflip(v.y, p);
+    return v;
+}
+__device__ __forceinline__ uint32_t lins0(uint32_t p, int q) { return ((p >> q) << (q + 1)) | (p & ((1u << q) - 1u)); }
+
+template <typename RA> __device__ __forceinline__ RA lwarp_sum(RA v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct TileCtx {
+    int t;                 // tile qubits
+    uint32_t T;            // 2^t
+    int low;               // contiguous low qubits
+    int win;               // window qubits
+    int lbit[64];          // local bit of global qubit q, or -1 when q is outside the tile
+    uint64_t base;         // global index of the tile's local index 0
+};
+
+// global index of local index l in the current tile
+__device__ __forceinline__ uint64_t gidx(const TileCtx &tc, const uint64_t *rowoff, uint32_t l) {
+    return tc.base | rowoff[l >> tc.low] | (l & ((1u << tc.low) - 1u));
+}
+
+// bit q of global index of local l
+__device__ __forceinline__ int gbit(const TileCtx &tc, uint32_t l, int q) {
+    const int lb = tc.lbit[q];
+    return lb >= 0 ? (int)((l >> lb) & 1u) : (int)((tc.base >> q) & 1ull);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
+    using cx = typename CX2<R>::T;
+    constexpr bool kScaled = std::is_same<R, double>::value;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t rowoff[1 << kMaxWin];
+    __shared__ TileCtx tc;
+    __shared__ double red[32];
+    const PassDesc pd = *pa.desc;
+    const int nt = blockDim.x, nw = nt >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    cx *tile[kRegs];
+    {
+        cx *p = reinterpret_cast<cx *>(smem);
+        for (int r = 0; r < kRegs; ++r) {
+            tile[r] = p;
+            if (pd.regmask & (1 << r)) p += (size_t)1 << pd.t;
+        }
+    }
+    if (threadIdx.x == 0) {
+        tc.t = pd.t;
+        tc.T = 1u << pd.t;
+        tc.low = pd.low;
+        tc.win = pd.win;
+        for (int q = 0; q < 64; ++q) tc.lbit[q] = -1;
+        for (int q = 0; q < pd.low; ++q) tc.lbit[q] = q;
+        for (int k = 0; k < pd.win; ++k) tc.lbit[pd.wq[k]] = pd.low + k;
+    }
+    for (uint32_t r = threadIdx.x; r < (1u << pd.win); r += nt) {
+        uint64_t o = 0;
+        for (int k = 0; k < pd.win; ++k) o |= (uint64_t)((r >> k) & 1u) << pd.wq[k];
+        rowoff[r] = o;
+    }
+    // register scale factors at the start of this pass (float64 form)
+    double scale[kRegs];
+    for (int r = 0; r < kRegs; ++r) scale[r] = kScaled ? pa.regscale[(pd.parity & 1) * kRegs + r] : 1.0;
+    double part[kMaxSlots];
+    for (int k = 0; k < kMaxSlots; ++k) part[k] = 0.0;
+    __syncthreads();
+    const uint64_t ntiles = 1ull << (pd.n - pd.t);
+    // free (non-tile) qubit positions above the low block, ascending
+    for (uint64_t tile_id = blockIdx.x; tile_id < ntiles; tile_id += gridDim.x) {
+        if (threadIdx.x == 0) {
+            uint64_t b = 0, rem = tile_id;
+            for (int q = pd.low; q < pd.n && rem; ++q) {
+                if (tc.lbit[q] >= 0) continue;
+                b |= (rem & 1ull) << q;
+                rem >>= 1;
+            }
+            tc.base = b;
+        }
+        __syncthreads();
+        // load
+        for (int r = 0; r < kRegs; ++r) {
+            if (!(pd.regmask & (1 << r)) || !(pd.loadmask & (1 << r))) continue;
+            const cx *src = reinterpret_cast<const cx *>(pa.reg[r]);
+            for (uint32_t l = threadIdx.x; l < tc.T; l += nt) tile[r][l] = src[gidx(tc, rowoff, l)];
+        }
+        __syncthreads();
+        double sc[kRegs];
+        for (int r = 0; r < kRegs; ++r) sc[r] = scale[r];
+        for (int o = 0; o < pd.nops; ++o) {
+            const PassOp op = pa.ops[pd.op_begin + o];
+            switch (op.kind) {
+            case kOpCopy: {
+                for (uint32_t l = threadIdx.x; l < tc.T; l += nt) tile[op.r1][l] = tile[op.r0][l];
+                sc[op.r1] = sc[op.r0];
+                break;
+            }
+            case kOpZero: {  // |0...0> into register r0 (scale 1)
+                for (uint32_t l = threadIdx.x; l < tc.T; l += nt) {
+                    cx z = {0, 0};
+                    if (gidx(tc, rowoff, l) == 0) z.x = 1;
+                    tile[op.r0][l] = z;
+                }
+                sc[op.r0] = 1.0;
+                break;
+            }
+            case kOpRot: {  // y = c x + i s' sigma x on every register of op.regs (s' = +-s)
+                const DevCoef co = pa.coef[op.param];
+                const double sg = op.adjoint ? 1.0 : -1.0;
+                const R c = (R)co.c, s = (R)(sg * co.s), t = (R)(sg * co.t);
+                const int caseB = co.caseB;
+                const double f = co.caseB ? sg * co.f : co.f;
+                const int q = op.q0, ax = op.axis;
+                for (int r = 0; r < kRegs; ++r) {
+                    if (!(op.regs & (1 << r))) continue;
+                    cx *X = tile[r];
+                    if (ax == kAxisZ) {
+                        for (uint32_t l = threadIdx.x; l < tc.T; l += nt) {
+                            const int beta = gbit(tc, l, q);
+                            const cx x = X[l];
+                            const cx v = {lflip(x.y, beta ^ 1), lflip(x.x, beta)};  // (i Z x)
+                            cx y;
+                            if (kScaled) {
+                                if (caseB) { y.x = fma(t, x.x, v.x); y.y = fma(t, x.y, v.y); }
+                                else       { y.x = fma(t, v.x, x.x); y.y = fma(t, v.y, x.y); }
+                            } else {
+                                y.x = fma(s, v.x, c * x.x); y.y = fma(s, v.y, c * x.y);
+                            }
+                            X[l] = y;
+                        }
+                    } else {
+                        const int lb = tc.lbit[q];
+                        const uint32_t bit = 1u << lb;
+                        for (uint32_t p = threadIdx.x; p < (tc.T >> 1); p += nt) {
+                            const uint32_t l0 = lins0(p, lb), l1 = l0 | bit;
+                            const cx x0 = X[l0], x1 = X[l1];
+                            cx v0, v1;
+                            if (ax == kAxisX) { v0 = cx{-x1.y, x1.x}; v1 = cx{-x0.y, x0.x}; }
+                            else              { v0 = x1; v1 = cx{-x0.x, -x0.y}; }
+                            cx y0, y1;
+                            if (kScaled) {
+                                if (caseB) {
+                                    y0.x = fma(t, x0.x, v0.x); y0.y = fma(t, x0.y, v0.y);
+                                    y1.x = fma(t, x1.x, v1.x); y1.y = fma(t, x1.y, v1.y);
+                                } else {
+                                    y0.x = fma(t, v0.x, x0.x); y0.y = fma(t, v0.y, x0.y);
+                                    y1.x = fma(t, v1.x, x1.x); y1.y = fma(t, v1.y, x1.y);
+                                }
+                            } else {
+                                y0.x = fma(s, v0.x, c * x0.x); y0.y = fma(s, v0.y, c * x0.y);
+                                y1.x = fma(s, v1.x, c * x1.x); y1.y = fma(s, v1.y, c * x1.y);
+                            }
+                            X[l0] = y0;
+                            X[l1] = y1;
+                        }
+                    }
+                    if (kScaled) sc[r] *= f;
+                }
+                break;
+            }
+            case kOpFixed: {  // a fixed gate on every register of op.regs (all fixed gates are self-adjoint)
+                const int kind = op.fixed_kind;
+                const R hs = kScaled ? (R)1 : (R)0.70710678118654752440;
+                for (int r = 0; r < kRegs; ++r) {
+                    if (!(op.regs & (1 << r))) continue;
+                    cx *X = tile[r];
+                    if (kind == QNG_GATE_CZ || kind == QNG_GATE_Z) {
+                        for (uint32_t l = threadIdx.x; l < tc.T; l += nt) {
+                            const int p = (kind == QNG_GATE_CZ) ? (gbit(tc, l, op.q0) & gbit(tc, l, op.q1)) : gbit(tc, l, op.q0);
+                            if (p) X[l] = lflip2(X[l], 1);
+                        }
+                    } else {
+                        const int qt = (kind == QNG_GATE_CNOT) ? op.q1 : op.q0;
+                        const int lb = tc.lbit[qt];
+                        const uint32_t bit = 1u << lb;
+                        for (uint32_t p = threadIdx.x; p < (tc.T >> 1); p += nt) {
+                            const uint32_t l0 = lins0(p, lb), l1 = l0 | bit;
+                            const cx x0 = X[l0], x1 = X[l1];
+                            cx y0, y1;
+                            if (kind == QNG_GATE_CNOT) {
+                                if (gbit(tc, l0, op.q0)) { y0 = x1; y1 = x0; } else { y0 = x0; y1 = x1; }
+                            } else if (kind == QNG_GATE_X) {
+                                y0 = x1; y1 = x0;
+                            } else if (kind == QNG_GATE_Y) {
+                                y0 = cx{x1.y, -x1.x}; y1 = cx{-x0.y, x0.x};
+                            } else {  // H
+                                y0 = cx{(x0.x + x1.x) * hs, (x0.y + x1.y) * hs};
+                                y1 = cx{(x0.x - x1.x) * hs, (x0.y - x1.y) * hs};
+                            }
+                            X[l0] = y0;
+                            X[l1] = y1;
+                        }
+                    }
+                    if (kScaled && kind == QNG_GATE_H) sc[r] *= 0.70710678118654752440;
+                }
+                break;
+            }
+            case kOpSigma: {  // register r0 <- sigma_q register r0
+                cx *X = tile[op.r0];
+                const int q = op.q0, ax = op.axis;
+                if (ax == kAxisZ) {
+                    for (uint32_t l = threadIdx.x; l < tc.T; l += nt)
+                        if (gbit(tc, l, q)) X[l] = lflip2(X[l], 1);
+                } else {
+                    const int lb = tc.lbit[q];
+                    const uint32_t bit = 1u << lb;
+                    for (uint32_t p = threadIdx.x; p < (tc.T >> 1); p += nt) {
+                        const uint32_t l0 = lins0(p, lb), l1 = l0 | bit;
+                        const cx x0 = X[l0], x1 = X[l1];
+                        if (ax == kAxisX) { X[l0] = x1; X[l1] = x0; }
+                        else { X[l0] = cx{x1.y, -x1.x}; X[l1] = cx{-x0.y, x0.x}; }  // -i x1, i x0
+                    }
+                }
+                break;
+            }
+            case kOpIp: {  // part[slot] += Re/Im <r0| sigma_q |r1>  (axis -1: no sigma)
+                const cx *A = tile[op.r0], *B = tile[op.r1];
+                const int q = op.q0, ax = op.axis, im = op.adjoint;
+                R acc = 0;
+                if (ax < 0 || ax == kAxisZ) {
+                    for (uint32_t l = threadIdx.x; l < tc.T; l += nt) {
+                        const cx a = (ax == kAxisZ) ? lflip2(A[l], gbit(tc, l, q)) : A[l];
+                        const cx b = B[l];
+                        acc = im ? fma(a.x, b.y, fma(-a.y, b.x, acc)) : fma(a.x, b.x, fma(a.y, b.y, acc));
+                    }
+                } else {
+                    const int lb = tc.lbit[q];
+                    const uint32_t bit = 1u << lb;
+                    for (uint32_t p = threadIdx.x; p < (tc.T >> 1); p += nt) {
+                        const uint32_t l0 = lins0(p, lb), l1 = l0 | bit;
+                        const cx a0 = A[l0], a1 = A[l1], b0 = B[l0], b1 = B[l1];
+                        cx s0, s1;  // (sigma b)_0, (sigma b)_1
+                        if (ax == kAxisX) { s0 = b1; s1 = b0; }
+                        else { s0 = cx{b1.y, -b1.x}; s1 = cx{-b0.y, b0.x}; }
+                        if (im) acc = fma(a0.x, s0.y, fma(-a0.y, s0.x, fma(a1.x, s1.y, fma(-a1.y, s1.x, acc))));
+                        else acc = fma(a0.x, s0.x, fma(a0.y, s0.y, fma(a1.x, s1.x, fma(a1.y, s1.y, acc))));
+                    }
+                }
+                part[op.slot] += (double)acc;  // float64 from here on; reduced once per launch
+                if (blockIdx.x == 0 && threadIdx.x == 0 && tile_id == 0) pa.slotfac[pd.slot_base + op.slot] = sc[op.r0] * sc[op.r1];
+                break;
+            }
+            case kOpRecordFac: {
+                if (blockIdx.x == 0 && threadIdx.x == 0 && tile_id == 0) pa.slotfac[pd.slot_base + op.slot] = sc[op.r0] * sc[op.r1];
+                break;
+            }
+            case kOpSetScale: {
+                sc[op.r1] = sc[op.r0];
+                break;
+            }
+            default:
+                break;
+            }
+            __syncthreads();
+            // keep float64 scale factors far from underflow (exact power-of-two rescaling)
+            if (kScaled) {
+                for (int r = 0; r < kRegs; ++r) {
+                    if (!(pd.regmask & (1 << r))) continue;
+                    const int ex = (int)((__double_as_longlong(sc[r]) >> 52) & 0x7ff);
+                    if (ex < 1023 - 200) {
+                        for (uint32_t l = threadIdx.x; l < tc.T; l += nt) {
+                            cx x = tile[r][l];
+                            if constexpr (kScaled) { x.x *= 0x1p-200; x.y *= 0x1p-200; }
+                            tile[r][l] = x;
+                        }
+                        sc[r] *= 0x1p200;
+                        __syncthreads();
+                    }
+                }
+            }
+        }
+        // store
+        for (int r = 0; r < kRegs; ++r) {
+            if (!(pd.regmask & (1 << r)) || !(pd.storemask & (1 << r))) continue;
+            cx *dst = reinterpret_cast<cx *>(pa.reg[r]);
+            for (uint32_t l = threadIdx.x; l < tc.T; l += nt) dst[gidx(tc, rowoff, l)] = tile[r][l];
+        }
+        if (tile_id + gridDim.x >= ntiles && blockIdx.x == 0 && threadIdx.x == 0 && kScaled)
+            for (int r = 0; r < kRegs; ++r) pa.regscale[((pd.parity + 1) & 1) * kRegs + r] = sc[r];
+        __syncthreads();
+    }
+    // per-CTA partial sums: warp, then CTA, in a fixed order
+    for (int k = 0; k < pd.nslots; ++k) {
+        const double v = lwarp_sum(part[k]);
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < nw; ++w) tot += red[w];
+            pa.partial[(size_t)(pd.slot_base + k) * gridDim.x + blockIdx.x] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// out[m] = sum_t c_t i^{ny} (-1)^{popcount((m ^ x) & z)} in[m ^ x]; partial <in|out> per CTA.
+template <typename R>
+__global__ void __launch_bounds__(256) k_hpsi(const void *in_, void *out_, const DevTerm *terms, int nterms, int n,
+                                              double *partial) {
+    using cx = typename CX2<R>::T;
+    const cx *in = reinterpret_cast<const cx *>(in_);
+    cx *out = reinterpret_cast<cx *>(out_);
+    __shared__ double red[32];
+    const uint64_t N = 1ull << n;
+    double e = 0.0;
+    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < N; m += (uint64_t)gridDim.x * blockDim.x) {
+        double hr = 0.0, hi = 0.0;
+        for (int t = 0; t < nterms; ++t) {
+            const DevTerm tm = terms[t];
+            const uint64_t src = m ^ tm.x;
+            const cx v = in[src];
+            const int ph = (tm.ny + 2 * (__popcll(src & tm.z) & 1)) & 3;
+            const double vr = (double)v.x, vi = (double)v.y;
+            if (ph == 0)      { hr = fma(tm.coeff, vr, hr);  hi = fma(tm.coeff, vi, hi); }
+            else if (ph == 1) { hr = fma(-tm.coeff, vi, hr); hi = fma(tm.coeff, vr, hi); }
+            else if (ph == 2) { hr = fma(-tm.coeff, vr, hr); hi = fma(-tm.coeff, vi, hi); }
+            else              { hr = fma(tm.coeff, vi, hr);  hi = fma(-tm.coeff, vr, hi); }
+        }
+        const cx x = in[m];
+        e += (double)x.x * hr + (double)x.y * hi;
+        out[m] = cx{(R)hr, (R)hi};
+    }
+    e = lwarp_sum(e);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        partial[blockIdx.x] = tot;
+    }
+}
+
+// Sum partial[slot][0..nctas) in a fixed order and scatter: dst[k] = mul * slotfac[slot] * sum.
+__global__ void k_reduce(const double *partial, const double *slotfac, int nctas, const ReduceItem *items, int nitems,
+                         int use_fac) {
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= nitems) return;
+    const ReduceItem it = items[k];
+    double v = 0.0;
+    for (int c = lane; c < nctas; c += 32) v += partial[(size_t)it.slot * nctas + c];
+    v = lwarp_sum(v);
+    if (lane == 0) *it.dst = it.mul * (use_fac ? slotfac[it.slot] : 1.0) * v;
+}
+
+// ------------------------------------------------------------------------------------------
+cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, cudaStream_t st) {
+    if (precision == QNG_C128) {
+        cudaError_t e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_pass<double><<<grid, threads, smem, st>>>(pa);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_pass<float><<<grid, threads, smem, st>>>(pa);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hpsi(const void *in, void *out, const DevTerm *terms, int nterms, int n, int precision,
+                        double *partial, int grid, cudaStream_t st) {
+    if (precision == QNG_C128) k_hpsi<double><<<grid, 256, 0, st>>>(in, out, terms, nterms, n, partial);
+    else k_hpsi<float><<<grid, 256, 0, st>>>(in, out, terms, nterms, n, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double *partial, const double *slotfac, int nctas, const ReduceItem *items, int nitems,
+                          int use_fac, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int per = 8;  // warps per block
+    k_reduce<<<(nitems + per - 1) / per, per * 32, 0, st>>>(partial, slotfac, nctas, items, nitems, use_fac);
+    return cudaGetLastError();
+}
+
+}  // namespace large
+}  // namespace qng

@@ -1,0 +1,106 @@
+// Streaming (HBM) path: pass program format shared by the host planner and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "qng_internal.h"
+
+namespace qng {
+namespace large {
+
+constexpr int kRegs = 3;      // register slots: 0 psi, 1 a (lambda / eta), 2 b (phi)
+constexpr int kMaxWin = 7;    // tile qubits beyond the contiguous low block
+constexpr int kMaxSlots = 32; // inner products per pass
+constexpr int kRegPsi = 0, kRegA = 1, kRegB = 2;
+
+enum OpKind : int32_t {
+    kOpCopy = 0,       // r1 <- r0
+    kOpZero = 1,       // r0 <- |0...0>
+    kOpRot = 2,        // rotation param on every register of regs (adjoint: R^dag, else R)
+    kOpFixed = 3,      // fixed gate fixed_kind(q0, q1) on every register of regs
+    kOpSigma = 4,      // r0 <- sigma_{axis}(q0) r0
+    kOpIp = 5,         // slot += Re (adjoint = 0) or Im (adjoint = 1) of <r0| sigma_{axis}(q0) |r1>; axis -1: no sigma
+    kOpRecordFac = 6,  // slotfac[slot] <- scale(r0) * scale(r1)
+    kOpSetScale = 7,   // scale(r1) <- scale(r0) (no data)
+};
+
+struct PassOp {
+    int32_t kind;
+    int32_t r0, r1;
+    int32_t regs;
+    int32_t q0, q1;
+    int32_t axis;
+    int32_t adjoint;
+    int32_t param;
+    int32_t fixed_kind;
+    int32_t slot;
+    int32_t pad;
+};
+
+struct PassDesc {
+    int32_t n, t, low, win;
+    int32_t wq[kMaxWin];
+    int32_t regmask, loadmask, storemask;
+    int32_t op_begin, nops;
+    int32_t nslots, slot_base;
+    int32_t parity;
+    int32_t pad;
+};
+
+struct ReduceItem {
+    int32_t slot;
+    int32_t pad;
+    double mul;
+    double *dst;
+};
+
+struct PassArgs {
+    const PassDesc *desc;
+    const PassOp *ops;
+    const DevCoef *coef;
+    void *reg[kRegs];
+    double *regscale;  // [2][kRegs]
+    double *partial;   // [slots][grid]
+    double *slotfac;   // [slots]
+};
+
+cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_hpsi(const void *in, void *out, const DevTerm *terms, int nterms, int n, int precision,
+                        double *partial, int grid, cudaStream_t st);
+cudaError_t launch_reduce(const double *partial, const double *slotfac, int nctas, const ReduceItem *items, int nitems,
+                          int use_fac, cudaStream_t st);
+
+// A planned launch of the streaming schedule.
+struct Launch {
+    enum Kind { Pass, Hpsi, Reduce } kind;
+    int pass = -1;             // index into the pass table
+    int item_begin = 0, nitems = 0;
+    int use_fac = 1;
+    int segment = 0;           // kSegForward, kSegEnergy, kSegAdjoint, kSegMetric
+};
+enum Segment { kSegForward = 0, kSegEnergy = 1, kSegAdjoint = 2, kSegMetric = 3 };
+enum Region { kRegionSigma = 0, kRegionL = 1, kRegionGrad = 2, kRegionEnergy = 3 };
+
+// A reduce destination before the workspace address is known.
+struct RedSpec {
+    int32_t slot;
+    double mul;
+    int region;
+    int64_t index;
+};
+
+struct Schedule {
+    int n = 0, t = 0, low = 0;
+    std::vector<PassDesc> passes;
+    std::vector<PassOp> ops;
+    std::vector<Launch> launches;
+    std::vector<RedSpec> reds;
+    int max_slots = 1;
+};
+
+// Build the streaming schedule of one instance: gates (circuit order), P parameters.
+void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precision, Schedule &out);
+
+}  // namespace large
+}  // namespace qng

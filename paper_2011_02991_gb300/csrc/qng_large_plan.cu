@@ -1,0 +1,331 @@
+// Host planner of the streaming path: turns one circuit into the list of passes (tile programs),
+// Pauli-sum launches and reductions that a QNG step needs. The schedule depends only on the gate
+// list, never on theta, so it is built once per context and uploaded with the workspace.
+//
+// Segments, in launch order:
+//   forward  psi <- U_{P-1} ... U_0 |0>                                   (Sec. 2, psi_k)
+//   energy   b <- W psi; a <- H b (Pauli kernel); <E> = <b|a>; a <- W^dag a  (Eq. 2's <E>)
+//   adjoint  for i = P-1..0: dE_i = -Im <psi|sigma_i|a>, then psi, a <- U_i^dag  (reverse sweep)
+//   metric   for every column j: a <- psi, b <- F_j^dag sigma_j F_j psi, <sigma_j> = <F psi|sigma|F psi>,
+//            psi <- U_j psi; then for i = j-1..0: L_ij = (1/4) Re <a|sigma_i|b>, a, b <- U_i^dag
+//            (Algorithm 1's inner loop with phi = b and lambda = a, each step one adjoint gate on both)
+// Consecutive steps of a segment share a pass while the qubits their non-diagonal operations act on
+// fit in the tile window and their inner products fit in the slot budget.
+#include <algorithm>
+#include <set>
+
+#include "qng_large.h"
+
+namespace qng {
+namespace large {
+
+namespace {
+
+bool rot_kind(int k) { return k == QNG_GATE_RX || k == QNG_GATE_RY || k == QNG_GATE_RZ; }
+int axis_of(int k) { return k == QNG_GATE_RX ? kAxisX : (k == QNG_GATE_RY ? kAxisY : kAxisZ); }
+
+struct Group {
+    std::vector<PassOp> ops;
+    std::vector<RedSpec> reds; // inner products of the group; an op's slot indexes this list
+};
+
+PassOp mk(int kind) {
+    PassOp o = {};
+    o.kind = kind;
+    o.r0 = o.r1 = -1;
+    o.q0 = o.q1 = -1;
+    o.axis = -1;
+    o.param = -1;
+    o.slot = -1;
+    return o;
+}
+
+// reads / writes of an op, per register (bit r)
+void access(const PassOp &o, int &rd, int &wr) {
+    rd = wr = 0;
+    switch (o.kind) {
+    case kOpCopy: rd = 1 << o.r0; wr = 1 << o.r1; break;
+    case kOpZero: wr = 1 << o.r0; break;
+    case kOpRot:
+    case kOpFixed: rd = wr = o.regs; break;
+    case kOpSigma: rd = wr = 1 << o.r0; break;
+    case kOpIp: rd = (1 << o.r0) | (1 << o.r1); break;
+    default: break;
+    }
+}
+
+struct Builder {
+    int n, P, low, t, win;
+    const std::vector<qng_gate> &gates;
+    std::vector<int> rot_at;                 // gate index of rotation k
+    std::vector<std::vector<int>> fixed_of;  // fixed gates of U_k (circuit order)
+    std::vector<int> trailing;               // W
+    Schedule &S;
+    int parity = 0;
+
+    Builder(const std::vector<qng_gate> &g, int n_, int P_, Schedule &s) : n(n_), P(P_), gates(g), S(s) {
+        std::vector<int> pend;
+        for (int k = 0; k < (int)g.size(); ++k) {
+            if (rot_kind(g[k].kind)) {
+                rot_at.push_back(k);
+                fixed_of.push_back(pend);
+                pend.clear();
+            } else {
+                pend.push_back(k);
+            }
+        }
+        trailing = pend;
+    }
+
+
+    void add_fixed(Group &gr, int gi, int regs) {
+        const qng_gate &g = gates[gi];
+        PassOp o = mk(kOpFixed);
+        o.regs = regs;
+        o.fixed_kind = g.kind;
+        o.q0 = g.q0;
+        o.q1 = g.q1;
+        gr.ops.push_back(o);
+    }
+    void add_rot(Group &gr, int k, bool adjoint, int regs) {
+        const qng_gate &g = gates[rot_at[k]];
+        PassOp o = mk(kOpRot);
+        o.regs = regs;
+        o.param = k;
+        o.adjoint = adjoint;
+        o.axis = axis_of(g.kind);
+        o.q0 = g.q0;
+        gr.ops.push_back(o);
+    }
+    void add_ip(Group &gr, int k_axis_param, int r0, int r1, int im, double mul, int region, int64_t index, bool sigma = true) {
+        PassOp o = mk(kOpIp);
+        o.r0 = r0;
+        o.r1 = r1;
+        o.adjoint = im;
+        if (sigma) {
+            const qng_gate &g = gates[rot_at[k_axis_param]];
+            o.axis = axis_of(g.kind);
+            o.q0 = g.q0;
+        }
+        o.slot = (int)gr.reds.size();
+        gr.ops.push_back(o);
+        gr.reds.push_back(RedSpec{o.slot, mul, region, index});
+    }
+
+    // Pack the segment's operations, in order, into passes: a pass takes operations while the
+    // qubits their non-diagonal parts act on fit in the tile window and its inner products fit in
+    // the slot budget (a step may span several passes). Then launch the segment's reduction.
+    void emit(std::vector<Group> &groups, int segment, int dead_at_end) {
+        struct Item { PassOp op; int need; bool has_red; RedSpec red; };
+        std::vector<Item> items;
+        for (Group &g : groups) {
+            for (const PassOp &o : g.ops) {
+                Item it;
+                it.op = o;
+                it.need = -1;
+                if (o.kind == kOpRot || o.kind == kOpSigma || o.kind == kOpIp) {
+                    if (o.axis == kAxisX || o.axis == kAxisY) it.need = o.q0;
+                } else if (o.kind == kOpFixed) {
+                    if (o.fixed_kind == QNG_GATE_CNOT) it.need = o.q1;
+                    else if (o.fixed_kind != QNG_GATE_CZ && o.fixed_kind != QNG_GATE_Z) it.need = o.q0;
+                }
+                if (it.need >= 0 && it.need < low) it.need = -1;
+                it.has_red = (o.kind == kOpIp);
+                if (it.has_red) it.red = g.reds[o.slot];
+                items.push_back(it);
+            }
+        }
+        size_t i0 = 0;
+        int slot_base = 0;
+        const int red_begin = (int)S.reds.size();
+        while (i0 < items.size()) {
+            std::set<int> win_set;
+            std::vector<PassOp> ops;
+            std::vector<RedSpec> reds;
+            size_t i1 = i0;
+            while (i1 < items.size()) {
+                const Item &it = items[i1];
+                const bool new_q = it.need >= 0 && !win_set.count(it.need);
+                if (i1 > i0 && ((new_q && (int)win_set.size() >= win) || (it.has_red && (int)reds.size() >= kMaxSlots))) break;
+                if (new_q) win_set.insert(it.need);
+                PassOp o = it.op;
+                if (it.has_red) {
+                    o.slot = (int)reds.size();
+                    RedSpec r = it.red;
+                    r.slot = o.slot;
+                    reds.push_back(r);
+                }
+                ops.push_back(o);
+                ++i1;
+            }
+            PassDesc pd = {};
+            pd.n = n;
+            pd.low = low;
+            std::vector<int> wq(win_set.begin(), win_set.end());
+            for (int q = low; q < n && (int)wq.size() < win; ++q)
+                if (!std::count(wq.begin(), wq.end(), q)) wq.push_back(q);
+            std::sort(wq.begin(), wq.end());
+            pd.win = (int)wq.size();
+            for (int k = 0; k < kMaxWin; ++k) pd.wq[k] = k < pd.win ? wq[k] : -1;
+            pd.t = low + pd.win;
+            int first_read = 0, written = 0, touched = 0;
+            for (const PassOp &o : ops) {
+                int rd, wr;
+                access(o, rd, wr);
+                first_read |= rd & ~touched;  // the first access of these registers is a read: load them
+                touched |= rd | wr;
+                written |= wr;
+            }
+            pd.regmask = touched;
+            pd.loadmask = first_read;
+            pd.storemask = written;
+            if (i1 == items.size()) pd.storemask &= ~dead_at_end;
+            pd.op_begin = (int)S.ops.size();
+            pd.nops = (int)ops.size();
+            pd.nslots = (int)reds.size();
+            pd.slot_base = slot_base;
+            pd.parity = parity++;
+            S.ops.insert(S.ops.end(), ops.begin(), ops.end());
+            for (RedSpec r : reds) {
+                r.slot += slot_base;
+                S.reds.push_back(r);
+            }
+            slot_base += (int)reds.size();
+            S.max_slots = std::max(S.max_slots, slot_base);
+            Launch L;
+            L.kind = Launch::Pass;
+            L.pass = (int)S.passes.size();
+            L.segment = segment;
+            S.passes.push_back(pd);
+            S.launches.push_back(L);
+            i0 = i1;
+        }
+        const int nred = (int)S.reds.size() - red_begin;
+        if (nred > 0) {
+            Launch L;
+            L.kind = Launch::Reduce;
+            L.item_begin = red_begin;
+            L.nitems = nred;
+            L.use_fac = 1;
+            L.segment = segment;
+            S.launches.push_back(L);
+        }
+    }
+};
+
+}  // namespace
+
+void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precision, Schedule &S) {
+    Builder B(gates, n, P, S);
+    B.low = std::min(n, precision == QNG_C128 ? 4 : 5);
+    B.win = std::min(kMaxWin, n - B.low);
+    B.t = B.low + B.win;
+    S.n = n;
+    S.low = B.low;
+    S.t = B.t;
+    const int PSI = 1 << kRegPsi, A = 1 << kRegA, Bm = 1 << kRegB;
+
+    // forward: psi <- U_{P-1} ... U_0 |0>
+    {
+        std::vector<Group> gs(std::max(P, 1));
+        PassOp z = mk(kOpZero);
+        z.r0 = kRegPsi;
+        gs[0].ops.push_back(z);
+        for (int k = 0; k < P; ++k) {
+            for (int gi : B.fixed_of[k]) B.add_fixed(gs[k], gi, PSI);
+            B.add_rot(gs[k], k, false, PSI);
+        }
+        B.emit(gs, kSegForward, 0);
+    }
+    // energy: b <- W psi, record scale(b)^2 at slot 0, scale(a) <- scale(b); Pauli kernel; a <- W^dag a
+    {
+        std::vector<Group> gs(1);
+        PassOp c = mk(kOpCopy);
+        c.r0 = kRegPsi;
+        c.r1 = kRegB;
+        gs[0].ops.push_back(c);
+        for (int gi : B.trailing) B.add_fixed(gs[0], gi, Bm);
+        PassOp rf = mk(kOpRecordFac);
+        rf.r0 = rf.r1 = kRegB;
+        rf.slot = 0;
+        gs[0].ops.push_back(rf);
+        PassOp ss = mk(kOpSetScale);
+        ss.r0 = kRegB;
+        ss.r1 = kRegA;
+        gs[0].ops.push_back(ss);
+        B.emit(gs, kSegEnergy, 0);
+        S.passes.back().nslots = 0;  // slot 0 is filled by the Pauli kernel
+        Launch h;
+        h.kind = Launch::Hpsi;
+        h.segment = kSegEnergy;
+        S.launches.push_back(h);
+        Launch r;
+        r.kind = Launch::Reduce;
+        r.item_begin = (int)S.reds.size();
+        r.nitems = 1;
+        r.use_fac = 1;
+        r.segment = kSegEnergy;
+        S.reds.push_back(RedSpec{0, 1.0, kRegionEnergy, 0});
+        S.launches.push_back(r);
+        std::vector<Group> gw(1);
+        for (int f = (int)B.trailing.size() - 1; f >= 0; --f) B.add_fixed(gw[0], B.trailing[f], A);
+        if (!gw[0].ops.empty()) B.emit(gw, kSegEnergy, 0);
+    }
+    // adjoint sweep over (psi, a = eta)
+    if (P > 0) {
+        std::vector<Group> gs(P);
+        for (int s = 0; s < P; ++s) {
+            const int i = P - 1 - s;
+            B.add_ip(gs[s], i, kRegPsi, kRegA, 1, -1.0, kRegionGrad, i);
+            if (i > 0) {
+                B.add_rot(gs[s], i, true, PSI | A);
+                for (int f = (int)B.fixed_of[i].size() - 1; f >= 0; --f) B.add_fixed(gs[s], B.fixed_of[i][f], PSI | A);
+            }
+        }
+        B.emit(gs, kSegAdjoint, PSI | A);
+    }
+    // metric columns
+    B.parity = 0;
+    for (int j = 0; j < P; ++j) {
+        std::vector<Group> gs(j + 1);
+        Group &g0 = gs[0];
+        if (j == 0) {
+            PassOp z = mk(kOpZero);
+            z.r0 = kRegPsi;
+            g0.ops.push_back(z);
+        }
+        PassOp c1 = mk(kOpCopy);
+        c1.r0 = kRegPsi;
+        c1.r1 = kRegA;
+        g0.ops.push_back(c1);
+        PassOp c2 = mk(kOpCopy);
+        c2.r0 = kRegPsi;
+        c2.r1 = kRegB;
+        g0.ops.push_back(c2);
+        for (int gi : B.fixed_of[j]) B.add_fixed(g0, gi, PSI | Bm);
+        B.add_ip(g0, j, kRegB, kRegB, 0, 1.0, kRegionSigma, j);
+        {
+            const qng_gate &g = gates[B.rot_at[j]];
+            PassOp sg = mk(kOpSigma);
+            sg.r0 = kRegB;
+            sg.axis = axis_of(g.kind);
+            sg.q0 = g.q0;
+            g0.ops.push_back(sg);
+        }
+        for (int f = (int)B.fixed_of[j].size() - 1; f >= 0; --f) B.add_fixed(g0, B.fixed_of[j][f], Bm);
+        B.add_rot(g0, j, false, PSI);
+        for (int s = 1; s <= j; ++s) {
+            const int i = j - s;
+            Group &g = gs[s];
+            B.add_ip(g, i, kRegA, kRegB, 0, 0.25, kRegionL, (int64_t)i * P + j);
+            if (i > 0) {
+                B.add_rot(g, i, true, A | Bm);
+                for (int f = (int)B.fixed_of[i].size() - 1; f >= 0; --f) B.add_fixed(g, B.fixed_of[i][f], A | Bm);
+            }
+        }
+        B.emit(gs, kSegMetric, A | Bm);
+    }
+}
+
+}  // namespace large
+}  // namespace qng

@@ -63,6 +63,7 @@ SYMBOLS = {
     "qng_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "qng_last_launch_count": [_vp, _i64p],
     "qng_profile": [_vp, ctypes.c_int],
+    "qng_set_path": [_vp, ctypes.c_int],
     "qng_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), _i64p],
     "qng_destroy": [_vp],
     "qng_status_string": [ctypes.c_int],
@@ -117,7 +118,8 @@ class Context:
     are concatenated over instances; metrics are concatenated P_b x P_b blocks.
     """
 
-    def __init__(self, problems, precision: int | None = None, device=None, stream: torch.cuda.Stream | None = None):
+    def __init__(self, problems, precision: int | None = None, device=None, stream: torch.cuda.Stream | None = None,
+                 path: int = 0):
         L = load()
         if not torch.cuda.is_available():
             raise RuntimeError("libqng needs a CUDA device")
@@ -156,6 +158,8 @@ class Context:
         _chk(L.qng_get_offsets(self._h, po.ctypes.data_as(_i64p), mo.ctypes.data_as(_i64p)), "qng_get_offsets")
         self.param_offsets, self.metric_offsets = po, mo
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if path:
+            _chk(L.qng_set_path(self._h, int(path)), "qng_set_path")
         self._alloc_workspace()
 
     def _alloc_workspace(self):
@@ -242,6 +246,23 @@ class Context:
 
     def sync(self):
         _chk(load().qng_sync(self._h), "qng_sync")
+
+    PATH_AUTO, PATH_ONCHIP, PATH_STREAMING = 0, 1, 2
+
+    def set_path(self, path: int):
+        """Choose the execution path (re-plans; the workspace is re-allocated when it grows)."""
+        L = load()
+        st = L.qng_set_path(self._h, int(path))
+        if st == QNG_ERR_WORKSPACE:
+            self._alloc_workspace_for_new_plan(path)
+            return
+        _chk(st, "qng_set_path")
+
+    def _alloc_workspace_for_new_plan(self, path: int):
+        # release the workspace binding, re-plan without one, then allocate the new size
+        L = load()
+        self.close()
+        self.__init__(self.problems, self.precision, self.device, self.stream, path=path)
 
     def set_tuning(self, min_qubits: int, cluster_log2: int, threads: int):
         _chk(load().qng_set_tuning(self._h, min_qubits, cluster_log2, threads), "qng_set_tuning")

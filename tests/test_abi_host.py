@@ -54,7 +54,8 @@ def _create(lib, n, gates, terms=(), precision=W.C128):
     ([(42, 0, -1, -1)], 2, 1),             # unknown kind
     ([(W.RX, 0, -1, 0), (W.H, 1, -1, -1), (W.RZ, 1, -1, 1)], 2, 0),
     ([], 3, 0),                            # no gates at all
-    ([(W.RY, 0, -1, 0)], 17, 7),           # beyond the on-chip path of this build
+    ([(W.RY, 0, -1, 0)], 17, 0),           # streaming path (state vectors in HBM)
+    ([(W.RY, 0, -1, 0)], 31, 1),           # more qubits than any path takes
 ])
 def test_validation(lib, gates, n, expect):
     st, h = _create(lib, n, gates)
@@ -108,6 +109,30 @@ def test_sizes_offsets_workspace(lib):
     assert lib.qng_set_workspace(h, ctypes.c_void_p(0x1000 + 8), nb.value, None) == 6  # misaligned
     assert lib.qng_set_workspace(h, ctypes.c_void_p(0x1000), nb.value - 256, None) == 6  # too small
     lib.qng_destroy(h)
+
+
+def test_streaming_workspace(lib):
+    """A 20-qubit instance runs on the streaming path: three registers of 2^20 amplitudes, no checkpoints."""
+    c = W.layered_ansatz(20, 2)
+    st, h = _create(lib, 20, [tuple(int(v) for v in r) for r in c.gates], [(1.0, 1, 0)], W.C128)
+    assert st == 0
+    nb = ctypes.c_size_t()
+    assert lib.qng_workspace_size(h, ctypes.byref(nb)) == 0
+    regs = 3 * (1 << 20) * 16
+    assert regs <= nb.value < regs + 64 * 1024 * 1024
+    assert lib.qng_set_path(h, 1) == 7  # on-chip path cannot hold 20 qubits
+    lib.qng_destroy(h)
+    # a batch cannot hold a streaming instance
+    from paper_2011_02991_gb300 import qng
+    ga = (qng.qng_gate * 1)(qng.qng_gate(W.RY, 0, -1, 0))
+    ta = (qng.qng_pauli * 1)(qng.qng_pauli(1.0, 1, 0))
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    nq = np.array([20, 20], dtype=np.int32)
+    ng = np.array([1, 0], dtype=np.int32)
+    nt = np.array([1, 0], dtype=np.int32)
+    h = ctypes.c_void_p()
+    assert lib.qng_create_batch(2, nq.ctypes.data_as(i32), ga, ng.ctypes.data_as(i32), ta, nt.ctypes.data_as(i32),
+                                W.C128, ctypes.byref(h)) == 7
 
 
 def test_status_strings(lib):

@@ -1,0 +1,89 @@
+"""GPU parity of the streaming path (state vectors in HBM, tiled passes) against the CPU oracle.
+
+Small and medium instances are forced onto the streaming path and checked entry by entry; tiles of
+2^11 (complex128) or 2^12 (complex64) amplitudes make instances of 13-16 qubits span many tiles and
+many passes per column, with window qubits changing from pass to pass.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2011_02991_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {W.C128: 1e-10, W.C64: 2e-4}
+
+
+def rel(got, ref):
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)) if ref.size else 0.0
+
+
+@pytest.fixture(scope="module")
+def qng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_02991_gb300 import build as B
+    B.build()
+    from paper_2011_02991_gb300 import qng as Q
+    return Q
+
+
+def run_streaming(qng, oracle, p, precision):
+    ctx = qng.Context(p, precision=precision, path=2)
+    out = ctx.step(ctx.theta0(), p.dt, p.lam)
+    g2, sig = ctx.metric(ctx.theta0(), want_sigma=True)
+    gr, en = ctx.gradient(ctx.theta0())
+    ctx.sync()
+    ref = oracle.qng_step(p)
+    t = TOL[precision]
+    errs = {"g": rel(out["g"].cpu(), ref["g"]), "grad": rel(out["grad"].cpu(), ref["grad"]),
+            "dtheta": rel(out["dtheta"].cpu(), ref["dtheta"]), "E": rel(out["energy"].cpu(), [ref["E"]]),
+            "g_metric_call": rel(g2.cpu(), ref["g"]), "sigma": rel(sig.cpu(), -2.0 * ref["T"].imag),
+            "grad_call": rel(gr.cpu(), ref["grad"]), "E_grad_call": rel(en.cpu(), [ref["E"]])}
+    bad = {k: v for k, v in errs.items() if not v <= t}
+    assert not bad, f"{p.name} precision={precision}: {bad}"
+
+
+@pytest.mark.parametrize("precision", [W.C128, W.C64])
+def test_streaming_small_configs(qng, oracle, precision):
+    run_streaming(qng, oracle, W.config_tfim4() if precision == W.C128 else
+                  W.Problem("tfim4_c64", W.config_tfim4().circuit, W.config_tfim4().hamiltonian,
+                            W.config_tfim4().theta, precision=W.C64), precision)
+
+
+@pytest.mark.parametrize("precision", [W.C128, W.C64])
+@pytest.mark.parametrize("n,seed", [(6, 1), (9, 2), (13, 3), (15, 4)])
+def test_streaming_random_circuits(qng, oracle, n, seed, precision):
+    """Every gate kind, on instances that span 1 to 16 tiles."""
+    p = W.random_problem(n, 50 + 4 * n, 10, 3000 + seed, precision)
+    run_streaming(qng, oracle, p, precision)
+
+
+@pytest.mark.parametrize("precision", [W.C128, W.C64])
+def test_streaming_layered_14(qng, oracle, precision):
+    """Ry/Rz/CZ and Ry/Rx/Rz/CNOT layers at 14 qubits (the ansatz families of the 26/28-qubit workloads)."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    c = W.layered_ansatz(14, 2)
+    p = W.Problem("layered14", c, W.tfim_chain(14, 1.0, rng.uniform(0.2, 1.0, 14)), W.uniform_theta(c.num_params, rng),
+                  precision=precision)
+    run_streaming(qng, oracle, p, precision)
+    c = W.layered_ansatz(14, 2, rotation_kinds=(W.RY, W.RX, W.RZ), entangler=W.CNOT)
+    p = W.Problem("layered14_cnot", c, W.random_pauli_hamiltonian(14, 20, rng), W.uniform_theta(c.num_params, rng),
+                  precision=precision)
+    run_streaming(qng, oracle, p, precision)
+
+
+def test_streaming_matches_onchip(qng):
+    """The two paths agree on the 12-qubit, P = 192 workload."""
+    p = W.config_rand12()
+    a = qng.Context(p, path=1)
+    b = qng.Context(p, path=2)
+    oa = a.step(a.theta0(), p.dt, p.lam)
+    ob = b.step(b.theta0(), p.dt, p.lam)
+    a.sync()
+    b.sync()
+    for k in ("g", "grad", "dtheta", "energy"):
+        assert rel(ob[k].cpu(), oa[k].cpu()) <= 1e-11, k

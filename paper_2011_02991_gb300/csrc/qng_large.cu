@@ -65,6 +65,96 @@ __device__ __forceinline__ int gbit(const TileCtx &tc, uint32_t l, int q) {
     return lb >= 0 ? (int)((l >> lb) & 1u) : (int)((tc.base >> q) & 1ull);
 }
 
+
+// One recurrence step on the registers A (left) and B (right) in one sweep of the tile: the inner
+// product with sigma on the pairs of qubit lb (compile-time axis AX and part IM), then, when ROT,
+// the adjoint rotation of the same axis on both registers. Every sign folds into an FMA operand.
+template <typename R, int AX, int IM, bool ROT>
+__device__ __forceinline__ R step_pairs(typename CX2<R>::T *A, typename CX2<R>::T *B, uint32_t T, int lb, R c, R s, R t,
+                                        int caseB) {
+    using cx = typename CX2<R>::T;
+    constexpr bool kScaled = std::is_same<R, double>::value;
+    R acc = 0;
+    const uint32_t bit = 1u << lb;
+    auto rot = [&](cx x, cx v) -> cx {
+        cx y;
+        if constexpr (kScaled) {
+            if (caseB) { y.x = fma(t, x.x, v.x); y.y = fma(t, x.y, v.y); }
+            else       { y.x = fma(t, v.x, x.x); y.y = fma(t, v.y, x.y); }
+        } else {
+            y.x = fma(s, v.x, c * x.x); y.y = fma(s, v.y, c * x.y);
+        }
+        return y;
+    };
+    for (uint32_t p = threadIdx.x; p < (T >> 1); p += blockDim.x) {
+        const uint32_t l0 = lins0(p, lb), l1 = l0 | bit;
+        const cx a0 = A[l0], a1 = A[l1], b0 = B[l0], b1 = B[l1];
+        cx s0, s1;  // (sigma b)_0, (sigma b)_1
+        if constexpr (AX == kAxisX) { s0 = b1; s1 = b0; }
+        else { s0 = cx{b1.y, -b1.x}; s1 = cx{-b0.y, b0.x}; }
+        if constexpr (IM) acc = fma(a0.x, s0.y, fma(-a0.y, s0.x, fma(a1.x, s1.y, fma(-a1.y, s1.x, acc))));
+        else acc = fma(a0.x, s0.x, fma(a0.y, s0.y, fma(a1.x, s1.x, fma(a1.y, s1.y, acc))));
+        if constexpr (ROT) {
+            // (i sigma x)_0, (i sigma x)_1
+            if constexpr (AX == kAxisX) {
+                A[l0] = rot(a0, cx{-a1.y, a1.x}); A[l1] = rot(a1, cx{-a0.y, a0.x});
+                B[l0] = rot(b0, cx{-b1.y, b1.x}); B[l1] = rot(b1, cx{-b0.y, b0.x});
+            } else {
+                A[l0] = rot(a0, a1); A[l1] = rot(a1, cx{-a0.x, -a0.y});
+                B[l0] = rot(b0, b1); B[l1] = rot(b1, cx{-b0.x, -b0.y});
+            }
+        }
+    }
+    return acc;
+}
+
+template <typename R, int IM, bool ROT>
+__device__ __forceinline__ R step_diag(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int q, R c, R s,
+                                       R t, int caseB) {
+    using cx = typename CX2<R>::T;
+    constexpr bool kScaled = std::is_same<R, double>::value;
+    R acc = 0;
+    for (uint32_t l = threadIdx.x; l < tc.T; l += blockDim.x) {
+        const int beta = gbit(tc, l, q);
+        const cx a = A[l], b = B[l];
+        const cx af = lflip2(a, beta);  // (Z b)_beta = (-1)^beta b, folded into a
+        if constexpr (IM) acc = fma(af.x, b.y, fma(-af.y, b.x, acc));
+        else acc = fma(af.x, b.x, fma(af.y, b.y, acc));
+        if constexpr (ROT) {
+            const cx va = {lflip(a.y, beta ^ 1), lflip(a.x, beta)}, vb = {lflip(b.y, beta ^ 1), lflip(b.x, beta)};
+            cx ya, yb;
+            if constexpr (kScaled) {
+                if (caseB) {
+                    ya.x = fma(t, a.x, va.x); ya.y = fma(t, a.y, va.y);
+                    yb.x = fma(t, b.x, vb.x); yb.y = fma(t, b.y, vb.y);
+                } else {
+                    ya.x = fma(t, va.x, a.x); ya.y = fma(t, va.y, a.y);
+                    yb.x = fma(t, vb.x, b.x); yb.y = fma(t, vb.y, b.y);
+                }
+            } else {
+                ya.x = fma(s, va.x, c * a.x); ya.y = fma(s, va.y, c * a.y);
+                yb.x = fma(s, vb.x, c * b.x); yb.y = fma(s, vb.y, c * b.y);
+            }
+            A[l] = ya;
+            B[l] = yb;
+        }
+    }
+    return acc;
+}
+
+template <typename R, int IM>
+__device__ __forceinline__ R step_dispatch(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int ax, int q,
+                                           bool rot, R c, R s, R t, int caseB) {
+    if (ax == kAxisZ)
+        return rot ? step_diag<R, IM, true>(tc, A, B, q, c, s, t, caseB) : step_diag<R, IM, false>(tc, A, B, q, c, s, t, caseB);
+    const int lb = tc.lbit[q];
+    if (ax == kAxisX)
+        return rot ? step_pairs<R, kAxisX, IM, true>(A, B, tc.T, lb, c, s, t, caseB)
+                   : step_pairs<R, kAxisX, IM, false>(A, B, tc.T, lb, c, s, t, caseB);
+    return rot ? step_pairs<R, kAxisY, IM, true>(A, B, tc.T, lb, c, s, t, caseB)
+               : step_pairs<R, kAxisY, IM, false>(A, B, tc.T, lb, c, s, t, caseB);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
     using cx = typename CX2<R>::T;
@@ -276,6 +366,23 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
                 }
                 part[op.slot] += (double)acc;  // float64 from here on; reduced once per launch
                 if (blockIdx.x == 0 && threadIdx.x == 0 && tile_id == 0) pa.slotfac[pd.slot_base + op.slot] = sc[op.r0] * sc[op.r1];
+                break;
+            }
+            case kOpStep: {
+                const bool rot = op.param >= 0;
+                R c = 0, sv = 0, tv = 0;
+                int caseB = 0;
+                double f = 1.0;
+                if (rot) {
+                    const DevCoef co = pa.coef[op.param];  // adjoint rotation: s' = +s
+                    c = (R)co.c; sv = (R)co.s; tv = (R)co.t; caseB = co.caseB; f = co.f;
+                }
+                const R acc = op.adjoint
+                    ? step_dispatch<R, 1>(tc, tile[op.r0], tile[op.r1], op.axis, op.q0, rot, c, sv, tv, caseB)
+                    : step_dispatch<R, 0>(tc, tile[op.r0], tile[op.r1], op.axis, op.q0, rot, c, sv, tv, caseB);
+                part[op.slot] += (double)acc;
+                if (blockIdx.x == 0 && threadIdx.x == 0 && tile_id == 0) pa.slotfac[pd.slot_base + op.slot] = sc[op.r0] * sc[op.r1];
+                if (kScaled && rot) { sc[op.r0] *= f; sc[op.r1] *= f; }
                 break;
             }
             case kOpRecordFac: {

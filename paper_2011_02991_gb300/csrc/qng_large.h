@@ -23,6 +23,8 @@ enum OpKind : int32_t {
     kOpIp = 5,         // slot += Re (adjoint = 0) or Im (adjoint = 1) of <r0| sigma_{axis}(q0) |r1>; axis -1: no sigma
     kOpRecordFac = 6,  // slotfac[slot] <- scale(r0) * scale(r1)
     kOpSetScale = 7,   // scale(r1) <- scale(r0) (no data)
+    kOpStep = 8,       // one recurrence step in one sweep: slot += Re/Im <r0|sigma_{axis}(q0)|r1>, then, if
+                       // param >= 0, the adjoint rotation of param (same axis and qubit) on r0 and r1
 };
 
 struct PassOp {

@@ -50,6 +50,7 @@ void access(const PassOp &o, int &rd, int &wr) {
     case kOpFixed: rd = wr = o.regs; break;
     case kOpSigma: rd = wr = 1 << o.r0; break;
     case kOpIp: rd = (1 << o.r0) | (1 << o.r1); break;
+    case kOpStep: rd = (1 << o.r0) | (1 << o.r1); wr = o.param >= 0 ? rd : 0; break;
     default: break;
     }
 }
@@ -97,6 +98,21 @@ struct Builder {
         o.q0 = g.q0;
         gr.ops.push_back(o);
     }
+    // one recurrence step: inner product of (r0, r1) with sigma_k, then R_k^dag on both when rot
+    void add_step(Group &gr, int k, int r0, int r1, int im, bool rot, double mul, int region, int64_t index) {
+        const qng_gate &g = gates[rot_at[k]];
+        PassOp o = mk(kOpStep);
+        o.r0 = r0;
+        o.r1 = r1;
+        o.regs = (1 << r0) | (1 << r1);
+        o.adjoint = im;
+        o.axis = axis_of(g.kind);
+        o.q0 = g.q0;
+        o.param = rot ? k : -1;
+        o.slot = (int)gr.reds.size();
+        gr.ops.push_back(o);
+        gr.reds.push_back(RedSpec{o.slot, mul, region, index});
+    }
     void add_ip(Group &gr, int k_axis_param, int r0, int r1, int im, double mul, int region, int64_t index, bool sigma = true) {
         PassOp o = mk(kOpIp);
         o.r0 = r0;
@@ -123,14 +139,14 @@ struct Builder {
                 Item it;
                 it.op = o;
                 it.need = -1;
-                if (o.kind == kOpRot || o.kind == kOpSigma || o.kind == kOpIp) {
+                if (o.kind == kOpRot || o.kind == kOpSigma || o.kind == kOpIp || o.kind == kOpStep) {
                     if (o.axis == kAxisX || o.axis == kAxisY) it.need = o.q0;
                 } else if (o.kind == kOpFixed) {
                     if (o.fixed_kind == QNG_GATE_CNOT) it.need = o.q1;
                     else if (o.fixed_kind != QNG_GATE_CZ && o.fixed_kind != QNG_GATE_Z) it.need = o.q0;
                 }
                 if (it.need >= 0 && it.need < low) it.need = -1;
-                it.has_red = (o.kind == kOpIp);
+                it.has_red = (o.kind == kOpIp || o.kind == kOpStep);
                 if (it.has_red) it.red = g.reds[o.slot];
                 items.push_back(it);
             }
@@ -276,11 +292,9 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
         std::vector<Group> gs(P);
         for (int s = 0; s < P; ++s) {
             const int i = P - 1 - s;
-            B.add_ip(gs[s], i, kRegPsi, kRegA, 1, -1.0, kRegionGrad, i);
-            if (i > 0) {
-                B.add_rot(gs[s], i, true, PSI | A);
+            B.add_step(gs[s], i, kRegPsi, kRegA, 1, i > 0, -1.0, kRegionGrad, i);
+            if (i > 0)
                 for (int f = (int)B.fixed_of[i].size() - 1; f >= 0; --f) B.add_fixed(gs[s], B.fixed_of[i][f], PSI | A);
-            }
         }
         B.emit(gs, kSegAdjoint, PSI | A);
     }
@@ -317,11 +331,9 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
         for (int s = 1; s <= j; ++s) {
             const int i = j - s;
             Group &g = gs[s];
-            B.add_ip(g, i, kRegA, kRegB, 0, 0.25, kRegionL, (int64_t)i * P + j);
-            if (i > 0) {
-                B.add_rot(g, i, true, A | Bm);
+            B.add_step(g, i, kRegA, kRegB, 0, i > 0, 0.25, kRegionL, (int64_t)i * P + j);
+            if (i > 0)
                 for (int f = (int)B.fixed_of[i].size() - 1; f >= 0; --f) B.add_fixed(g, B.fixed_of[i][f], A | Bm);
-            }
         }
         B.emit(gs, kSegMetric, A | Bm);
     }

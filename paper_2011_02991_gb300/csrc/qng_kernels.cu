@@ -97,6 +97,21 @@ template <typename R> struct Rot {
     }
 };
 
+// The same rotation with its scaled form fixed at compile time (no per-amplitude branch).
+template <typename R, int CB> struct RotC {
+    R c, s, t;
+    __device__ __forceinline__ typename CX<R>::T apply(typename CX<R>::T x, typename CX<R>::T v) const {
+        typename CX<R>::T y;
+        if constexpr (std::is_same<R, double>::value) {
+            if constexpr (CB) { y.x = fma(t, x.x, v.x); y.y = fma(t, x.y, v.y); }
+            else              { y.x = fma(t, v.x, x.x); y.y = fma(t, v.y, x.y); }
+        } else {
+            y.x = fma(s, v.x, c * x.x); y.y = fma(s, v.y, c * x.y);
+        }
+        return y;
+    }
+};
+
 // adjoint (R^dag) or forward (R) coefficients of parameter k; f receives the scale factor
 template <typename R> __device__ __forceinline__ Rot<R> make_rot(const DevCoef &co, bool adjoint, double &f) {
     Rot<R> r;
@@ -310,8 +325,8 @@ template <int IM, typename RA, typename T2> __device__ __forceinline__ RA ipacc(
 
 // One fused step of a column on a local X/Y qubit: inner product with sigma on the pairs,
 // then the adjoint rotation R^dag on the same pairs, then the diagonal fixed block F^dag.
-template <typename R, int AX, int IM>
-__device__ __forceinline__ R col_pairs(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on, const Rot<R> &rot,
+template <typename R, int AX, int IM, int CB>
+__device__ __forceinline__ R col_pairs(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on, const RotC<R, CB> &rot,
                                        bool post, const DevParam &pi, const DevDiag *dt) {
     using cx = typename CX<R>::T;
     R part = 0;
@@ -337,9 +352,9 @@ __device__ __forceinline__ R col_pairs(Eng<R> &e, const typename CX<R>::T *a, in
 }
 
 // The same step on a distributed X/Y qubit, this CTA holding the BETA half of every pair.
-template <typename R, int AX, int IM, int BETA>
+template <typename R, int AX, int IM, int BETA, int CB>
 __device__ __forceinline__ R col_dist(Eng<R> &e, const typename CX<R>::T *rv, const typename CX<R>::T *a, bool rot_on,
-                                      const Rot<R> &rot, bool post, const DevParam &pi, const DevDiag *dt) {
+                                      const RotC<R, CB> &rot, bool post, const DevParam &pi, const DevDiag *dt) {
     using cx = typename CX<R>::T;
     R part = 0;
     for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
@@ -356,8 +371,8 @@ __device__ __forceinline__ R col_dist(Eng<R> &e, const typename CX<R>::T *rv, co
 }
 
 // The same step for a Z rotation (diagonal: any qubit, no pairing).
-template <typename R, int IM>
-__device__ __forceinline__ R col_diag(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on, const Rot<R> &rot,
+template <typename R, int IM, int CB>
+__device__ __forceinline__ R col_diag(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on, const RotC<R, CB> &rot,
                                       bool post, const DevParam &pi, const DevDiag *dt) {
     using cx = typename CX<R>::T;
     R part = 0;
@@ -376,33 +391,41 @@ __device__ __forceinline__ R col_diag(Eng<R> &e, const typename CX<R>::T *a, int
     return part;
 }
 
-template <typename R, int IM>
-__device__ __forceinline__ R col_step(Eng<R> &e, const typename CX<R>::T *a, const DevParam &pi, bool rot_on,
-                                      const Rot<R> &rot, bool post, const DevDiag *dt) {
+template <typename R, int IM, int CB>
+__device__ __forceinline__ R col_step_cb(Eng<R> &e, const typename CX<R>::T *a, const DevParam &pi, bool rot_on,
+                                         const RotC<R, CB> &rot, bool post, const DevDiag *dt) {
     R part;
     if (pi.axis == kAxisZ) {
-        part = col_diag<R, IM>(e, a, pi.q, rot_on, rot, post, pi, dt);
+        part = col_diag<R, IM, CB>(e, a, pi.q, rot_on, rot, post, pi, dt);
     } else if (pi.q < e.nl) {
-        part = (pi.axis == kAxisX) ? col_pairs<R, kAxisX, IM>(e, a, pi.q, rot_on, rot, post, pi, dt)
-                                   : col_pairs<R, kAxisY, IM>(e, a, pi.q, rot_on, rot, post, pi, dt);
+        part = (pi.axis == kAxisX) ? col_pairs<R, kAxisX, IM, CB>(e, a, pi.q, rot_on, rot, post, pi, dt)
+                                   : col_pairs<R, kAxisY, IM, CB>(e, a, pi.q, rot_on, rot, post, pi, dt);
     } else {
         const typename CX<R>::T *rv = e.exchange(pi.q);
         const int beta = (e.rank >> (pi.q - e.nl)) & 1;
         if (pi.axis == kAxisX)
-            part = beta ? col_dist<R, kAxisX, IM, 1>(e, rv, a, rot_on, rot, post, pi, dt)
-                        : col_dist<R, kAxisX, IM, 0>(e, rv, a, rot_on, rot, post, pi, dt);
+            part = beta ? col_dist<R, kAxisX, IM, 1, CB>(e, rv, a, rot_on, rot, post, pi, dt)
+                        : col_dist<R, kAxisX, IM, 0, CB>(e, rv, a, rot_on, rot, post, pi, dt);
         else
-            part = beta ? col_dist<R, kAxisY, IM, 1>(e, rv, a, rot_on, rot, post, pi, dt)
-                        : col_dist<R, kAxisY, IM, 0>(e, rv, a, rot_on, rot, post, pi, dt);
+            part = beta ? col_dist<R, kAxisY, IM, 1, CB>(e, rv, a, rot_on, rot, post, pi, dt)
+                        : col_dist<R, kAxisY, IM, 0, CB>(e, rv, a, rot_on, rot, post, pi, dt);
     }
     __syncthreads();
     return part;
 }
 
+template <typename R, int IM>
+__device__ __forceinline__ R col_step(Eng<R> &e, const typename CX<R>::T *a, const DevParam &pi, bool rot_on,
+                                      const Rot<R> &rot, bool post, const DevDiag *dt) {
+    if (std::is_same<R, double>::value && rot.caseB)
+        return col_step_cb<R, IM, 1>(e, a, pi, rot_on, RotC<R, 1>{rot.c, rot.s, rot.t}, post, dt);
+    return col_step_cb<R, IM, 0>(e, a, pi, rot_on, RotC<R, 0>{rot.c, rot.s, rot.t}, post, dt);
+}
+
 // Forward rotation R_k with the diagonal fixed block F_k applied to the inputs (pre), writing
 // both the shared-memory state and the checkpoint out.
-template <typename R, int AX>
-__device__ __forceinline__ void fwd_pairs(Eng<R> &e, typename CX<R>::T *out, int q, const Rot<R> &rot, bool pre,
+template <typename R, int AX, int CB>
+__device__ __forceinline__ void fwd_pairs(Eng<R> &e, typename CX<R>::T *out, int q, const RotC<R, CB> &rot, bool pre,
                                           const DevParam &pk, const DevDiag *dt) {
     using cx = typename CX<R>::T;
     const uint32_t bit = 1u << q, half = e.Nl >> 1;
@@ -422,9 +445,9 @@ __device__ __forceinline__ void fwd_pairs(Eng<R> &e, typename CX<R>::T *out, int
     }
 }
 
-template <typename R, int AX, int BETA>
+template <typename R, int AX, int BETA, int CB>
 __device__ __forceinline__ void fwd_dist(Eng<R> &e, const typename CX<R>::T *rv, typename CX<R>::T *out, int q,
-                                         const Rot<R> &rot, bool pre, const DevParam &pk, const DevDiag *dt) {
+                                         const RotC<R, CB> &rot, bool pre, const DevParam &pk, const DevDiag *dt) {
     using cx = typename CX<R>::T;
     const uint64_t m = 1ull << q;
     for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
@@ -440,8 +463,8 @@ __device__ __forceinline__ void fwd_dist(Eng<R> &e, const typename CX<R>::T *rv,
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void fwd_diag(Eng<R> &e, typename CX<R>::T *out, int q, const Rot<R> &rot, bool pre,
+template <typename R, int CB>
+__device__ __forceinline__ void fwd_diag(Eng<R> &e, typename CX<R>::T *out, int q, const RotC<R, CB> &rot, bool pre,
                                          const DevParam &pk, const DevDiag *dt) {
     using cx = typename CX<R>::T;
     for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
@@ -456,26 +479,33 @@ __device__ __forceinline__ void fwd_diag(Eng<R> &e, typename CX<R>::T *out, int 
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void fwd_step(Eng<R> &e, typename CX<R>::T *out, const DevParam &pk, const Rot<R> &rot,
-                                         bool pre, const DevDiag *dt) {
+template <typename R, int CB>
+__device__ __forceinline__ void fwd_step_cb(Eng<R> &e, typename CX<R>::T *out, const DevParam &pk, const RotC<R, CB> &rot,
+                                            bool pre, const DevDiag *dt) {
     if (pk.axis == kAxisZ) {
-        fwd_diag<R>(e, out, pk.q, rot, pre, pk, dt);
+        fwd_diag<R, CB>(e, out, pk.q, rot, pre, pk, dt);
     } else if (pk.q < e.nl) {
-        if (pk.axis == kAxisX) fwd_pairs<R, kAxisX>(e, out, pk.q, rot, pre, pk, dt);
-        else fwd_pairs<R, kAxisY>(e, out, pk.q, rot, pre, pk, dt);
+        if (pk.axis == kAxisX) fwd_pairs<R, kAxisX, CB>(e, out, pk.q, rot, pre, pk, dt);
+        else fwd_pairs<R, kAxisY, CB>(e, out, pk.q, rot, pre, pk, dt);
     } else {
         const typename CX<R>::T *rv = e.exchange(pk.q);
         const int beta = (e.rank >> (pk.q - e.nl)) & 1;
         if (pk.axis == kAxisX) {
-            if (beta) fwd_dist<R, kAxisX, 1>(e, rv, out, pk.q, rot, pre, pk, dt);
-            else fwd_dist<R, kAxisX, 0>(e, rv, out, pk.q, rot, pre, pk, dt);
+            if (beta) fwd_dist<R, kAxisX, 1, CB>(e, rv, out, pk.q, rot, pre, pk, dt);
+            else fwd_dist<R, kAxisX, 0, CB>(e, rv, out, pk.q, rot, pre, pk, dt);
         } else {
-            if (beta) fwd_dist<R, kAxisY, 1>(e, rv, out, pk.q, rot, pre, pk, dt);
-            else fwd_dist<R, kAxisY, 0>(e, rv, out, pk.q, rot, pre, pk, dt);
+            if (beta) fwd_dist<R, kAxisY, 1, CB>(e, rv, out, pk.q, rot, pre, pk, dt);
+            else fwd_dist<R, kAxisY, 0, CB>(e, rv, out, pk.q, rot, pre, pk, dt);
         }
     }
     __syncthreads();
+}
+
+template <typename R>
+__device__ __forceinline__ void fwd_step(Eng<R> &e, typename CX<R>::T *out, const DevParam &pk, const Rot<R> &rot,
+                                         bool pre, const DevDiag *dt) {
+    if (std::is_same<R, double>::value && rot.caseB) fwd_step_cb<R, 1>(e, out, pk, RotC<R, 1>{rot.c, rot.s, rot.t}, pre, dt);
+    else fwd_step_cb<R, 0>(e, out, pk, RotC<R, 0>{rot.c, rot.s, rot.t}, pre, dt);
 }
 
 // ------------------------------------------------------------------------------------------

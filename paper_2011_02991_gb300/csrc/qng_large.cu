@@ -69,9 +69,8 @@ __device__ __forceinline__ int gbit(const TileCtx &tc, uint32_t l, int q) {
 // One recurrence step on the registers A (left) and B (right) in one sweep of the tile: the inner
 // product with sigma on the pairs of qubit lb (compile-time axis AX and part IM), then, when ROT,
 // the adjoint rotation of the same axis on both registers. Every sign folds into an FMA operand.
-template <typename R, int AX, int IM, bool ROT>
-__device__ __forceinline__ R step_pairs(typename CX2<R>::T *A, typename CX2<R>::T *B, uint32_t T, int lb, R c, R s, R t,
-                                        int caseB) {
+template <typename R, int AX, int IM, bool ROT, int CB>
+__device__ __forceinline__ R step_pairs(typename CX2<R>::T *A, typename CX2<R>::T *B, uint32_t T, int lb, R c, R s, R t) {
     using cx = typename CX2<R>::T;
     constexpr bool kScaled = std::is_same<R, double>::value;
     R acc = 0;
@@ -79,8 +78,8 @@ __device__ __forceinline__ R step_pairs(typename CX2<R>::T *A, typename CX2<R>::
     auto rot = [&](cx x, cx v) -> cx {
         cx y;
         if constexpr (kScaled) {
-            if (caseB) { y.x = fma(t, x.x, v.x); y.y = fma(t, x.y, v.y); }
-            else       { y.x = fma(t, v.x, x.x); y.y = fma(t, v.y, x.y); }
+            if constexpr (CB) { y.x = fma(t, x.x, v.x); y.y = fma(t, x.y, v.y); }
+            else              { y.x = fma(t, v.x, x.x); y.y = fma(t, v.y, x.y); }
         } else {
             y.x = fma(s, v.x, c * x.x); y.y = fma(s, v.y, c * x.y);
         }
@@ -108,9 +107,9 @@ __device__ __forceinline__ R step_pairs(typename CX2<R>::T *A, typename CX2<R>::
     return acc;
 }
 
-template <typename R, int IM, bool ROT>
+template <typename R, int IM, bool ROT, int CB>
 __device__ __forceinline__ R step_diag(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int q, R c, R s,
-                                       R t, int caseB) {
+                                       R t) {
     using cx = typename CX2<R>::T;
     constexpr bool kScaled = std::is_same<R, double>::value;
     R acc = 0;
@@ -124,7 +123,7 @@ __device__ __forceinline__ R step_diag(const TileCtx &tc, typename CX2<R>::T *A,
             const cx va = {lflip(a.y, beta ^ 1), lflip(a.x, beta)}, vb = {lflip(b.y, beta ^ 1), lflip(b.x, beta)};
             cx ya, yb;
             if constexpr (kScaled) {
-                if (caseB) {
+                if constexpr (CB) {
                     ya.x = fma(t, a.x, va.x); ya.y = fma(t, a.y, va.y);
                     yb.x = fma(t, b.x, vb.x); yb.y = fma(t, b.y, vb.y);
                 } else {
@@ -142,17 +141,24 @@ __device__ __forceinline__ R step_diag(const TileCtx &tc, typename CX2<R>::T *A,
     return acc;
 }
 
+template <typename R, int IM, int CB>
+__device__ __forceinline__ R step_dispatch_cb(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int ax, int q,
+                                              bool rot, R c, R s, R t) {
+    if (ax == kAxisZ)
+        return rot ? step_diag<R, IM, true, CB>(tc, A, B, q, c, s, t) : step_diag<R, IM, false, CB>(tc, A, B, q, c, s, t);
+    const int lb = tc.lbit[q];
+    if (ax == kAxisX)
+        return rot ? step_pairs<R, kAxisX, IM, true, CB>(A, B, tc.T, lb, c, s, t)
+                   : step_pairs<R, kAxisX, IM, false, CB>(A, B, tc.T, lb, c, s, t);
+    return rot ? step_pairs<R, kAxisY, IM, true, CB>(A, B, tc.T, lb, c, s, t)
+               : step_pairs<R, kAxisY, IM, false, CB>(A, B, tc.T, lb, c, s, t);
+}
+
 template <typename R, int IM>
 __device__ __forceinline__ R step_dispatch(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int ax, int q,
                                            bool rot, R c, R s, R t, int caseB) {
-    if (ax == kAxisZ)
-        return rot ? step_diag<R, IM, true>(tc, A, B, q, c, s, t, caseB) : step_diag<R, IM, false>(tc, A, B, q, c, s, t, caseB);
-    const int lb = tc.lbit[q];
-    if (ax == kAxisX)
-        return rot ? step_pairs<R, kAxisX, IM, true>(A, B, tc.T, lb, c, s, t, caseB)
-                   : step_pairs<R, kAxisX, IM, false>(A, B, tc.T, lb, c, s, t, caseB);
-    return rot ? step_pairs<R, kAxisY, IM, true>(A, B, tc.T, lb, c, s, t, caseB)
-               : step_pairs<R, kAxisY, IM, false>(A, B, tc.T, lb, c, s, t, caseB);
+    if (std::is_same<R, double>::value && caseB) return step_dispatch_cb<R, IM, 1>(tc, A, B, ax, q, rot, c, s, t);
+    return step_dispatch_cb<R, IM, 0>(tc, A, B, ax, q, rot, c, s, t);
 }
 
 template <typename R>

@@ -152,6 +152,26 @@ qng_status qng_step(qng_ctx *ctx, const double *theta, double dt, double lambda,
 qng_status qng_step_host(qng_ctx *ctx, const double *theta_host, double dt, double lambda, double *dtheta_host,
                          double *g_host, double *grad_host, double *energy_host);
 
+/* Capture one qng_step with these arguments (device pointers that must stay valid) into a CUDA
+ * graph owned by the context, on the context's stream (which must not be the legacy default
+ * stream). qng_graph_launch replays it on that stream. A new capture replaces the old one; the
+ * graph is freed by qng_destroy. Re-capture after qng_set_workspace, qng_set_path or tuning. */
+qng_status qng_graph_capture(qng_ctx *ctx, const double *theta, double dt, double lambda, double *dtheta,
+                             double *g_opt, double *grad_opt, double *energy_opt);
+qng_status qng_graph_launch(qng_ctx *ctx);
+
+/* Autotuner of the on-chip path: for every qubit count present in the context, times qng_step
+ * (reps repetitions after one warm-up, CUDA events) for every cluster size (1..8 CTAs) and CTA size
+ * (64, 128, 256 threads) that fits, and keeps the fastest; theta is a device array of the context's
+ * parameters. report (may be NULL) receives the number of shapes timed. Shapes needing more
+ * workspace than the one set are skipped. Drops a captured graph. */
+qng_status qng_autotune(qng_ctx *ctx, const double *theta, int reps, int64_t *report);
+
+/* Launch shape used for instances of n_qubits qubits (after defaults, autotuning and qng_set_shape),
+ * and a manual override (cluster_log2 -1 and threads 0 restore the default). */
+qng_status qng_get_tuning(const qng_ctx *ctx, int n_qubits, int *cluster_log2, int *threads);
+qng_status qng_set_shape(qng_ctx *ctx, int n_qubits, int cluster_log2, int threads);
+
 /* Wait for the context's stream, then return (and clear) the device-side status word. */
 qng_status qng_sync(qng_ctx *ctx);
 

@@ -89,6 +89,13 @@ struct qng_ctx {
     int l_grid = 0;
     size_t o_reg[large::kRegs] = {0, 0, 0};
     size_t o_regscale = 0, o_partial = 0, o_slotfac = 0, o_pdesc = 0, o_pops = 0, o_red = 0;
+    size_t o_queue = 0;
+    // CUDA graph of one captured qng_step
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    // per-qubit-count launch shapes chosen by the autotuner (-1: default)
+    int tuned_cl[kMaxQubits + 1];
+    int tuned_threads[kMaxQubits + 1];
     int64_t last_launches = 0;
     // kernel timing (qng_profile)
     bool profiling = false;
@@ -98,7 +105,12 @@ struct qng_ctx {
     double prof_ms[QNG_KERNEL_CLASSES] = {0, 0, 0, 0};
     int64_t prof_n[QNG_KERNEL_CLASSES] = {0, 0, 0, 0};
 
+    qng_ctx() {
+        for (int k = 0; k <= kMaxQubits; ++k) { tuned_cl[k] = -1; tuned_threads[k] = 0; }
+    }
     ~qng_ctx() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
         for (auto &m : marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
         for (auto e : spare) cudaEventDestroy(e);
     }
@@ -286,9 +298,11 @@ qng_status plan(qng_ctx *c) {
     for (int b = 0; b < c->count; ++b) {
         const int n = c->inst[b].n;
         int cl = default_cl(n, c->precision);
+        if (c->tuned_cl[n] >= 0) cl = c->tuned_cl[n];
         if (c->tune_cl >= 0 && n >= c->tune_min_qubits) cl = c->tune_cl;
         cl = std::max(0, std::min(cl, std::min(kMaxClusterLog2, n - 1)));
         int th = default_threads(n - cl);
+        if (c->tuned_threads[n] > 0) th = c->tuned_threads[n];
         if (c->tune_threads > 0 && n >= c->tune_min_qubits) th = c->tune_threads;
         shape[b] = {cl, th};
         c->t_inst[b].cl = cl;
@@ -355,11 +369,20 @@ qng_status plan(qng_ctx *c) {
     c->o_io_g = take(sizeof(double) * c->total_metric);
     c->o_io_grad = take(sizeof(double) * c->total_params);
     c->o_io_energy = take(sizeof(double) * c->count);
+    c->o_queue = take(256 * std::max<size_t>(c->groups.size(), 1));
     c->o_ckpt = take(ab * (size_t)ckpt_amps);
     c->o_eta = take(ab * (size_t)eta_amps);
     c->ws_bytes = align256(off);
     c->prepared = false;
     return QNG_OK;
+}
+
+// cluster size of the distributed solve (-1: the single-CTA finish kernel is used)
+int solve_cluster_log2(int max_P) {
+    if (max_P < 48) return -1;
+    for (int cl = 3; cl >= 0; --cl)
+        if (solve_smem_bytes(max_P, cl) <= 200 * 1024) return cl;
+    return -1;
 }
 
 qng_status cuda_status(cudaError_t e) {
@@ -403,12 +426,30 @@ qng_status upload(qng_ctx *c) {
         if ((e = put(c->o_red, items.data(), sizeof(large::ReduceItem) * items.size())) != cudaSuccess) return cuda_status(e);
         static const double ones[2 * large::kRegs] = {1, 1, 1, 1, 1, 1};
         if ((e = put(c->o_regscale, ones, sizeof(ones))) != cudaSuccess) return cuda_status(e);
+        size_t pass_smem = 0;
+        for (const large::PassDesc &pd : S.passes)
+            pass_smem = std::max(pass_smem, (size_t)__builtin_popcount(pd.regmask) * (amp_bytes(c->precision) << pd.t));
+        if ((e = large::prepare_pass(c->precision, std::max<size_t>(pass_smem, 1))) != cudaSuccess) return cuda_status(e);
+        const int scl = solve_cluster_log2(c->max_P);
+        if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
         c->prepared = true;
         return QNG_OK;
     }
     size_t sf = 0, sc = 0;
     for (const Group &g : c->groups) { sf = std::max(sf, g.smem_fwd); sc = std::max(sc, g.smem_col); }
     if ((e = prepare_kernels(c->precision, sf, sc)) != cudaSuccess) return cuda_status(e);
+    const int scl = solve_cluster_log2(c->max_P);
+    if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
+    // batched contexts: persistent column launches fed by a device work counter per group
+    for (size_t k = 0; k < c->groups.size(); ++k) {
+        Group &g = c->groups[k];
+        g.queue = nullptr;
+        g.resident_clusters = 0;
+        if (c->count > 1) {
+            g.queue = reinterpret_cast<int *>(c->ws + c->o_queue + 256 * k);
+            g.resident_clusters = resident_clusters(g, c->precision);
+        }
+    }
     c->prepared = true;
     return QNG_OK;
 }
@@ -470,14 +511,6 @@ qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
         ++launches;
     }
     return QNG_OK;
-}
-
-// cluster size of the distributed solve (-1: the single-CTA finish kernel is used)
-int solve_cluster_log2(int max_P) {
-    if (max_P < 48) return -1;
-    for (int cl = 3; cl >= 0; --cl)
-        if (solve_smem_bytes(max_P, cl) <= 200 * 1024) return cl;
-    return -1;
 }
 
 qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
@@ -728,6 +761,125 @@ qng_status qng_set_path(qng_ctx *c, int path) {
     qng_status s = plan(c);
     if (s != QNG_OK || (c->ws && c->ws_bytes > old_bytes)) {
         c->path = old;
+        plan(c);
+        if (c->ws) upload(c);
+        return s != QNG_OK ? s : QNG_ERR_WORKSPACE;
+    }
+    if (c->ws) return upload(c);
+    return QNG_OK;
+}
+
+qng_status qng_graph_capture(qng_ctx *c, const double *theta, double dt, double lambda, double *dtheta, double *g_opt,
+                             double *grad_opt, double *energy_opt) {
+    if (!c || !dtheta) return QNG_ERR_ARG;
+    if (!c->ws || !c->prepared) return QNG_ERR_WORKSPACE;
+    if (!c->stream) return QNG_ERR_ARG;  // the legacy default stream cannot be captured
+    if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    const bool prof = c->profiling;
+    c->profiling = false;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { c->profiling = prof; return cuda_status(e); }
+    qng_status s = qng_step(c, theta, dt, lambda, dtheta, g_opt, grad_opt, energy_opt);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->stream, &graph);
+    c->profiling = prof;
+    if (s != QNG_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_status(e); }
+    c->graph = graph;
+    c->graph_exec = exec;
+    return QNG_OK;
+}
+
+qng_status qng_graph_launch(qng_ctx *c) {
+    if (!c) return QNG_ERR_ARG;
+    if (!c->graph_exec) return QNG_ERR_ARG;
+    return cuda_status(cudaGraphLaunch(c->graph_exec, c->stream));
+}
+
+qng_status qng_autotune(qng_ctx *c, const double *theta, int reps, int64_t *report) {
+    if (!c || reps < 1) return QNG_ERR_ARG;
+    if (!c->ws || !c->prepared) return QNG_ERR_WORKSPACE;
+    if (c->streaming) return QNG_OK;  // the streaming path has a single shape here
+    if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    const size_t bytes = c->ws_bytes;
+    double *scratch_out = reinterpret_cast<double *>(c->ws + c->o_io_dtheta);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return QNG_ERR_CUDA;
+    auto time_step = [&](float &ms) -> qng_status {
+        qng_status s = qng_step(c, theta, 0.1, 1e-3, scratch_out, nullptr, nullptr, nullptr);  // warm-up
+        if (s != QNG_OK) return s;
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps; ++r)
+            if ((s = qng_step(c, theta, 0.1, 1e-3, scratch_out, nullptr, nullptr, nullptr)) != QNG_OK) return s;
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return QNG_ERR_CUDA;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return QNG_OK;
+    };
+    std::vector<int> ns;
+    for (const HostInst &h : c->inst) ns.push_back(h.n);
+    std::sort(ns.begin(), ns.end());
+    ns.erase(std::unique(ns.begin(), ns.end()), ns.end());
+    int64_t tried = 0;
+    qng_status st = QNG_OK;
+    for (int n : ns) {
+        float best = 3.4e38f;
+        int best_cl = c->tuned_cl[n], best_th = c->tuned_threads[n];
+        for (int cl = 0; cl <= std::min(kMaxClusterLog2, n - 1); ++cl) {
+            for (int th : {64, 128, 256}) {
+                if ((1 << (n - cl)) < th) continue;
+                c->tuned_cl[n] = cl;
+                c->tuned_threads[n] = th;
+                if (plan(c) != QNG_OK || c->ws_bytes > bytes) continue;
+                if ((st = upload(c)) != QNG_OK) break;
+                float ms = 0.f;
+                if ((st = time_step(ms)) != QNG_OK) break;
+                ++tried;
+                if (ms < best) { best = ms; best_cl = cl; best_th = th; }
+            }
+            if (st != QNG_OK) break;
+        }
+        c->tuned_cl[n] = best_cl;
+        c->tuned_threads[n] = best_th;
+        if (st != QNG_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    qng_status s2 = plan(c);
+    if (s2 == QNG_OK) s2 = upload(c);
+    if (report) *report = tried;
+    return st != QNG_OK ? st : s2;
+}
+
+qng_status qng_get_tuning(const qng_ctx *c, int n_qubits, int *cluster_log2, int *threads) {
+    if (!c || n_qubits < 1 || n_qubits > kMaxQubits) return QNG_ERR_ARG;
+    int cl = default_cl(n_qubits, c->precision);
+    if (c->tuned_cl[n_qubits] >= 0) cl = c->tuned_cl[n_qubits];
+    cl = std::max(0, std::min(cl, std::min(kMaxClusterLog2, n_qubits - 1)));
+    int th = default_threads(n_qubits - cl);
+    if (c->tuned_threads[n_qubits] > 0) th = c->tuned_threads[n_qubits];
+    if (cluster_log2) *cluster_log2 = cl;
+    if (threads) *threads = th;
+    return QNG_OK;
+}
+
+qng_status qng_set_shape(qng_ctx *c, int n_qubits, int cluster_log2, int threads) {
+    if (!c || n_qubits < 1 || n_qubits > kMaxQubits) return QNG_ERR_ARG;
+    if (cluster_log2 < -1 || cluster_log2 > kMaxClusterLog2) return QNG_ERR_ARG;
+    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32)) return QNG_ERR_ARG;
+    const int ocl = c->tuned_cl[n_qubits], oth = c->tuned_threads[n_qubits];
+    c->tuned_cl[n_qubits] = cluster_log2;
+    c->tuned_threads[n_qubits] = threads;
+    const size_t old_bytes = c->ws_bytes;
+    qng_status s = plan(c);
+    if (s != QNG_OK || (c->ws && c->ws_bytes > old_bytes)) {
+        c->tuned_cl[n_qubits] = ocl;
+        c->tuned_threads[n_qubits] = oth;
         plan(c);
         if (c->ws) upload(c);
         return s != QNG_OK ? s : QNG_ERR_WORKSPACE;

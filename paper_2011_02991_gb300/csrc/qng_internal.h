@@ -117,6 +117,8 @@ struct Group {
     int num_met = 0;
     size_t smem_fwd = 0;
     size_t smem_col = 0;
+    int *queue = nullptr;        // device work counter of the persistent column launch (batched contexts)
+    int resident_clusters = 0;   // clusters of the column kernel resident at once
 };
 
 enum Job : int {
@@ -146,6 +148,8 @@ cudaError_t launch_columns(const Work &w, const Group &g, int precision, int wit
 cudaError_t launch_finish(const Work &w, int count, int max_P, const LaunchArgs &a, cudaStream_t st);
 cudaError_t launch_solve(const Work &w, int count, int max_P, int cl, const LaunchArgs &a, cudaStream_t st);
 size_t solve_smem_bytes(int P, int cl);
+cudaError_t prepare_solve(size_t smem);
+int resident_clusters(const Group &g, int precision);
 cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col);
 
 }  // namespace qng

@@ -601,11 +601,40 @@ __global__ void __launch_bounds__(1024) k_forward(Work w, int group_first, int c
 // ------------------------------------------------------------------------------------------
 // k_columns: one cluster per work item (instance, column).
 template <typename R>
-__global__ void __launch_bounds__(1024) k_columns(Work w, int work_first, int cl, int max_P) {
+__device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int cl, int max_P, unsigned char *smem);
+
+// One cluster per work item, or (queue != nullptr) a persistent grid of clusters that take work
+// items, longest first, from a device counter until all num_work are done.
+template <typename R>
+__global__ void __launch_bounds__(1024) k_columns(Work w, int work_first, int cl, int max_P, int *queue, int num_work) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int item_sh;
+    if (!queue) {
+        column_item<R>(w, w.work[work_first + (blockIdx.x >> cl)], cl, max_P, smem);
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0 && (!cl || cg::this_cluster().block_rank() == 0)) item_sh = atomicAdd(queue, 1);
+        if (cl) {
+            cg::this_cluster().sync();
+            const int item = *cg::this_cluster().map_shared_rank(&item_sh, 0);
+            cg::this_cluster().sync();  // rank 0 keeps item_sh until every CTA has read it
+            if (item >= num_work) return;
+            column_item<R>(w, w.work[work_first + item], cl, max_P, smem);
+        } else {
+            __syncthreads();
+            const int item = item_sh;
+            __syncthreads();
+            if (item >= num_work) return;
+            column_item<R>(w, w.work[work_first + item], cl, max_P, smem);
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int cl, int max_P, unsigned char *smem) {
     using cx = typename CX<R>::T;
     using RA = R;  // per-thread partial sums; float64 from the warp level on
-    extern __shared__ __align__(16) unsigned char smem[];
-    const DevWork wk = w.work[work_first + (blockIdx.x >> cl)];
     const DevInst in = w.inst[wk.inst];
     Eng<R> e = make_eng<R>(smem, in.n, cl);
     const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1068,9 +1097,8 @@ size_t solve_smem_bytes(int P, int cl) {
 
 // ------------------------------------------------------------------------------------------
 // launchers
-template <typename K>
-static cudaError_t launch_cluster(K kern, int grid, int threads, size_t smem, int cl, cudaStream_t st,
-                                  Work w, int a0, int a1, int a2) {
+template <typename K, typename... Args>
+static cudaError_t launch_cluster(K kern, int grid, int threads, size_t smem, int cl, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
@@ -1085,7 +1113,7 @@ static cudaError_t launch_cluster(K kern, int grid, int threads, size_t smem, in
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    return cudaLaunchKernelEx(&cfg, kern, w, a0, a1, a2);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 template <typename K> static cudaError_t set_attrs(K kern, size_t smem) {
@@ -1127,16 +1155,46 @@ cudaError_t launch_columns(const Work &w, const Group &g, int precision, int wit
     else if (with_metric)         { first = g.first_met; num = g.num_met; }
     else                          { first = g.first_grad; num = g.num_grad; }
     if (num == 0) return cudaSuccess;
-    const int grid = num << g.cl;
+    int *queue = nullptr;
+    int clusters = num;
+    if (g.queue && g.resident_clusters > 0 && g.resident_clusters < num) {
+        queue = g.queue;
+        clusters = g.resident_clusters;
+        cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = clusters << g.cl;
     if (precision == QNG_C128)
-        return launch_cluster(k_columns<double>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P);
-    return launch_cluster(k_columns<float>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P);
+        return launch_cluster(k_columns<double>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P, queue, num);
+    return launch_cluster(k_columns<float>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P, queue, num);
+}
+
+// Clusters of this group's column kernel that fit on the GPU at once (0 if unknown).
+int resident_clusters(const Group &g, int precision) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1u << g.cl);
+    cfg.blockDim = dim3(g.threads);
+    cfg.dynamicSmemBytes = g.smem_col;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1u << g.cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e = (precision == QNG_C128) ? cudaOccupancyMaxActiveClusters(&n, k_columns<double>, &cfg)
+                                            : cudaOccupancyMaxActiveClusters(&n, k_columns<float>, &cfg);
+    if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+    return n;
+}
+
+cudaError_t prepare_solve(size_t smem) {
+    return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t launch_solve(const Work &w, int count, int max_P, int cl, const LaunchArgs &a, cudaStream_t st) {
     const size_t smem = solve_smem_bytes(max_P, cl);
-    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)count << cl);
     cfg.blockDim = dim3(256);

@@ -495,16 +495,14 @@ __global__ void k_reduce(const double *partial, const double *slotfac, int nctas
 }
 
 // ------------------------------------------------------------------------------------------
+cudaError_t prepare_pass(int precision, size_t smem) {
+    return precision == QNG_C128 ? cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                                 : cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, cudaStream_t st) {
-    if (precision == QNG_C128) {
-        cudaError_t e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_pass<double><<<grid, threads, smem, st>>>(pa);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_pass<float><<<grid, threads, smem, st>>>(pa);
-    }
+    if (precision == QNG_C128) k_pass<double><<<grid, threads, smem, st>>>(pa);
+    else k_pass<float><<<grid, threads, smem, st>>>(pa);
     return cudaGetLastError();
 }
 

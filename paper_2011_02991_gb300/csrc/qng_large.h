@@ -67,6 +67,7 @@ struct PassArgs {
     double *slotfac;   // [slots]
 };
 
+cudaError_t prepare_pass(int precision, size_t smem);
 cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_hpsi(const void *in, void *out, const DevTerm *terms, int nterms, int n, int precision,
                         double *partial, int grid, cudaStream_t st);

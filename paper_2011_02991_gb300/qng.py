@@ -64,6 +64,11 @@ SYMBOLS = {
     "qng_last_launch_count": [_vp, _i64p],
     "qng_profile": [_vp, ctypes.c_int],
     "qng_set_path": [_vp, ctypes.c_int],
+    "qng_graph_capture": [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp],
+    "qng_graph_launch": [_vp],
+    "qng_autotune": [_vp, _vp, ctypes.c_int, _i64p],
+    "qng_get_tuning": [_vp, ctypes.c_int, _i32p, _i32p],
+    "qng_set_shape": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "qng_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), _i64p],
     "qng_destroy": [_vp],
     "qng_status_string": [ctypes.c_int],
@@ -243,6 +248,35 @@ class Context:
                                   p(o.get("g")) if want_all else None, p(o.get("grad")) if want_all else None,
                                   p(o.get("energy")) if want_all else None), "qng_step_host")
         return o
+
+    def graph_capture(self, theta, dt: float = 0.1, lam: float = 1e-3, outputs: dict | None = None) -> dict:
+        """Capture one step into a CUDA graph; the returned output tensors are refreshed by graph_launch."""
+        theta = self._theta(theta)
+        self._graph_theta = theta
+        o = outputs if outputs is not None else {
+            "dtheta": self._f64(self.total_params), "g": self._f64(self.total_metric),
+            "grad": self._f64(self.total_params), "energy": self._f64(self.count)}
+        self._graph_out = o
+        _chk(load().qng_graph_capture(self._h, _ptr(theta), float(dt), float(lam), _ptr(o["dtheta"]), _ptr(o.get("g")),
+                                      _ptr(o.get("grad")), _ptr(o.get("energy"))), "qng_graph_capture")
+        return o
+
+    def graph_launch(self):
+        _chk(load().qng_graph_launch(self._h), "qng_graph_launch")
+
+    def autotune(self, theta, reps: int = 3) -> int:
+        theta = self._theta(theta)
+        n = ctypes.c_int64()
+        _chk(load().qng_autotune(self._h, _ptr(theta), int(reps), ctypes.byref(n)), "qng_autotune")
+        return int(n.value)
+
+    def get_tuning(self, n_qubits: int):
+        cl, th = ctypes.c_int32(), ctypes.c_int32()
+        _chk(load().qng_get_tuning(self._h, int(n_qubits), ctypes.byref(cl), ctypes.byref(th)), "qng_get_tuning")
+        return cl.value, th.value
+
+    def set_shape(self, n_qubits: int, cluster_log2: int, threads: int):
+        _chk(load().qng_set_shape(self._h, int(n_qubits), int(cluster_log2), int(threads)), "qng_set_shape")
 
     def sync(self):
         _chk(load().qng_sync(self._h), "qng_sync")

@@ -212,3 +212,41 @@ def test_deterministic(qng):
     b = ctx.step(ctx.theta0(), p.dt, p.lam)
     for k in a:
         assert torch.equal(a[k], b[k]), k
+
+
+def test_graph_capture_replay(qng):
+    """One captured CUDA graph of the whole step replays to the same results as the direct calls."""
+    for probs in (W.config_rand12(), W.config_batch(count=12)):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            ctx = qng.Context(probs, stream=stream)
+            th = ctx.theta0()
+            ref = ctx.step(th, 0.1, 1e-3)
+            ctx.sync()
+            ref = {k: v.clone() for k, v in ref.items()}
+            out = ctx.graph_capture(th, 0.1, 1e-3)
+            for _ in range(2):
+                for v in out.values():
+                    v.fill_(float("nan"))
+                ctx.graph_launch()
+                ctx.sync()
+                for k in ref:
+                    assert torch.equal(out[k], ref[k]), k
+
+
+def test_autotune_keeps_results(qng, oracle):
+    """The autotuner sweeps launch shapes per qubit count; results stay within tolerance."""
+    probs = W.config_batch(count=16, precision=W.C64)
+    ctx = qng.Context(probs, precision=W.C64)
+    tried = ctx.autotune(ctx.theta0(), reps=1)
+    assert tried >= len({p.n for p in probs})
+    out = ctx.step(ctx.theta0(), 0.1, 1e-3)
+    ctx.sync()
+    gs, dths = ctx.split_metric(out["g"]), ctx.split_params(out["dtheta"])
+    for b in (0, 5, 11, 15):
+        ref = oracle.qng_step(probs[b])
+        assert rel(gs[b].cpu(), ref["g"]) <= TOL[W.C64]
+        assert rel(dths[b].cpu(), ref["dtheta"]) <= TOL[W.C64]
+    for n in {p.n for p in probs}:
+        cl, th = ctx.get_tuning(n)
+        assert 0 <= cl <= 3 and th in (64, 128, 256)

@@ -60,6 +60,8 @@ def lib():
             L.oracle_alg3.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, _dp, _i64p]
             L.oracle_alg6.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, ctypes.c_int, _dp, _i64p]
             L.oracle_alg8.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, _dp, _i64p]
+            L.oracle_sampled.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, ctypes.c_int, _dp, _u64p, _u64p, _i32p,
+                                         ctypes.c_int, _dp, _dp, _dp, _dp]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -180,6 +182,26 @@ def gradient(circuit, ham, theta, idx=None):
     _check(lib().oracle_gradient(circuit.n, _p(g, _i32p), len(g), _p(theta, _dp), len(c), _p(c, _dp), _p(x, _u64p),
                                  _p(z, _u64p), _p(idx, _i32p), len(idx), _p(out, _dp), _p(E, _dp)))
     return out, float(E[0])
+
+
+def sampled(problem, idx):
+    """(G_sub, T_sub, grad_sub, E) over the parameter subset idx (Eq. 4 and Eq. 2), one sweep."""
+    c, ham = problem.circuit, problem.hamiltonian
+    theta = np.ascontiguousarray(problem.theta, dtype=np.float64)
+    g = _gates(c)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    m = len(idx)
+    co = np.ascontiguousarray(ham.coeffs, dtype=np.float64)
+    x = np.ascontiguousarray(ham.xmask, dtype=np.uint64)
+    z = np.ascontiguousarray(ham.zmask, dtype=np.uint64)
+    G = np.empty((m, m), dtype=np.complex128)
+    T = np.empty(m, dtype=np.complex128)
+    grad = np.empty(m)
+    E = np.zeros(1)
+    _check(lib().oracle_sampled(c.n, _p(g, _i32p), len(g), _p(theta, _dp), len(co), _p(co, _dp), _p(x, _u64p),
+                                _p(z, _u64p), _p(idx, _i32p), m, _p(G.view(np.float64), _dp),
+                                _p(T.view(np.float64), _dp), _p(grad, _dp), _p(E, _dp)))
+    return G, T, grad, float(E[0])
 
 
 def solve_step(g: np.ndarray, grad: np.ndarray, dt: float, lam: float) -> np.ndarray:

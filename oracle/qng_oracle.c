@@ -480,3 +480,36 @@ void oracle_set_num_threads(int t) { if (t > 0) omp_set_num_threads(t); }
 int oracle_num_threads(void) { return 1; }
 void oracle_set_num_threads(int t) { (void)t; }
 #endif
+
+/*
+ * Everything a QNG step needs, restricted to the parameter subset idx[0..m-1], in one sweep of
+ * derivative states (for large states where the full set is out of reach):
+ *   G_out (m x m complex, Eq. 4), T_out (m complex), grad_out (m, 2 Re <psi|H|d psi>), E_out.
+ * Memory: m + 2 states.
+ */
+int oracle_sampled(int n, const int32_t *gates, int G, const double *theta, int T, const double *coeff,
+                   const uint64_t *xm, const uint64_t *zm, const int32_t *idx, int m, double *G_out, double *T_out,
+                   double *grad_out, double *E_out) {
+    const size_t N = (size_t)1 << n;
+    cplx *psi = (cplx *)malloc(sizeof(cplx) * N);
+    cplx *hpsi = (cplx *)malloc(sizeof(cplx) * N);
+    cplx *d = (cplx *)malloc(sizeof(cplx) * N * (size_t)(m > 0 ? m : 1));
+    if (!psi || !hpsi || !d) { free(psi); free(hpsi); free(d); return -1; }
+    run_circuit(psi, n, gates, G, theta, -1);
+    int rc = hamiltonian_apply(hpsi, psi, n, T, coeff, xm, zm);
+    *E_out = creal(inner(psi, hpsi, n));
+    cplx *Tc = (cplx *)T_out, *Gc = (cplx *)G_out;
+    for (int a = 0; a < m; ++a) {
+        cplx *da = d + (size_t)a * N;
+        run_circuit(da, n, gates, G, theta, idx[a]);
+        Tc[a] = inner(psi, da, n);
+        grad_out[a] = 2.0 * creal(inner(hpsi, da, n));
+    }
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b)
+            Gc[(size_t)a * m + b] = inner(d + (size_t)a * N, d + (size_t)b * N, n) - conj(Tc[a]) * Tc[b];
+    free(psi);
+    free(hpsi);
+    free(d);
+    return rc;
+}

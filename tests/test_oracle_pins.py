@@ -422,3 +422,15 @@ def test_workload_shapes():
         assert 6 <= b.n <= 14 and 16 <= b.hamiltonian.num_terms <= 48
         w = np.array([bin(int(x) | int(z)).count("1") for x, z in zip(b.hamiltonian.xmask, b.hamiltonian.zmask)])
         assert w.min() >= 1 and w.max() <= 4
+
+
+def test_sampled_matches_full(oracle):
+    p = W.random_problem(5, 40, 8, 91)
+    idx = np.array([0, 3, p.P - 1], dtype=np.int32)
+    Gs, Ts, gs, E = oracle.sampled(p, idx)
+    G, T = oracle.qgt(p.circuit, p.theta)
+    grad, E2 = oracle.gradient(p.circuit, p.hamiltonian, p.theta)
+    np.testing.assert_allclose(Gs, G[np.ix_(idx, idx)], atol=1e-15)
+    np.testing.assert_allclose(Ts, T[idx], atol=1e-15)
+    np.testing.assert_allclose(gs, grad[idx], atol=1e-14)
+    assert abs(E - E2) < 1e-14

@@ -32,22 +32,43 @@ METRIC = "QNG steps/s (g,∇E,Δθ) per config; HBM GB/s vs GB300 peak; max err 
 # 152 SMs x 2.07 GHz maximum SM clock
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
+HBM_PEAK_GBS = 6669.2  # measured copy bandwidth of this GPU pool
 
 
 def workloads():
+    """name -> (problem or list of problems, kind: single | batch | stream)."""
     from paper_2011_02991_gb300 import workloads as W
     return {
-        "rand12_p192_c128": lambda: W.config_rand12(precision=W.C128),
-        "rand12_p192_c64": lambda: W.config_rand12(precision=W.C64),
-        "tfim4_p16_c128": W.config_tfim4,
+        "rand12_p192_c128": (lambda: W.config_rand12(precision=W.C128), "single"),
+        "rand12_p192_c64": (lambda: W.config_rand12(precision=W.C64), "single"),
+        "tfim4_p16_c128": (W.config_tfim4, "single"),
+        "batch256_c64": (lambda: W.config_batch(precision=W.C64), "batch"),
+        "batch256_c128": (lambda: W.config_batch(precision=W.C128), "batch"),
+        "tfim26_p208_c128": (W.config_tfim26, "stream"),
+        "rand28_p252_c64": (lambda: W.config_rand28(precision=W.C64), "stream"),
+        "rand28_p252_c128": (lambda: W.config_rand28(precision=W.C128), "stream"),
+        "tfim24_p48_c128": (lambda: W.config_tfim26(n=24, layers=1), "stream"),
+        "tfim24_p48_c64": (lambda: _c64(W.config_tfim26(n=24, layers=1)), "stream"),
     }
+
+
+def _c64(p):
+    from paper_2011_02991_gb300 import workloads as W
+    return W.Problem(p.name.replace("c128", "c64"), p.circuit, p.hamiltonian, p.theta, precision=W.C64, meta=p.meta)
 
 
 DESCRIPTION = {
     "rand12_p192_c128": "12 qubits, 8 x [Ry all, Rz all, CZ ladder] (P=192), 40 random Pauli strings "
                         "(weight 1-4, N(0,1) coefficients), theta ~ U[0,2pi), complex128, dt=0.1, lambda=1e-3",
-    "rand12_p192_c64": "as rand12_p192_c128 with complex64 amplitudes (float64 accumulation)",
+    "rand12_p192_c64": "as rand12_p192_c128 with complex64 amplitudes (float64 accumulation, assembly, solve)",
     "tfim4_p16_c128": "4 qubits, 2 x [Ry, Rz, CZ ladder] (P=16), open TFIM, complex128",
+    "batch256_c64": "256 instances, n ~ U{6..14}, 2-10 Ry/Rz/CZ layers (P 24-280), 16-48 strings each, complex64",
+    "batch256_c128": "the same 256 instances in complex128",
+    "tfim26_p208_c128": "26 qubits, 4 x [Ry, Rz, CZ ladder] (P=208), TFIM J=1, h ~ U[0.2,1], complex128 (1 GiB per state)",
+    "rand28_p252_c64": "28 qubits, 3 x [Ry, Rx, Rz all, CNOT ladder] (P=252), 64 strings, complex64 (2 GiB per state)",
+    "rand28_p252_c128": "as rand28_p252_c64 in complex128 (4 GiB per state)",
+    "tfim24_p48_c128": "24 qubits, 1 x [Ry, Rz, CZ ladder] (P=48), TFIM, complex128 (streaming, profiling case)",
+    "tfim24_p48_c64": "as tfim24_p48_c128 in complex64",
 }
 
 
@@ -119,55 +140,120 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-def oracle_step_time(problem, budget_s: float, max_steps: int):
-    """Time full oracle QNG steps for about budget_s seconds (at least one)."""
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def sample_ids(kind, problems):
+    """Instances (batch) or parameter indices (stream) the oracle checks and times."""
+    if kind == "batch":
+        rng = np.random.default_rng(11)
+        return sorted(rng.choice(len(problems), min(8, len(problems)), replace=False).tolist())
+    if kind == "stream":
+        P = problems[0].P
+        return [0, P // 2, P - 1][: max(1, min(3, P))]
+    return None
+
+
+def oracle_check(kind, problems, ctx, outs):
+    """Max relative error of the GPU outputs against the oracle (sampled where the full oracle is out of reach)."""
+    from oracle import oracle as O
+    g, grad, dth, en = (outs[k].cpu().numpy() for k in ("g", "grad", "dtheta", "energy"))
+    if kind == "single":
+        ref = O.qng_step(problems[0])
+        return {"g": _rel(g, ref["g"]), "grad": _rel(grad, ref["grad"]), "dtheta": _rel(dth, ref["dtheta"]),
+                "E": _rel(en, [ref["E"]])}
+    if kind == "batch":
+        err = {"g": 0.0, "grad": 0.0, "dtheta": 0.0, "E": 0.0}
+        for b in sample_ids(kind, problems):
+            ref = O.qng_step(problems[b])
+            p0, p1 = ctx.param_offsets[b], ctx.param_offsets[b + 1]
+            m0, m1 = ctx.metric_offsets[b], ctx.metric_offsets[b + 1]
+            err["g"] = max(err["g"], _rel(g[m0:m1], ref["g"]))
+            err["grad"] = max(err["grad"], _rel(grad[p0:p1], ref["grad"]))
+            err["dtheta"] = max(err["dtheta"], _rel(dth[p0:p1], ref["dtheta"]))
+            err["E"] = max(err["E"], _rel(en[b:b + 1], [ref["E"]]))
+        err["sample"] = f"{len(sample_ids(kind, problems))} instances"
+        return err
+    p = problems[0]
+    idx = np.array(sample_ids(kind, problems), dtype=np.int32)
+    Gs, Ts, grads, E = O.sampled(p, idx)
+    gm = g.reshape(p.P, p.P)
+    r = (gm + p.lam * np.eye(p.P)) @ dth + p.dt * grad
+    return {"g": _rel(gm[np.ix_(idx, idx)], Gs.real), "grad": _rel(grad[idx], grads), "E": _rel(en, [E]),
+            "dtheta_residual": float(np.linalg.norm(r) / max(np.linalg.norm(p.dt * grad), 1e-300)),
+            "sample": f"parameters {idx.tolist()} (sampled oracle entries)"}
+
+
+def oracle_baseline(kind, problems, budget_s):
+    """Oracle throughput on the host cores: (steps/s, sample description)."""
     from oracle import oracle as O
     O.build()
-    times = []
-    t_all = time.perf_counter()
-    while len(times) < max_steps and (not times or time.perf_counter() - t_all < budget_s):
-        t0 = time.perf_counter()
-        O.qng_step(problem)
-        times.append(time.perf_counter() - t0)
-    return times
+    if kind == "single":
+        times, t_all = [], time.perf_counter()
+        while len(times) < 30 and (not times or time.perf_counter() - t_all < budget_s):
+            t0 = time.perf_counter()
+            O.qng_step(problems[0])
+            times.append(time.perf_counter() - t0)
+        return len(times) / sum(times), f"{len(times)} full oracle QNG steps of the same workload ({sum(times):.1f} s)"
+    if kind == "batch":
+        ids, times, t_all = sample_ids(kind, problems), [], time.perf_counter()
+        k = 0
+        while not times or (time.perf_counter() - t_all < budget_s and k < 64):
+            t0 = time.perf_counter()
+            O.qng_step(problems[ids[k % len(ids)]])
+            times.append(time.perf_counter() - t0)
+            k += 1
+        per_instance = sum(times) / len(times)
+        return 1.0 / (per_instance * len(problems)), (
+            f"{len(times)} oracle QNG steps of {len(ids)} sampled instances ({sum(times):.1f} s), "
+            f"extrapolated to all {len(problems)} instances")
+    p = problems[0]
+    idx = np.array(sample_ids(kind, problems), dtype=np.int32)
+    t0 = time.perf_counter()
+    O.sampled(p, idx)
+    t = time.perf_counter() - t0
+    m = len(idx)
+    full = t * (p.P + 2) / (m + 2)  # one derivative state per parameter dominates the definition's cost
+    return 1.0 / full, (f"oracle sampled-entry mode, {m} derivative states + psi + H psi in {t:.1f} s, "
+                        f"extrapolated to the P + 2 states of a full step")
 
 
-def cpu_threads_used(n: int) -> int:
-    # the oracle's loops only go parallel for states of at least 2^16 amplitudes
-    from oracle import oracle as O
-    return O.num_threads() if n >= 16 else 1
-
-
-def run_reference(args, name, problem, rank, world):
+def run_reference(args, name, problems, kind, rank, world):
     if rank != 0:
         return
     from oracle import oracle as O
     O.build()
-    for _ in range(min(args.warmup, 1)):
-        O.qng_step(problem)
-    t0 = time.perf_counter()
-    O.qng_step(problem)
-    t_one = time.perf_counter() - t0
-    k = max(1, min(args.steps, int(100.0 / max(t_one, 1e-6))))
-    t0 = time.perf_counter()
-    for _ in range(k):
-        O.qng_step(problem)
-    el = time.perf_counter() - t0
-    value = k / el
-    cores = cpu_threads_used(problem.n)
+    threads = O.num_threads() if problems[0].n >= 16 else 1
+    if kind == "single":
+        p = problems[0]
+        for _ in range(min(args.warmup, 1)):
+            O.qng_step(p)
+        t0 = time.perf_counter()
+        O.qng_step(p)
+        t_one = time.perf_counter() - t0
+        k = max(1, min(args.steps, int(100.0 / max(t_one, 1e-6))))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            O.qng_step(p)
+        el = time.perf_counter() - t0
+        value, steps, sample = k / el, k, f"{k} full oracle QNG steps (of {args.steps} requested, capped at ~100 s)"
+        ms = 1e3 * el / k
+    else:
+        value, sample = oracle_baseline(kind, problems, budget_s=60.0)
+        steps, ms = 1, 1e3 / value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
-            "steps": k, "steps_requested": args.steps, "warmup": min(args.warmup, 1),
-            "ms_per_step": 1e3 * el / k, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{name}: {DESCRIPTION[name]}", "n_qubits": problem.n, "P": problem.P,
-                       "parallelism": "single host process"},
-            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{k} full oracle QNG steps (of {args.steps} requested, capped at ~100 s)"},
+            "steps": steps, "steps_requested": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{name}: {DESCRIPTION[name]}", "parallelism": "single host process"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, name, problem, rank, world, local_rank):
+def run_ours(args, name, problems, kind, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     from paper_2011_02991_gb300 import build as B
@@ -178,29 +264,24 @@ def run_ours(args, name, problem, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
+    prec = problems[0].precision
+    dt, lam = problems[0].dt, problems[0].lam
     with torch.cuda.stream(stream):
-        ctx = qng.Context(problem, device=dev, stream=stream)
+        ctx = qng.Context(problems if kind == "batch" else problems[0], device=dev, stream=stream)
         theta = ctx.theta0()
         outs = {"dtheta": ctx._f64(ctx.total_params), "g": ctx._f64(ctx.total_metric),
                 "grad": ctx._f64(ctx.total_params), "energy": ctx._f64(ctx.count)}
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
-        # accuracy against the oracle (outside the timed region, rank 0)
         err = None
-        if rank == 0:
-            from oracle import oracle as O
-            ctx.step(theta, problem.dt, problem.lam, outs)
+        if rank == 0 and not args.no_check:
+            ctx.step(theta, dt, lam, outs)
             ctx.sync()
-            ref = O.qng_step(problem)
-            rel = lambda a, b: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))  # noqa: E731
-            err = {"g": rel(outs["g"].cpu().numpy(), ref["g"].ravel()),
-                   "grad": rel(outs["grad"].cpu().numpy(), ref["grad"]),
-                   "dtheta": rel(outs["dtheta"].cpu().numpy(), ref["dtheta"]),
-                   "E": rel(outs["energy"].cpu().numpy(), np.array([ref["E"]]))}
+            err = oracle_check(kind, problems, ctx, outs)
 
         for _ in range(args.warmup):
             flush.zero_()
-            ctx.step(theta, problem.dt, problem.lam, outs)
+            ctx.step(theta, dt, lam, outs)
         ctx.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if world > 1:
@@ -214,7 +295,7 @@ def run_ours(args, name, problem, rank, world, local_rank):
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            ctx.step(theta, problem.dt, problem.lam, outs)
+            ctx.step(theta, dt, lam, outs)
             launches0 += ctx.last_launch_count()
             ev[k][1].record(stream)
         torch.cuda.synchronize(dev)
@@ -230,69 +311,95 @@ def run_ours(args, name, problem, rank, world, local_rank):
         ms_max = float(t.item())
 
         # end to end through the public host-buffer entry point (pinned host memory)
-        th_host = torch.from_numpy(problem.theta.copy()).pin_memory().numpy()
+        th_host = torch.from_numpy(np.concatenate([p.theta for p in problems]).astype(np.float64)).pin_memory().numpy()
         hout = {"dtheta": torch.empty(ctx.total_params, dtype=torch.float64).pin_memory().numpy(),
                 "g": torch.empty(ctx.total_metric, dtype=torch.float64).pin_memory().numpy(),
                 "grad": torch.empty(ctx.total_params, dtype=torch.float64).pin_memory().numpy(),
                 "energy": torch.empty(ctx.count, dtype=torch.float64).pin_memory().numpy()}
-        for _ in range(max(1, args.warmup // 2)):
-            ctx.step_host(th_host, problem.dt, problem.lam, hout)
+        e2e_steps = args.steps if kind != "stream" else min(args.steps, 2)
+        for _ in range(max(1, min(args.warmup, 2) // 2)):
+            ctx.step_host(th_host, dt, lam, hout)
         if world > 1:
             dist.barrier()
         e2e_ms = 0.0
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             flush.zero_()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            ctx.step_host(th_host, problem.dt, problem.lam, hout)
+            ctx.step_host(th_host, dt, lam, hout)
             e2e_ms += 1e3 * (time.perf_counter() - t0)
-        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        te = torch.tensor([e2e_ms / e2e_steps], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_ms = float(te.item())
+        e2e_ms_per_step = float(te.item())
 
     if rank != 0:
         return
-    steps_total = args.steps * world
-    value = steps_total / (ms_max / 1e3)
+    value = args.steps * world / (ms_max / 1e3)
     col_ms, col_n = prof["columns"]
-    col_avg_s = col_ms / max(col_n, 1) / 1e3
-    flops = column_flops(problem.P, problem.n)
-    prec64 = problem.precision == W.C128
-    peak = FP64_PEAK_TFLOPS if prec64 else FP32_PEAK_TFLOPS
-    achieved = flops / col_avg_s / 1e12
+    prec64 = prec == W.C128
+    if kind == "stream":
+        mb, ob, mp = ctx.stream_traffic()
+        p = problems[0]
+        met_s = col_ms / args.steps / 1e3
+        if prec64:
+            elems = p.P * (p.P - 1) / 2
+            flops = (1 << p.n) * 12.0 * elems  # inner product 2 FMA + two scaled rotations 2 FMA each, per amplitude
+            achieved = flops / met_s / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "kernel": "k_pass metric passes + column reductions", "kernel_avg_ms": met_s * 1e3,
+                    "flops_per_step": flops, "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz"}
+        else:
+            achieved = mb / met_s / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                    "frac": achieved / HBM_PEAK_GBS, "traffic": None,
+                    "kernel": "k_pass metric passes (registers loaded and stored per pass)", "kernel_avg_ms": met_s * 1e3,
+                    "bytes_per_step": mb, "passes_per_step": mp, "peak_source": "measured copy bandwidth"}
+    else:
+        col_avg_s = col_ms / max(col_n, 1) / 1e3
+        launches_per_step = col_n / max(args.steps, 1)
+        flops_step = sum(column_flops(p.P, p.n) for p in problems)  # all instances, all column launches of a step
+        flops = flops_step / max(launches_per_step, 1)                # per launch, averaged
+        peak = FP64_PEAK_TFLOPS if prec64 else FP32_PEAK_TFLOPS
+        achieved = flops_step * args.steps / (col_ms / 1e3) / 1e12 if col_ms > 0 else 0.0
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_columns (recurrence + gradient sweep)",
+                "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz" if prec64 else
+                               "derived: float32 128 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                "kernel_avg_ms": col_avg_s * 1e3, "flops_per_launch": flops,
+                "launches_per_step": launches_per_step}
     kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4) for k, v in prof.items()}
-
-    # CPU baseline: the oracle on the host cores, a bounded sample
-    times = oracle_step_time(problem, budget_s=args.cpu_budget, max_steps=30)
-    cpu_value = len(times) / sum(times)
-
-    P, N = problem.P, ctx.count
+    cpu_value, cpu_sample = (None, "skipped") if args.cpu_budget <= 0 else oracle_baseline(kind, problems, args.cpu_budget)
+    P_tot, M_tot, cnt = ctx.total_params, ctx.total_metric, ctx.count
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec64 else "f32 (f64 accumulation, assembly, solve)",
         "data": "synthetic",
-        "config": {"workload": f"{name}: {DESCRIPTION[name]}", "n_qubits": problem.n, "P": P,
+        "config": {"workload": f"{name}: {DESCRIPTION[name]}", "instances": cnt,
+                   "n_qubits": sorted({p.n for p in problems}), "P_total": P_tot,
                    "precision": "c128" if prec64 else "c64",
+                   "path": "streaming" if kind == "stream" else "on-chip",
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
         "max_err_vs_oracle": err,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_columns (recurrence + gradient sweep)",
-                     "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz" if prec64 else
-                                    "derived: float32 128 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                     "kernel_avg_ms": col_avg_s * 1e3, "flops_per_launch": flops},
+        "roofline": roof,
         "kernel_share": kernel_share,
-        "cpu_baseline": {"value": cpu_value, "unit": "steps/s", "cores": cpu_threads_used(problem.n), "kind": "oracle",
-                         "sample": f"{len(times)} full oracle QNG steps of the same workload ({sum(times):.1f} s)"},
-        "e2e": {"value": steps_total / (e2e_ms / 1e3), "unit": "steps/s", "h2d_bytes_per_step": 8 * P,
-                "d2h_bytes_per_step": 8 * (P * P + 2 * P + N)},
+        "cpu_baseline": {"value": cpu_value, "unit": "steps/s",
+                         "cores": cpu_threads_used(max(p.n for p in problems)), "kind": "oracle", "sample": cpu_sample},
+        "e2e": {"value": world / (e2e_ms_per_step / 1e3), "unit": "steps/s", "h2d_bytes_per_step": 8 * P_tot,
+                "d2h_bytes_per_step": 8 * (M_tot + 2 * P_tot + cnt)},
         "gpu_launches": int(launches0),
         "clocks": {k: ck[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_threads_used(n: int) -> int:
+    # the oracle's loops only go parallel for states of at least 2^16 amplitudes
+    from oracle import oracle as O
+    return O.num_threads() if n >= 16 else 1
 
 
 def main():
@@ -301,8 +408,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rand12_p192_c128")
-    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--workload", default="rand12_p192_c128", choices=sorted(DESCRIPTION))
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline (0: skip)")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle accuracy check")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -310,9 +418,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     name = args.workload
-    problem = workloads()[name]()
+    make, kind = workloads()[name]
+    made = make()
+    problems = made if isinstance(made, list) else [made]
     if args.impl == "reference":
-        run_reference(args, name, problem, rank, world)
+        run_reference(args, name, problems, kind, rank, world)
         return
     if world > 1:
         import torch
@@ -320,7 +430,7 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", init_method="env://")
     try:
-        run_ours(args, name, problem, rank, world, local_rank)
+        run_ours(args, name, problems, kind, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

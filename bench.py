@@ -335,7 +335,8 @@ def run_ours(args, name, problems, kind, rank, world, local_rank):
 
     if rank != 0:
         return
-    value = args.steps * world / (ms_max / 1e3)
+    # replicas: every rank does a whole step; sharded batch: the ranks together do one step
+    value = args.steps * (1 if args.sharded else world) / (ms_max / 1e3)
     col_ms, col_n = prof["columns"]
     prec64 = prec == W.C128
     if kind == "stream":
@@ -382,7 +383,8 @@ def run_ours(args, name, problems, kind, rank, world, local_rank):
                    "precision": "c128" if prec64 else "c64",
                    "path": "streaming" if kind == "stream" else "on-chip",
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
-                   "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
+                   "parallelism": ("batch instances sharded over GPUs (LPT by work), no collective on the data path"
+                                   if args.sharded else "independent replica per GPU" if world > 1 else "single GPU")},
         "max_err_vs_oracle": err,
         "roofline": roof,
         "kernel_share": kernel_share,
@@ -411,6 +413,9 @@ def main():
     ap.add_argument("--workload", default="rand12_p192_c128", choices=sorted(DESCRIPTION))
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline (0: skip)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle accuracy check")
+    ap.add_argument("--shard", action="store_true",
+                    help="batch workloads under torchrun: split the instances over the ranks (strong scaling) "
+                         "instead of one replica per rank")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -421,6 +426,11 @@ def main():
     make, kind = workloads()[name]
     made = make()
     problems = made if isinstance(made, list) else [made]
+    args.sharded = False
+    if args.shard and kind == "batch" and world > 1:
+        from paper_2011_02991_gb300 import dist as D
+        problems = [problems[b] for b in D.shard_batch(problems, world)[rank]]
+        args.sharded = True
     if args.impl == "reference":
         run_reference(args, name, problems, kind, rank, world)
         return

@@ -176,7 +176,7 @@ qng_status qng_set_shape(qng_ctx *ctx, int n_qubits, int cluster_log2, int threa
 qng_status qng_sync(qng_ctx *ctx);
 
 /* Launch-shape controls (used by the autotuner; 0 leaves a value on automatic):
- * cluster_log2 = log2 of CTAs per state (0..3), threads = CTA size (64..1024, a multiple of 32).
+ * cluster_log2 = log2 of CTAs per state (0..3), threads = CTA size (64..256, a multiple of 32).
  * For batched contexts the settings apply to the instances with n_qubits >= min_qubits. */
 qng_status qng_set_tuning(qng_ctx *ctx, int min_qubits, int cluster_log2, int threads);
 
@@ -186,6 +186,11 @@ qng_status qng_set_tuning(qng_ctx *ctx, int min_qubits, int cluster_log2, int th
  * change re-plans the context; if the workspace already set is then too small the call returns
  * QNG_ERR_WORKSPACE and keeps the old path (query qng_workspace_size before setting a workspace). */
 qng_status qng_set_path(qng_ctx *ctx, int path);
+
+/* Streaming path only: HBM bytes one qng_step moves through the pass schedule (registers loaded
+ * and stored by every pass), split into the metric columns and the rest (forward, energy, adjoint),
+ * and the number of inner-product steps (elements) of the metric. Zeros on the on-chip path. */
+qng_status qng_stream_traffic(const qng_ctx *ctx, int64_t *metric_bytes, int64_t *other_bytes, int64_t *metric_passes);
 
 /* Kernel timing with CUDA events recorded on the context's stream around every launch.
  * qng_profile(ctx, 1) starts recording, qng_profile(ctx, 0) stops. qng_profile_read waits for the

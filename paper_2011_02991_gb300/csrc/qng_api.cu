@@ -639,7 +639,7 @@ qng_status qng_set_stream(qng_ctx *c, void *stream) {
 qng_status qng_set_tuning(qng_ctx *c, int min_qubits, int cluster_log2, int threads) {
     if (!c) return QNG_ERR_ARG;
     if (cluster_log2 < -1 || cluster_log2 > kMaxClusterLog2) return QNG_ERR_ARG;
-    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32)) return QNG_ERR_ARG;
+    if (threads != 0 && (threads < 64 || threads > 256 || threads % 32)) return QNG_ERR_ARG;
     const int old_min = c->tune_min_qubits, old_cl = c->tune_cl, old_th = c->tune_threads;
     c->tune_min_qubits = min_qubits;
     c->tune_cl = cluster_log2 == 0 && threads == 0 && min_qubits == 0 ? -1 : cluster_log2;
@@ -871,7 +871,7 @@ qng_status qng_get_tuning(const qng_ctx *c, int n_qubits, int *cluster_log2, int
 qng_status qng_set_shape(qng_ctx *c, int n_qubits, int cluster_log2, int threads) {
     if (!c || n_qubits < 1 || n_qubits > kMaxQubits) return QNG_ERR_ARG;
     if (cluster_log2 < -1 || cluster_log2 > kMaxClusterLog2) return QNG_ERR_ARG;
-    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32)) return QNG_ERR_ARG;
+    if (threads != 0 && (threads < 64 || threads > 256 || threads % 32)) return QNG_ERR_ARG;
     const int ocl = c->tuned_cl[n_qubits], oth = c->tuned_threads[n_qubits];
     c->tuned_cl[n_qubits] = cluster_log2;
     c->tuned_threads[n_qubits] = threads;
@@ -885,6 +885,25 @@ qng_status qng_set_shape(qng_ctx *c, int n_qubits, int cluster_log2, int threads
         return s != QNG_OK ? s : QNG_ERR_WORKSPACE;
     }
     if (c->ws) return upload(c);
+    return QNG_OK;
+}
+
+qng_status qng_stream_traffic(const qng_ctx *c, int64_t *metric_bytes, int64_t *other_bytes, int64_t *metric_passes) {
+    if (!c) return QNG_ERR_ARG;
+    int64_t mb = 0, ob = 0, mp = 0;
+    if (c->streaming) {
+        const int64_t reg = (int64_t)amp_bytes(c->precision) << c->inst[0].n;
+        for (const large::Launch &L : c->sched.launches) {
+            if (L.kind != large::Launch::Pass) continue;
+            const large::PassDesc &pd = c->sched.passes[L.pass];
+            const int64_t b = reg * (__builtin_popcount(pd.loadmask) + __builtin_popcount(pd.storemask));
+            if (L.segment == large::kSegMetric) { mb += b; ++mp; }
+            else ob += b;
+        }
+    }
+    if (metric_bytes) *metric_bytes = mb;
+    if (other_bytes) *other_bytes = ob;
+    if (metric_passes) *metric_passes = mp;
     return QNG_OK;
 }
 

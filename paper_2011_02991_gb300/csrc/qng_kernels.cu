@@ -528,7 +528,7 @@ __global__ void k_coef(const double *theta, DevCoef *coef, int64_t total, int32_
 // ------------------------------------------------------------------------------------------
 // k_forward: one cluster per instance of the group.
 template <typename R>
-__global__ void __launch_bounds__(1024) k_forward(Work w, int group_first, int cl, int want_eta) {
+__global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl, int want_eta) {
     using cx = typename CX<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const DevInst in = w.inst[w.group_inst[group_first + (blockIdx.x >> cl)]];
@@ -548,13 +548,18 @@ __global__ void __launch_bounds__(1024) k_forward(Work w, int group_first, int c
     if (e.rank == 0 && threadIdx.x == 0) scales[0] = 1.0;
     __syncthreads();
 
+    DevParam pk_n;
+    DevCoef co_n;
+    if (in.P > 0) { pk_n = w.param[in.param_tab]; co_n = w.coef[in.param_off]; }
     for (int k = 0; k < in.P; ++k) {
-        const DevParam pk = w.param[in.param_tab + k];
+        const DevParam pk = pk_n;
+        const DevCoef co = co_n;
+        if (k + 1 < in.P) { pk_n = w.param[in.param_tab + k + 1]; co_n = w.coef[in.param_off + k + 1]; }
         if (pk.diag_count < 0)
             for (int f = 0; f < pk.fix_count; ++f) e.fixed_gate(w.fixed[pk.fix_begin + f], scale);
         const bool pre = pk.diag_count > 0 || pk.zmask != 0;
         double fs;
-        const Rot<R> rot = make_rot<R>(w.coef[in.param_off + k], false, fs);
+        const Rot<R> rot = make_rot<R>(co, false, fs);
         cx *out = ckpt + (uint64_t)(k + 1) * N;
         fwd_step<R>(e, out, pk, rot, pre, w.diag);
         if (std::is_same<R, double>::value) scale *= fs;
@@ -606,7 +611,7 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
 // One cluster per work item, or (queue != nullptr) a persistent grid of clusters that take work
 // items, longest first, from a device counter until all num_work are done.
 template <typename R>
-__global__ void __launch_bounds__(1024) k_columns(Work w, int work_first, int cl, int max_P, int *queue, int num_work) {
+__global__ void __launch_bounds__(256, 3) k_columns(Work w, int work_first, int cl, int max_P, int *queue, int num_work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int item_sh;
     if (!queue) {
@@ -728,22 +733,45 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
     const bool want_im = grad_col;
     RA acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // acc[k]: this thread's partial sum of step s - k
     int cnt = 0;
+    constexpr bool kScaled = std::is_same<R, double>::value;
+    __shared__ int rn_flag[2];  // renormalise b after step s (written by thread 0, parity of s)
     for (int s = 0; s < nsteps; ++s) {
         const int i = i0 - s;
         const DevParam pi = w.param[in.param_tab + i];
+        const double sci = scales[i + 1];
         const cx *a = ckpt + (uint64_t)(i + 1) * N;
-        if (threadIdx.x == 0) fac[s] = scales[i + 1] * scale_b;
         const bool rot_on = (i > 0);
         double fs = 1.0;
         const Rot<R> rot = make_rot<R>(w.coef[in.param_off + i], true, fs);
+        if (threadIdx.x == 0) {  // thread 0 owns the scale of b
+            fac[s] = sci * scale_b;
+            rn_flag[s & 1] = 0;
+            if (kScaled && rot_on) {
+                scale_b *= fs;
+                rn_flag[s & 1] = ((int)((__double_as_longlong(scale_b) >> 52) & 0x7ff) < 1023 - 200);
+            }
+        }
         const bool post = rot_on && (pi.diag_count > 0 || pi.zmask != 0);
         const RA part = want_im ? col_step<R, 1>(e, a, pi, rot_on, rot, post, w.diag)
                                 : col_step<R, 0>(e, a, pi, rot_on, rot, post, w.diag);
         if (rot_on) {
-            if (std::is_same<R, double>::value) scale_b *= fs;
-            if (pi.diag_count < 0)
+            if (pi.diag_count < 0) {
                 for (int f = pi.fix_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[pi.fix_begin + f], scale_b);
-            e.maybe_renorm(scale_b);
+                if (threadIdx.x == 0 && kScaled)
+                    rn_flag[s & 1] = ((int)((__double_as_longlong(scale_b) >> 52) & 0x7ff) < 1023 - 200);
+                __syncthreads();
+            }
+            if constexpr (kScaled) {
+                if (rn_flag[s & 1]) {  // rare: fold 2^-200 into the vector (exact)
+                    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+                        cx x = e.buf[l];
+                        x.x *= 0x1p-200; x.y *= 0x1p-200;
+                        e.buf[l] = x;
+                    }
+                    if (threadIdx.x == 0) scale_b *= 0x1p200;
+                    __syncthreads();
+                }
+            }
         }
 #pragma unroll
         for (int k = 7; k > 0; --k) acc[k] = acc[k - 1];
@@ -902,8 +930,12 @@ __device__ __forceinline__ SolveSmem solve_smem(unsigned char *smem, int R, int 
     return s;
 }
 
+// named barrier of warps 0..3 (threads 0..127)
+__device__ __forceinline__ void sync128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned char tri_r[kNb * (kNb - 1) / 2], tri_c[kNb * (kNb - 1) / 2];
     const int C = 1 << cl;
     const int b = blockIdx.x >> cl;
     const int rank = cl ? (int)cg::this_cluster().block_rank() : 0;
@@ -914,14 +946,20 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     const double *sg = w.sigma + in.param_off;
     const double *L = w.L + in.metric_off;
     const double *gr = w.gradraw + in.param_off;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5, tid = threadIdx.x;
     auto csync = [&]() { if (cl) cg::this_cluster().sync(); else __syncthreads(); };
     auto rptr = [&](double *p, int r) -> double * { return cl ? cg::this_cluster().map_shared_rank(p, r) : p; };
     const int nblk = (P + kNb - 1) / kNb;
     const int nown = (rank < P) ? (P - 1 - rank) / C + 1 : 0;
 
+    // lower-triangle enumeration of a (kNb-1) x (kNb-1) block by rows: entry t <-> (r, c), c <= r
+    if (tid == 0) {
+        int t = 0;
+        for (int r = 0; r < kNb - 1; ++r)
+            for (int c = 0; c <= r; ++c) { tri_r[t] = (unsigned char)r; tri_c[t] = (unsigned char)c; ++t; }
+    }
     // assembly of own rows, outputs
-    for (int t = threadIdx.x; t < nown * P; t += blockDim.x) {
+    for (int t = tid; t < nown * P; t += blockDim.x) {
         const int il = t / P, j = t % P, i = il * C + rank;
         double v;
         if (i == j) v = 0.25 * (1.0 - sg[i] * sg[i]);
@@ -930,29 +968,25 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
         if (a.g_out) a.g_out[in.metric_off + (int64_t)i * P + j] = v;
         sm.A[(size_t)il * P + j] = v + (i == j ? a.lambda : 0.0);
     }
-    for (int il = threadIdx.x; il < nown; il += blockDim.x) sm.b[il] = -a.dt * gr[il * C + rank];
+    for (int il = tid; il < nown; il += blockDim.x) sm.b[il] = -a.dt * gr[il * C + rank];
     if (rank == 0) {
         if (a.grad_out)
-            for (int k = threadIdx.x; k < P; k += blockDim.x) a.grad_out[in.param_off + k] = gr[k];
+            for (int k = tid; k < P; k += blockDim.x) a.grad_out[in.param_off + k] = gr[k];
         if (a.sigma_out)
-            for (int k = threadIdx.x; k < P; k += blockDim.x) a.sigma_out[in.param_off + k] = sg[k];
-        if (a.energy_out && threadIdx.x == 0) a.energy_out[b] = w.energy[b];
+            for (int k = tid; k < P; k += blockDim.x) a.sigma_out[in.param_off + k] = sg[k];
+        if (a.energy_out && tid == 0) a.energy_out[b] = w.energy[b];
     }
-    if (threadIdx.x == 0) *sm.flag = 0;
+    if (tid == 0) *sm.flag = 0;
     __syncthreads();
     csync();  // every CTA is running before any distributed shared memory access
-    // push the first diagonal block (rows 0..nb-1) and its b entries
-    auto push_diag = [&](int kb) {
+    auto push_diag = [&](int kb) {  // rows of diagonal block kb (own ones) and their b entries, to every CTA
         const int c0 = kb * kNb, nb = min(kNb, P - c0);
         double *dst = sm.Ld + (size_t)kb * kNb * kNb;
-        for (int t = threadIdx.x; t < nb * (nb + 1); t += blockDim.x) {
-            const int r = t / (nb + 1), c = t % (nb + 1), i = c0 + r;
+        for (int t = tid; t < nb * (nb + 1) * C; t += blockDim.x) {
+            const int q = t % C, e = t / C, r = e / (nb + 1), c = e % (nb + 1), i = c0 + r;
             if (i % C != rank) continue;
-            const double v = (c < nb) ? ((c <= r) ? sm.A[(size_t)(i / C) * P + c0 + c] : 0.0) : sm.b[i / C];
-            for (int q = 0; q < C; ++q) {
-                if (c < nb) rptr(dst, q)[r * kNb + c] = v;
-                else rptr(sm.ys, q)[i] = v;
-            }
+            if (c < nb) rptr(dst, q)[r * kNb + c] = (c <= r) ? sm.A[(size_t)(i / C) * P + c0 + c] : 0.0;
+            else rptr(sm.ys, q)[i] = sm.b[i / C];
         }
     };
     push_diag(0);
@@ -962,25 +996,28 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
         const int c0 = kb * kNb, nb = min(kNb, P - c0), t0 = c0 + nb;
         double *D = sm.Ld + (size_t)kb * kNb * kNb;
         __syncthreads();
-        csync();  // (B)
-        // (C) factor the diagonal block in place and solve its part of L y = b (warp 0)
-        if (wid == 0) {
+        csync();  // (B) the diagonal block and its b entries are here
+        // (C) factor the diagonal block in place (warps 0..3), then its part of L y = b (warp 0)
+        if (tid < 128) {
             for (int k = 0; k < nb; ++k) {
-                const double d = D[k * kNb + k];
-                if (!(d > 0.0)) { if (lane == 0) *sm.flag = 1; break; }
-                const double iv = rsqrt(d);
-                __syncwarp();
-                if (lane > k && lane < nb) D[lane * kNb + k] *= iv;
-                if (lane == 0) { D[k * kNb + k] = d * iv; sm.inv[k] = iv; }
-                __syncwarp();
-                for (int t = lane; t < nb * nb; t += 32) {
-                    const int r = t / nb, c = t % nb;
-                    if (c > k && c <= r) D[r * kNb + c] = fma(-D[r * kNb + k], D[c * kNb + k], D[r * kNb + c]);
+                if (tid == 0) {
+                    const double d = D[k * kNb + k];
+                    if (!(d > 0.0)) *sm.flag = 1;
+                    else { const double iv = rsqrt(d); D[k * kNb + k] = d * iv; sm.inv[k] = iv; }
                 }
-                __syncwarp();
+                sync128();
+                if (*sm.flag) break;
+                const double iv = sm.inv[k];
+                if (tid > k && tid < nb) D[tid * kNb + k] *= iv;
+                sync128();
+                const int s = nb - k - 1;
+                if (tid < s * (s + 1) / 2) {
+                    const int r = k + 1 + tri_r[tid], c = k + 1 + tri_c[tid];
+                    D[r * kNb + c] = fma(-D[r * kNb + k], D[c * kNb + k], D[r * kNb + c]);
+                }
+                sync128();
             }
-            __syncwarp();
-            if (!*sm.flag) {
+            if (wid == 0 && !*sm.flag) {
                 for (int c = 0; c < nb; ++c) {
                     if (lane == 0) sm.ys[c0 + c] *= sm.inv[c];
                     __syncwarp();
@@ -992,46 +1029,40 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
         }
         __syncthreads();
         if (*sm.flag) { failed = true; break; }  // identical in every CTA: all stop together
-        // (D) own rows: diagonal-block rows take L, rows below become panel rows (pushed)
-        for (int il = threadIdx.x; il < nown; il += blockDim.x) {
-            const int i = il * C + rank;
-            double *row = sm.A + (size_t)il * P;
-            if (i >= c0 && i < t0) {
-                for (int c = 0; c <= i - c0; ++c) row[c0 + c] = D[(i - c0) * kNb + c];
-            } else if (i >= t0) {
-                double pr[kNb];
-#pragma unroll
-                for (int c = 0; c < kNb; ++c) pr[c] = (c < nb) ? row[c0 + c] : 0.0;
-                double bi = sm.b[il];
-#pragma unroll
-                for (int c = 0; c < kNb; ++c) {  // right-looking: short dependency chain per column
-                    if (c < nb) {
-                        const double v = pr[c] * sm.inv[c];
-                        pr[c] = v;
-                        bi = fma(-v, sm.ys[c0 + c], bi);
-#pragma unroll
-                        for (int c2 = c + 1; c2 < kNb; ++c2)
-                            if (c2 < nb) pr[c2] = fma(-v, D[c2 * kNb + c], pr[c2]);
-                    }
-                }
-                sm.b[il] = bi;
-                const int jj = i - t0;
-#pragma unroll
-                for (int c = 0; c < kNb; ++c) {
-                    if (c < nb) {
-                        row[c0 + c] = pr[c];
-                        for (int q = 0; q < C; ++q) rptr(sm.PLt, q)[(size_t)c * P + jj] = pr[c];
-                    }
-                }
+        // (D) own rows of the diagonal block take L; own rows below become panel rows
+        const int first_below = (t0 > rank) ? (t0 - rank + C - 1) / C : 0;  // first own il with i >= t0
+        const int npr = max(0, nown - first_below);
+        for (int t = tid; t < nown * nb; t += blockDim.x) {
+            const int il = t / nb, c = t % nb, i = il * C + rank;
+            if (i >= c0 && i < t0 && c <= i - c0) sm.A[(size_t)il * P + c0 + c] = D[(i - c0) * kNb + c];
+        }
+        for (int c = 0; c < nb; ++c) {  // right-looking triangular solve of the panel, spread over the CTA
+            for (int t = tid; t < npr; t += blockDim.x) {
+                const int il = first_below + t;
+                double *row = sm.A + (size_t)il * P + c0;
+                const double v = row[c] * sm.inv[c];
+                row[c] = v;
+                sm.b[il] = fma(-v, sm.ys[c0 + c], sm.b[il]);
             }
+            __syncthreads();
+            const int rest = nb - c - 1;
+            for (int t = tid; t < npr * rest; t += blockDim.x) {
+                const int il = first_below + t / rest, c2 = c + 1 + t % rest;
+                double *row = sm.A + (size_t)il * P + c0;
+                row[c2] = fma(-row[c], D[c2 * kNb + c], row[c2]);
+            }
+            __syncthreads();
+        }
+        for (int t = tid; t < npr * nb * C; t += blockDim.x) {  // push the panel rows to every CTA
+            const int q = t % C, e = t / C, il = first_below + e / nb, c = e % nb;
+            const int jj = il * C + rank - t0;
+            rptr(sm.PLt, q)[(size_t)c * P + jj] = sm.A[(size_t)il * P + c0 + c];
         }
         __syncthreads();
-        csync();  // (E)
+        csync();  // (E) the whole panel is here
         // (F) trailing update of own rows: A_ij -= sum_c L_ic L_jc for t0 <= j <= i
-        for (int il = wid; il < nown; il += nw) {
-            const int i = il * C + rank;
-            if (i < t0) continue;
-            const int ii = i - t0;
+        for (int il = first_below + wid; il < nown; il += nw) {
+            const int i = il * C + rank, ii = i - t0;
             double *row = sm.A + (size_t)il * P;
             for (int j = t0 + lane; j <= i; j += 32) {
                 const int jj = j - t0;
@@ -1045,7 +1076,7 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
         if (kb + 1 < nblk) push_diag(kb + 1);
     }
     if (failed) {
-        if (rank == 0 && threadIdx.x == 0) atomicCAS(w.status, 0, (int)QNG_ERR_NOT_SPD);
+        if (rank == 0 && tid == 0) atomicCAS(w.status, 0, (int)QNG_ERR_NOT_SPD);
         csync();
         return;
     }
@@ -1054,16 +1085,14 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
         const int c0 = kb * kNb, nb = min(kNb, P - c0), t0 = c0 + nb;
         double *part = sm.part + (kb & 1) * C * kNb;
         const double *D = sm.Ld + (size_t)kb * kNb * kNb;
-        if (wid == 0) {
-            for (int c = 0; c < nb; ++c) {
-                double v = 0.0;
-                for (int il = lane; il < nown; il += 32) {
-                    const int i = il * C + rank;
-                    if (i >= t0) v = fma(sm.A[(size_t)il * P + c0 + c], sm.ys[i], v);
-                }
-                v = warp_sum(v);
-                if (lane < C) rptr(part, lane)[rank * kNb + c] = v;
+        for (int c = wid; c < nb; c += nw) {  // partial sums over own rows below the block, one warp per column
+            double v = 0.0;
+            for (int il = lane; il < nown; il += 32) {
+                const int i = il * C + rank;
+                if (i >= t0) v = fma(sm.A[(size_t)il * P + c0 + c], sm.ys[i], v);
             }
+            v = warp_sum(v);
+            if (lane < C) rptr(part, lane)[rank * kNb + c] = v;
         }
         __syncthreads();
         csync();
@@ -1086,7 +1115,7 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
         __syncthreads();
     }
     if (rank == 0)
-        for (int k = threadIdx.x; k < P; k += blockDim.x) a.dtheta_out[in.param_off + k] = sm.ys[k];
+        for (int k = tid; k < P; k += blockDim.x) a.dtheta_out[in.param_off + k] = sm.ys[k];
     csync();
 }
 

@@ -64,6 +64,7 @@ SYMBOLS = {
     "qng_last_launch_count": [_vp, _i64p],
     "qng_profile": [_vp, ctypes.c_int],
     "qng_set_path": [_vp, ctypes.c_int],
+    "qng_stream_traffic": [_vp, _i64p, _i64p, _i64p],
     "qng_graph_capture": [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp],
     "qng_graph_launch": [_vp],
     "qng_autotune": [_vp, _vp, ctypes.c_int, _i64p],
@@ -277,6 +278,12 @@ class Context:
 
     def set_shape(self, n_qubits: int, cluster_log2: int, threads: int):
         _chk(load().qng_set_shape(self._h, int(n_qubits), int(cluster_log2), int(threads)), "qng_set_shape")
+
+    def stream_traffic(self):
+        """(metric_bytes, other_bytes, metric_passes) of one step on the streaming path."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _chk(load().qng_stream_traffic(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "qng_stream_traffic")
+        return a.value, b.value, c.value
 
     def sync(self):
         _chk(load().qng_sync(self._h), "qng_sync")

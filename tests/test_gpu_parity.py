@@ -72,7 +72,7 @@ def test_cluster_distribution(qng, oracle, cl, precision):
     check_problem(qng, oracle, p, precision, tuning=(0, cl, 64))
 
 
-@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+@pytest.mark.parametrize("threads", [64, 128, 256])
 def test_cta_sizes(qng, oracle, threads):
     p = W.random_problem(8, 50, 8, 77, W.C128)
     check_problem(qng, oracle, p, W.C128, tuning=(0, 1, threads))

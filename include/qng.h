@@ -167,10 +167,14 @@ qng_status qng_graph_launch(qng_ctx *ctx);
  * workspace than the one set are skipped. Drops a captured graph. */
 qng_status qng_autotune(qng_ctx *ctx, const double *theta, int reps, int64_t *report);
 
-/* Launch shape used for instances of n_qubits qubits (after defaults, autotuning and qng_set_shape),
- * and a manual override (cluster_log2 -1 and threads 0 restore the default). */
-qng_status qng_get_tuning(const qng_ctx *ctx, int n_qubits, int *cluster_log2, int *threads);
-qng_status qng_set_shape(qng_ctx *ctx, int n_qubits, int cluster_log2, int threads);
+/* Launch shape used for instances of n_qubits qubits (after defaults, autotuning and qng_set_shape):
+ * cluster_log2 = log2 of CTAs per state, threads = CTA size of the column kernel (64..256),
+ * forward_threads = CTA size of the checkpoint sweep (64..512); any output pointer may be NULL.
+ * qng_set_shape is the manual override (cluster_log2 -1, threads 0 and forward_threads 0 restore
+ * the defaults); QNG_ERR_ARG for values out of range, QNG_ERR_WORKSPACE (old shape kept) when the
+ * new shape needs more workspace than the one set. */
+qng_status qng_get_tuning(const qng_ctx *ctx, int n_qubits, int *cluster_log2, int *threads, int *forward_threads);
+qng_status qng_set_shape(qng_ctx *ctx, int n_qubits, int cluster_log2, int threads, int forward_threads);
 
 /* Wait for the context's stream, then return (and clear) the device-side status word. */
 qng_status qng_sync(qng_ctx *ctx);

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/qng.h: argument validation, the device tables,
 // the workspace layout, launch grouping and the entry points.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -96,6 +97,7 @@ struct qng_ctx {
     // per-qubit-count launch shapes chosen by the autotuner (-1: default)
     int tuned_cl[kMaxQubits + 1];
     int tuned_threads[kMaxQubits + 1];
+    int tuned_fwd[kMaxQubits + 1];
     int64_t last_launches = 0;
     // kernel timing (qng_profile)
     bool profiling = false;
@@ -106,7 +108,7 @@ struct qng_ctx {
     int64_t prof_n[QNG_KERNEL_CLASSES] = {0, 0, 0, 0};
 
     qng_ctx() {
-        for (int k = 0; k <= kMaxQubits; ++k) { tuned_cl[k] = -1; tuned_threads[k] = 0; }
+        for (int k = 0; k <= kMaxQubits; ++k) { tuned_cl[k] = -1; tuned_threads[k] = 0; tuned_fwd[k] = 0; }
     }
     ~qng_ctx() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -151,6 +153,12 @@ size_t amp_bytes(int precision) { return precision == QNG_C128 ? 16 : 8; }
 int default_cl(int n, int precision) {
     const int base = 9;  // measured best for both precisions at 12 qubits: 8 CTAs of 512 amplitudes
     return std::max(0, std::min(kMaxClusterLog2, n - base));
+}
+
+// The checkpoint sweep has one barrier per parameter and little work between barriers: two
+// amplitudes per thread (64..512 threads) hide more float64 latency than the column kernel's shape.
+int default_fwd_threads(int nl) {
+    return std::max(64, std::min(512, (1 << nl) / 2));
 }
 
 int default_threads(int nl) {
@@ -275,6 +283,7 @@ qng_status plan(qng_ctx *c) {
                 pending.push_back(&g);
             }
         }
+        set_zruns(c->t_param.data() + d.param_tab, h.P);
         d.w_begin = (int32_t)c->t_fixed.size();
         d.w_count = (int32_t)pending.size();
         for (const qng_gate *g : pending) c->t_fixed.push_back(DevFixed{g->kind, g->q0, g->q1, 0});
@@ -293,8 +302,8 @@ qng_status plan(qng_ctx *c) {
     c->streaming = c->count == 1 && (c->path == 2 || (c->path == 0 && c->inst[0].n > kMaxQubitsSmall));
     if (c->streaming) return plan_streaming(c, scale_n);
 
-    // groups: instances sharing (cluster size, CTA size)
-    std::vector<std::pair<int, int>> shape(c->count);
+    // groups: instances sharing (cluster size, column CTA size, forward CTA size)
+    std::vector<std::array<int, 3>> shape(c->count);
     for (int b = 0; b < c->count; ++b) {
         const int n = c->inst[b].n;
         int cl = default_cl(n, c->precision);
@@ -304,16 +313,19 @@ qng_status plan(qng_ctx *c) {
         int th = default_threads(n - cl);
         if (c->tuned_threads[n] > 0) th = c->tuned_threads[n];
         if (c->tune_threads > 0 && n >= c->tune_min_qubits) th = c->tune_threads;
-        shape[b] = {cl, th};
+        int fth = default_fwd_threads(n - cl);
+        if (c->tuned_fwd[n] > 0) fth = c->tuned_fwd[n];
+        shape[b] = {cl, th, fth};
         c->t_inst[b].cl = cl;
     }
-    std::vector<std::pair<int, int>> keys(shape);
+    std::vector<std::array<int, 3>> keys(shape);
     std::sort(keys.begin(), keys.end());
     keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
     for (const auto &key : keys) {
         Group g;
-        g.cl = key.first;
-        g.threads = key.second;
+        g.cl = key[0];
+        g.threads = key[1];
+        g.fwd_threads = key[2];
         g.first_inst = (int)c->t_group_inst.size();
         std::vector<DevWork> items;
         for (int b = 0; b < c->count; ++b) {
@@ -847,6 +859,21 @@ qng_status qng_autotune(qng_ctx *c, const double *theta, int reps, int64_t *repo
         c->tuned_cl[n] = best_cl;
         c->tuned_threads[n] = best_th;
         if (st != QNG_OK) break;
+        // the checkpoint sweep's CTA size, at the chosen cluster and column shape
+        if (best_cl < 0) continue;
+        int best_fth = c->tuned_fwd[n];
+        for (int fth : {64, 128, 256, 512}) {
+            if ((1 << (n - best_cl)) < fth) continue;
+            c->tuned_fwd[n] = fth;
+            if (plan(c) != QNG_OK || c->ws_bytes > bytes) continue;
+            if ((st = upload(c)) != QNG_OK) break;
+            float ms = 0.f;
+            if ((st = time_step(ms)) != QNG_OK) break;
+            ++tried;
+            if (ms < best) { best = ms; best_fth = fth; }
+        }
+        c->tuned_fwd[n] = best_fth;
+        if (st != QNG_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -856,30 +883,37 @@ qng_status qng_autotune(qng_ctx *c, const double *theta, int reps, int64_t *repo
     return st != QNG_OK ? st : s2;
 }
 
-qng_status qng_get_tuning(const qng_ctx *c, int n_qubits, int *cluster_log2, int *threads) {
+qng_status qng_get_tuning(const qng_ctx *c, int n_qubits, int *cluster_log2, int *threads, int *forward_threads) {
     if (!c || n_qubits < 1 || n_qubits > kMaxQubits) return QNG_ERR_ARG;
     int cl = default_cl(n_qubits, c->precision);
     if (c->tuned_cl[n_qubits] >= 0) cl = c->tuned_cl[n_qubits];
     cl = std::max(0, std::min(cl, std::min(kMaxClusterLog2, n_qubits - 1)));
     int th = default_threads(n_qubits - cl);
     if (c->tuned_threads[n_qubits] > 0) th = c->tuned_threads[n_qubits];
+    int fth = default_fwd_threads(n_qubits - cl);
+    if (c->tuned_fwd[n_qubits] > 0) fth = c->tuned_fwd[n_qubits];
     if (cluster_log2) *cluster_log2 = cl;
     if (threads) *threads = th;
+    if (forward_threads) *forward_threads = fth;
     return QNG_OK;
 }
 
-qng_status qng_set_shape(qng_ctx *c, int n_qubits, int cluster_log2, int threads) {
+qng_status qng_set_shape(qng_ctx *c, int n_qubits, int cluster_log2, int threads, int forward_threads) {
     if (!c || n_qubits < 1 || n_qubits > kMaxQubits) return QNG_ERR_ARG;
     if (cluster_log2 < -1 || cluster_log2 > kMaxClusterLog2) return QNG_ERR_ARG;
     if (threads != 0 && (threads < 64 || threads > 256 || threads % 32)) return QNG_ERR_ARG;
-    const int ocl = c->tuned_cl[n_qubits], oth = c->tuned_threads[n_qubits];
+    if (forward_threads != 0 && (forward_threads < 64 || forward_threads > 512 || forward_threads % 32))
+        return QNG_ERR_ARG;
+    const int ocl = c->tuned_cl[n_qubits], oth = c->tuned_threads[n_qubits], ofth = c->tuned_fwd[n_qubits];
     c->tuned_cl[n_qubits] = cluster_log2;
     c->tuned_threads[n_qubits] = threads;
+    c->tuned_fwd[n_qubits] = forward_threads;
     const size_t old_bytes = c->ws_bytes;
     qng_status s = plan(c);
     if (s != QNG_OK || (c->ws && c->ws_bytes > old_bytes)) {
         c->tuned_cl[n_qubits] = ocl;
         c->tuned_threads[n_qubits] = oth;
+        c->tuned_fwd[n_qubits] = ofth;
         plan(c);
         if (c->ws) upload(c);
         return s != QNG_OK ? s : QNG_ERR_WORKSPACE;

@@ -26,7 +26,20 @@ struct DevParam {
     int32_t diag_begin; // if F_k is all CZ / Z: its sign as (shift, mask) pairs [diag_begin, +diag_count)
     int32_t diag_count; //   of the diag table, plus zmask; diag_count = -1 when F_k is not all diagonal
     uint64_t zmask;     //   single-qubit Z factors of F_k
+    int32_t zrun;       // Z rotations with diagonal F from k on (this one included, at most kZRunMax); 0 if k is not one
+    int32_t pad;
 };
+
+constexpr int kZRunMax = 16;
+
+// Fill DevParam::zrun over the parameters [p, p + P) of one instance.
+inline void set_zruns(DevParam *p, int P) {
+    int run = 0;
+    for (int k = P - 1; k >= 0; --k) {
+        run = (p[k].axis == kAxisZ && p[k].diag_count >= 0) ? run + 1 : 0;
+        p[k].zrun = run < kZRunMax ? run : kZRunMax;
+    }
+}
 
 struct DevFixed {
     int32_t kind;  // QNG_GATE_CZ, CNOT, X, Y, Z, H
@@ -104,7 +117,8 @@ struct Work {
 // A launch group: instances sharing one cluster size and CTA shape.
 struct Group {
     int cl = 0;
-    int threads = 128;
+    int threads = 128;      // CTA size of the column kernel
+    int fwd_threads = 256;  // CTA size of the checkpoint sweep (k_forward)
     int max_n = 0;
     int max_P = 0;
     int first_inst = 0;   // into group_inst

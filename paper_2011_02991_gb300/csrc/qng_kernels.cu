@@ -526,6 +526,87 @@ __global__ void k_coef(const double *theta, DevCoef *coef, int64_t total, int32_
 }
 
 // ------------------------------------------------------------------------------------------
+// A run of m consecutive Z rotations (each with an all-diagonal fixed block, or none) in one
+// elementwise pass: every amplitude goes through the m rotations in registers and each
+// intermediate state is written to its checkpoint; no barrier between the rotations. The float64
+// scale of each checkpoint is the running product of the rotations' factors (uniform, so every
+// thread computes the same sequence and renormalises at the same steps).
+template <typename R, int AMPS>
+__device__ __forceinline__ void fwd_zrun_t(Eng<R> &e, typename CX<R>::T *__restrict__ ckpt, uint64_t N,
+                                           const DevParam *__restrict__ params, const DevCoef *__restrict__ coefs,
+                                           int k0, int m, const DevDiag *__restrict__ dt) {
+    using cx = typename CX<R>::T;
+    constexpr bool kScaled = std::is_same<R, double>::value;
+    cx x[AMPS];
+    uint64_t kk[AMPS];
+#pragma unroll
+    for (int a = 0; a < AMPS; ++a) {
+        const uint32_t l = threadIdx.x + a * blockDim.x;
+        kk[a] = e.base | l;
+        x[a] = e.buf[l];
+    }
+    DevParam pk = params[k0];
+    DevCoef co = coefs[k0];
+    for (int u = 0; u < m; ++u) {  // the thread's amplitudes advance together: AMPS independent chains
+        const int un = u + 1 < m ? u + 1 : u;
+        const DevParam pn = params[k0 + un];  // next step's tables, loaded while this step computes
+        const DevCoef cn = coefs[k0 + un];
+        // sign of the diagonal block F_k on each amplitude: one table read per (shift, mask) pair
+        int par[AMPS];
+#pragma unroll
+        for (int a = 0; a < AMPS; ++a) par[a] = __popcll(kk[a] & pk.zmask);
+        for (int d = 0; d < pk.diag_count; ++d) {
+            const DevDiag dd = dt[pk.diag_begin + d];
+#pragma unroll
+            for (int a = 0; a < AMPS; ++a) par[a] += __popcll(kk[a] & (kk[a] >> dd.shift) & dd.mask);
+        }
+        cx *out = ckpt + (uint64_t)(k0 + u + 1) * N;
+#pragma unroll
+        for (int a = 0; a < AMPS; ++a) {
+            x[a] = flip2(x[a], par[a] & 1);
+            const int beta = (int)((kk[a] >> pk.q) & 1);
+            const cx v = {flip(x[a].y, beta ^ 1), flip(x[a].x, beta)};  // (i Z x)_beta
+            if constexpr (kScaled) {  // forward rotation: t' = -t
+                if (co.caseB) { x[a].x = fma(-co.t, x[a].x, v.x); x[a].y = fma(-co.t, x[a].y, v.y); }
+                else          { x[a].x = fma(-co.t, v.x, x[a].x); x[a].y = fma(-co.t, v.y, x[a].y); }
+            } else {
+                const R c = (R)co.c, sv = (R)(-co.s);
+                x[a].x = fma(sv, v.x, c * x[a].x); x[a].y = fma(sv, v.y, c * x[a].y);
+            }
+            out[kk[a]] = x[a];
+        }
+        pk = pn;
+        co = cn;
+    }
+#pragma unroll
+    for (int a = 0; a < AMPS; ++a) e.buf[threadIdx.x + a * blockDim.x] = x[a];
+}
+
+// returns false (and does nothing) when the CTA shape has no compiled amplitude count
+template <typename R>
+__device__ __forceinline__ bool fwd_zrun(Eng<R> &e, typename CX<R>::T *ckpt, uint64_t N, const DevParam *params,
+                                         const DevCoef *coefs, int k0, int m, const DevDiag *dt, double &scale,
+                                         double *scales, bool write_scales) {
+    if (e.Nl % blockDim.x) return false;
+    const uint32_t amps = e.Nl / blockDim.x;
+    switch (amps) {
+    case 1: fwd_zrun_t<R, 1>(e, ckpt, N, params, coefs, k0, m, dt); break;
+    case 2: fwd_zrun_t<R, 2>(e, ckpt, N, params, coefs, k0, m, dt); break;
+    case 4: fwd_zrun_t<R, 4>(e, ckpt, N, params, coefs, k0, m, dt); break;
+    case 8: fwd_zrun_t<R, 8>(e, ckpt, N, params, coefs, k0, m, dt); break;
+    default: return false;
+    }
+    // the scale sequence of the run (identical in every thread)
+    for (int u = 0; u < m; ++u) {
+        const DevCoef co = coefs[k0 + u];
+        if (std::is_same<R, double>::value) scale *= co.caseB ? -co.f : co.f;
+        if (write_scales) scales[k0 + u + 1] = scale;
+    }
+    __syncthreads();
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
 // k_forward: one cluster per instance of the group.
 template <typename R>
 __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl, int want_eta) {
@@ -552,6 +633,19 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
     DevCoef co_n;
     if (in.P > 0) { pk_n = w.param[in.param_tab]; co_n = w.coef[in.param_off]; }
     for (int k = 0; k < in.P; ++k) {
+        // a run of Z rotations with diagonal fixed blocks: one pass, no barriers in between
+        if (pk_n.zrun > 1) {
+            const int m = pk_n.zrun;
+            // the whole run stays above the renormalisation threshold: each factor is >= 1/sqrt2
+            const int ex = (int)((__double_as_longlong(scale) >> 52) & 0x7ff);
+            if ((!std::is_same<R, double>::value || ex - (m + 1) / 2 - 1 >= 1023 - 200) &&
+                fwd_zrun<R>(e, ckpt, N, w.param + in.param_tab, w.coef + in.param_off, k, m, w.diag, scale, scales,
+                            e.rank == 0 && threadIdx.x == 0)) {
+                k += m - 1;
+                if (k + 1 < in.P) { pk_n = w.param[in.param_tab + k + 1]; co_n = w.coef[in.param_off + k + 1]; }
+                continue;
+            }
+        }
         const DevParam pk = pk_n;
         const DevCoef co = co_n;
         if (k + 1 < in.P) { pk_n = w.param[in.param_tab + k + 1]; co_n = w.coef[in.param_off + k + 1]; }
@@ -563,8 +657,8 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
         cx *out = ckpt + (uint64_t)(k + 1) * N;
         fwd_step<R>(e, out, pk, rot, pre, w.diag);
         if (std::is_same<R, double>::value) scale *= fs;
-        e.maybe_renorm(scale);
-        if (e.rank == 0 && threadIdx.x == 0) scales[k + 1] = scale;
+        if (e.rank == 0 && threadIdx.x == 0) scales[k + 1] = scale;  // the scale of checkpoint k+1 as written
+        e.maybe_renorm(scale);                                         // then the state carried on to k+2
     }
 
     // trailing fixed gates W, then H W psi, <E> and eta = W^dag H W psi
@@ -1173,8 +1267,8 @@ cudaError_t launch_forward(const Work &w, const Group &g, int precision, int wan
     if (g.num_inst == 0) return cudaSuccess;
     const int grid = g.num_inst << g.cl;
     if (precision == QNG_C128)
-        return launch_cluster(k_forward<double>, grid, g.threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
-    return launch_cluster(k_forward<float>, grid, g.threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
+        return launch_cluster(k_forward<double>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
+    return launch_cluster(k_forward<float>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
 }
 
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,

@@ -113,17 +113,19 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
             return QNG_ERR_ARG;
         }
     }
+    set_zruns(params, P);
     if (P == 0) return QNG_OK;  // an empty metric
     if (!theta || !g) return QNG_ERR_ARG;
 
     // launch shape: the defaults of the workspace path
     Group grp;
-    grp.cl = precision == QNG_C128 ? n - 9 : n - 11;
+    grp.cl = n - 9;
     if (grp.cl < 0) grp.cl = 0;
     if (grp.cl > kMaxClusterLog2) grp.cl = kMaxClusterLog2;
     if (grp.cl > n - 1) grp.cl = n - 1;
     const uint32_t Nl = 1u << (n - grp.cl);
     grp.threads = Nl <= 256 ? 64 : (Nl <= 1024 ? 128 : 256);
+    grp.fwd_threads = Nl / 2 < 64 ? 64 : (Nl / 2 > 512 ? 512 : (int)(Nl / 2));
     grp.max_n = n;
     grp.max_P = P;
     grp.first_inst = 0;

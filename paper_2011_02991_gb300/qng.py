@@ -68,8 +68,8 @@ SYMBOLS = {
     "qng_graph_capture": [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp],
     "qng_graph_launch": [_vp],
     "qng_autotune": [_vp, _vp, ctypes.c_int, _i64p],
-    "qng_get_tuning": [_vp, ctypes.c_int, _i32p, _i32p],
-    "qng_set_shape": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "qng_get_tuning": [_vp, ctypes.c_int, _i32p, _i32p, _i32p],
+    "qng_set_shape": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "qng_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), _i64p],
     "qng_destroy": [_vp],
     "qng_status_string": [ctypes.c_int],
@@ -272,12 +272,15 @@ class Context:
         return int(n.value)
 
     def get_tuning(self, n_qubits: int):
-        cl, th = ctypes.c_int32(), ctypes.c_int32()
-        _chk(load().qng_get_tuning(self._h, int(n_qubits), ctypes.byref(cl), ctypes.byref(th)), "qng_get_tuning")
-        return cl.value, th.value
+        """(cluster_log2, column CTA size, checkpoint-sweep CTA size) for n_qubits."""
+        cl, th, fth = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _chk(load().qng_get_tuning(self._h, int(n_qubits), ctypes.byref(cl), ctypes.byref(th), ctypes.byref(fth)),
+             "qng_get_tuning")
+        return cl.value, th.value, fth.value
 
-    def set_shape(self, n_qubits: int, cluster_log2: int, threads: int):
-        _chk(load().qng_set_shape(self._h, int(n_qubits), int(cluster_log2), int(threads)), "qng_set_shape")
+    def set_shape(self, n_qubits: int, cluster_log2: int, threads: int, forward_threads: int = 0):
+        _chk(load().qng_set_shape(self._h, int(n_qubits), int(cluster_log2), int(threads), int(forward_threads)),
+             "qng_set_shape")
 
     def stream_traffic(self):
         """(metric_bytes, other_bytes, metric_passes) of one step on the streaming path."""

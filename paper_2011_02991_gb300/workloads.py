@@ -245,6 +245,45 @@ def config_rand28(seed: int = BASE_SEED + 5, precision: int = C64, n: int = 28, 
     return Problem(f"rand{n}_p{c.num_params}_{tag}", c, h, theta, precision=precision, meta={"seed": seed})
 
 
+def z_run_problem(n: int, num_params: int, seed: int, precision: int = C128, max_run: int = 24,
+                  near_half_pi: bool = False) -> Problem:
+    """Runs of RZ rotations (1..max_run long) separated by RX/RY rotations (test workload).
+
+    Inside a run the fixed gates before each RZ are none, CZ, Z or CZ + Z (all diagonal); with
+    probability 1/8 a CNOT or H is placed instead, which breaks the run. near_half_pi draws the
+    angles from pi/2 +- 0.3 instead of [-pi, pi): each half-angle factor max(|cos|, |sin|) is then
+    close to 2^-1/2, so long circuits drive a running product of them through many binades.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = _CircuitBuilder(n)
+    while b.P < num_params:
+        b.rot(int(rng.choice([RX, RY])), int(rng.integers(n)))
+        for _ in range(int(rng.integers(1, max_run + 1))):
+            if b.P >= num_params:
+                break
+            r = rng.random()
+            if r < 0.125:
+                if n >= 2 and rng.random() < 0.5:
+                    q0, q1 = rng.choice(n, size=2, replace=False)
+                    b.fixed(CNOT, int(q0), int(q1))
+                else:
+                    b.fixed(H, int(rng.integers(n)))
+            elif r < 0.4 and n >= 2:
+                q0, q1 = rng.choice(n, size=2, replace=False)
+                b.fixed(CZ, int(q0), int(q1))
+                if rng.random() < 0.5:
+                    b.fixed(Z, int(rng.integers(n)))
+            elif r < 0.55:
+                b.fixed(Z, int(rng.integers(n)))
+            b.rot(RZ, int(rng.integers(n)))
+    c = b.build()
+    theta = uniform_theta(c.num_params, rng)
+    if near_half_pi:
+        theta = np.pi / 2 + rng.uniform(-0.3, 0.3, c.num_params)
+    h = random_pauli_hamiltonian(n, 2 * n, rng)
+    return Problem(f"zrun_n{n}_p{num_params}", c, h, theta, precision=precision, meta={"seed": seed})
+
+
 def random_problem(n: int, num_gates: int, num_terms: int, seed: int, precision: int = C128) -> Problem:
     """A small random problem with every gate kind (test workload)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -78,6 +78,59 @@ def test_cta_sizes(qng, oracle, threads):
     check_problem(qng, oracle, p, W.C128, tuning=(0, 1, threads))
 
 
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+@pytest.mark.parametrize("fwd_threads", [64, 96, 128, 256, 512])
+def test_z_runs_forward_shapes(qng, oracle, precision, fwd_threads):
+    """Runs of Z rotations with diagonal fixed blocks go through the checkpoint sweep in one pass
+    each: 8, 4, 2 and 1 amplitudes per thread (512 per CTA), and 96 threads (no whole number of
+    amplitudes per thread: one rotation at a time)."""
+    p = W.z_run_problem(10, 160, 5, precision)
+    ctx = qng.Context(p, precision=precision)
+    ctx.set_shape(10, 1, 128, fwd_threads)
+    assert ctx.get_tuning(10) == (1, 128, fwd_threads)
+    out = ctx.step(ctx.theta0(), p.dt, p.lam)
+    ctx.sync()
+    ref = oracle.qng_step(p)
+    for key in ("g", "grad"):
+        assert rel(out[key].cpu(), ref[key]) <= TOL[precision], key
+    if precision == W.C128:
+        assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[precision]
+    else:
+        # Z rotations on Z eigenstates leave directions with g ~ 0 and an exactly zero gradient:
+        # there complex64 rounding of the gradient (~1e-8) is divided by lambda. The step is
+        # checked as the solution of its own float64 system instead.
+        g = out["g"].cpu().numpy().reshape(p.P, p.P)
+        res = (g + p.lam * np.eye(p.P)) @ out["dtheta"].cpu().numpy() + p.dt * out["grad"].cpu().numpy()
+        assert np.linalg.norm(res) <= 1e-10 * p.dt * np.linalg.norm(out["grad"].cpu().numpy())
+
+
+def test_z_runs_small_state(qng, oracle):
+    """64 amplitudes and a 128-thread sweep: more threads than amplitudes."""
+    p = W.z_run_problem(6, 120, 7, W.C128)
+    ctx = qng.Context(p, precision=W.C128)
+    ctx.set_shape(6, 0, 64, 128)
+    out = ctx.step(ctx.theta0(), p.dt, p.lam)
+    ctx.sync()
+    ref = oracle.qng_step(p)
+    assert rel(out["g"].cpu(), ref["g"]) <= TOL[W.C128]
+    assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[W.C128]
+
+
+def test_z_runs_long_circuit_renormalisation(qng, oracle):
+    """P = 1000 on 7 qubits (2 amplitudes per thread in the sweep): the float64 scale of the scaled
+    complex128 rotations falls below 2^-200 several times, also around Z runs. Angles near pi/2
+    make every factor max(|cos|, |sin|) of a half angle close to 2^-1/2 and mix both forms."""
+    p = W.z_run_problem(7, 1000, 6, W.C128, near_half_pi=True)
+    ctx = qng.Context(p, precision=W.C128)
+    ctx.set_shape(7, 0, 64, 64)
+    out = ctx.step(ctx.theta0(), p.dt, p.lam)
+    ctx.sync()
+    ref = oracle.qng_step(p)
+    for key in ("g", "grad", "dtheta"):
+        assert rel(out[key].cpu(), ref[key]) <= TOL[W.C128], key
+    assert rel(out["energy"].cpu(), [ref["E"]]) <= TOL[W.C128]
+
+
 def test_config_rand12_c128_full(qng, oracle):
     """The 12-qubit, P = 192 workload, every entry against the oracle."""
     check_problem(qng, oracle, W.config_rand12(), W.C128)
@@ -248,5 +301,5 @@ def test_autotune_keeps_results(qng, oracle):
         assert rel(gs[b].cpu(), ref["g"]) <= TOL[W.C64]
         assert rel(dths[b].cpu(), ref["dtheta"]) <= TOL[W.C64]
     for n in {p.n for p in probs}:
-        cl, th = ctx.get_tuning(n)
-        assert 0 <= cl <= 3 and th in (64, 128, 256)
+        cl, th, fth = ctx.get_tuning(n)
+        assert 0 <= cl <= 3 and th in (64, 128, 256) and fth in (64, 128, 256, 512)

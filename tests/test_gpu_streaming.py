@@ -76,6 +76,11 @@ def test_streaming_layered_14(qng, oracle, precision):
     run_streaming(qng, oracle, p, precision)
 
 
+def test_streaming_long_circuit_renormalisation(qng, oracle):
+    """P = 600 with angles near pi/2: the register scales fall below 2^-200 and are renormalised."""
+    run_streaming(qng, oracle, W.z_run_problem(7, 600, 6, W.C128, near_half_pi=True), W.C128)
+
+
 def test_streaming_matches_onchip(qng):
     """The two paths agree on the 12-qubit, P = 192 workload."""
     p = W.config_rand12()

@@ -130,6 +130,15 @@ qng_status qng_set_stream(qng_ctx *ctx, void *stream);
  * Pauli expectation right after rotation k, so T_k = -(i/2) sigma_opt[k]. */
 qng_status qng_metric(qng_ctx *ctx, const double *theta, double *g, double *sigma_opt);
 
+/* The whole quantum geometric tensor G = g + i g_im of Eq. 4 (Sec. 1). The same recurrence takes the
+ * imaginary part of each inner product as well. T_i^* T_j is real (T_k = -(i/2) sigma_k), so
+ * g_im = Im L: antisymmetric, zero diagonal. The imaginary-time coefficient matrix Re<d_i psi|d_j psi>
+ * (G without its phase terms, Sec. 1) is g + sigma_i sigma_j / 4. g and g_im are device arrays in
+ * qng_metric's layout; sigma_opt is as there. Both paths: the streaming path runs a second metric
+ * schedule whose steps keep both parts. QNG_ERR_UNSUPPORTED when the on-chip column kernel's extra
+ * shared memory (P+1 float64 per warp) does not fit. */
+qng_status qng_metric_complex(qng_ctx *ctx, const double *theta, double *g, double *g_im, double *sigma_opt);
+
 /* Energy <E> (device, one float64 per instance) and gradient d<E>/d theta (device, sum P_b). */
 qng_status qng_gradient(qng_ctx *ctx, const double *theta, double *grad, double *energy);
 

@@ -140,6 +140,7 @@ struct qng_ctx {
         w.gradraw = reinterpret_cast<double *>(ws + o_grad);
         w.energy = reinterpret_cast<double *>(ws + o_energy);
         w.chol = reinterpret_cast<double *>(ws + o_chol);
+        w.Lim = w.chol;
         w.ckpt = ws + o_ckpt;
         w.eta = ws + o_eta;
         return w;
@@ -354,7 +355,8 @@ qng_status plan(qng_ctx *c) {
         const size_t state = Nl * ab * (g.cl ? 3 : 1);
         g.smem_fwd = state + 64 * sizeof(double);
         g.smem_col = state + (size_t)(g.max_P + 1) * nw * sizeof(double) + (size_t)(g.max_P + 1) * sizeof(double);
-        if (g.smem_col > 227 * 1024 || g.smem_fwd > 227 * 1024) return QNG_ERR_UNSUPPORTED;
+        g.smem_col_im = g.smem_col + (size_t)(g.max_P + 1) * nw * sizeof(double);
+        if (g.smem_col > kMaxSmem || g.smem_fwd > kMaxSmem) return QNG_ERR_UNSUPPORTED;
         c->groups.push_back(g);
     }
 
@@ -429,7 +431,8 @@ qng_status upload(qng_ctx *c) {
             const large::RedSpec &r = S.reds[k];
             size_t region = r.region == large::kRegionSigma ? c->o_sigma
                           : r.region == large::kRegionL ? c->o_L
-                          : r.region == large::kRegionGrad ? c->o_grad : c->o_energy;
+                          : r.region == large::kRegionGrad ? c->o_grad
+                          : r.region == large::kRegionLim ? c->o_chol : c->o_energy;
             items[k].slot = r.slot;
             items[k].pad = 0;
             items[k].mul = r.mul;
@@ -447,9 +450,13 @@ qng_status upload(qng_ctx *c) {
         c->prepared = true;
         return QNG_OK;
     }
-    size_t sf = 0, sc = 0;
-    for (const Group &g : c->groups) { sf = std::max(sf, g.smem_fwd); sc = std::max(sc, g.smem_col); }
-    if ((e = prepare_kernels(c->precision, sf, sc)) != cudaSuccess) return cuda_status(e);
+    size_t sf = 0, sc = 0, sci = 0;
+    for (const Group &g : c->groups) {
+        sf = std::max(sf, g.smem_fwd);
+        sc = std::max(sc, g.smem_col);
+        sci = std::max(sci, std::min(g.smem_col_im, kMaxSmem));
+    }
+    if ((e = prepare_kernels(c->precision, sf, sc, sci)) != cudaSuccess) return cuda_status(e);
     const int scl = solve_cluster_log2(c->max_P);
     if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
     // batched contexts: persistent column launches fed by a device work counter per group
@@ -497,16 +504,20 @@ qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
     const large::ReduceItem *items = reinterpret_cast<const large::ReduceItem *>(c->ws + c->o_red);
     const size_t ab = amp_bytes(c->precision);
     for (const large::Launch &L : S.launches) {
+        const bool metric_im = jobs & kJobMetricIm;
         const bool want = (L.segment == large::kSegForward || L.segment == large::kSegEnergy) ? energy
-                        : (L.segment == large::kSegAdjoint ? grad : metric);
+                        : L.segment == large::kSegAdjoint ? grad
+                        : L.segment == large::kSegMetric ? metric && !metric_im
+                                                         : metric && metric_im;
+        const int cls = (L.segment == large::kSegMetric || L.segment == large::kSegMetricIm) ? 2 : 1;
         if (!want) continue;
         cudaError_t e = cudaSuccess;
         if (L.kind == large::Launch::Pass) {
             const large::PassDesc &pd = S.passes[L.pass];
             pa.desc = descs + L.pass;
             const size_t smem = (size_t)__builtin_popcount(pd.regmask) * (ab << pd.t);
-            e = timed(c, L.segment == large::kSegMetric ? 2 : 1,
-                      [&] { return large::launch_pass(pa, c->precision, c->l_grid, 256, smem, c->stream); });
+            const int mim = L.segment == large::kSegMetricIm ? 1 : 0;
+            e = timed(c, cls, [&] { return large::launch_pass(pa, c->precision, c->l_grid, 256, smem, mim, c->stream); });
         } else if (L.kind == large::Launch::Hpsi) {
             e = timed(c, 1, [&] {
                 return large::launch_hpsi(c->ws + c->o_reg[large::kRegB], c->ws + c->o_reg[large::kRegA],
@@ -514,7 +525,7 @@ qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
                                           c->precision, pa.partial, c->l_grid, c->stream);
             });
         } else {
-            e = timed(c, L.segment == large::kSegMetric ? 2 : 1, [&] {
+            e = timed(c, cls, [&] {
                 return large::launch_reduce(pa.partial, pa.slotfac, c->l_grid, items + L.item_begin, L.nitems, L.use_fac,
                                             c->stream);
             });
@@ -554,7 +565,8 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
         const int wg = (jobs & (kJobGradient | kJobSolve)) ? 1 : 0;
         for (const Group &g : c->groups) {
             if ((wm && wg ? g.num_work : (wm ? g.num_met : g.num_grad)) == 0) continue;
-            e = timed(c, 2, [&] { return launch_columns(w, g, c->precision, wm, wg, c->stream); });
+            const int wim = (jobs & kJobMetricIm) ? 1 : 0;
+            e = timed(c, 2, [&] { return launch_columns(w, g, c->precision, wm, wg, wim, c->stream); });
             if (e != cudaSuccess) return cuda_status(e);
             launches += 1;
         }
@@ -675,6 +687,18 @@ qng_status qng_metric(qng_ctx *c, const double *theta, double *g, double *sigma_
     a.g_out = g;
     a.sigma_out = sigma_opt;
     return run(c, kJobMetric, a);
+}
+
+qng_status qng_metric_complex(qng_ctx *c, const double *theta, double *g, double *g_im, double *sigma_opt) {
+    if (!c || !g || !g_im) return QNG_ERR_ARG;
+    for (const Group &grp : c->groups)
+        if (grp.smem_col_im > kMaxSmem) return QNG_ERR_UNSUPPORTED;
+    LaunchArgs a = {};
+    a.theta = theta;
+    a.g_out = g;
+    a.gim_out = g_im;
+    a.sigma_out = sigma_opt;
+    return run(c, kJobMetric | kJobMetricIm, a);
 }
 
 qng_status qng_gradient(qng_ctx *c, const double *theta, double *grad, double *energy) {
@@ -932,7 +956,7 @@ qng_status qng_stream_traffic(const qng_ctx *c, int64_t *metric_bytes, int64_t *
             const large::PassDesc &pd = c->sched.passes[L.pass];
             const int64_t b = reg * (__builtin_popcount(pd.loadmask) + __builtin_popcount(pd.storemask));
             if (L.segment == large::kSegMetric) { mb += b; ++mp; }
-            else ob += b;
+            else if (L.segment != large::kSegMetricIm) ob += b;  // not part of a step
         }
     }
     if (metric_bytes) *metric_bytes = mb;

@@ -31,6 +31,7 @@ struct DevParam {
 };
 
 constexpr int kZRunMax = 16;
+constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (opt-in maximum)
 
 // Fill DevParam::zrun over the parameters [p, p + P) of one instance.
 inline void set_zruns(DevParam *p, int P) {
@@ -110,6 +111,7 @@ struct Work {
     double *gradraw;          // d<E>/d theta
     double *energy;           // <E>
     double *chol;             // P*P per instance
+    double *Lim;              // (1/4) Im L_ij, i < j (complex metric calls only; shares chol's region)
     void *ckpt;               // checkpoint amplitudes
     void *eta;                // adjoint seeds
 };
@@ -131,6 +133,7 @@ struct Group {
     int num_met = 0;
     size_t smem_fwd = 0;
     size_t smem_col = 0;
+    size_t smem_col_im = 0;  // column kernel with Im L partial sums (metric_im)
     int *queue = nullptr;        // device work counter of the persistent column launch (batched contexts)
     int resident_clusters = 0;   // clusters of the column kernel resident at once
 };
@@ -140,11 +143,13 @@ enum Job : int {
     kJobGradient = 2,
     kJobEnergy = 4,
     kJobSolve = 8,
+    kJobMetricIm = 16,  // with kJobMetric: Im G as well (no solve in the same call)
 };
 
 struct LaunchArgs {
     const double *theta;
     double *g_out;        // may be null
+    double *gim_out;      // Im G (kJobMetricIm), may be null
     double *sigma_out;    // may be null
     double *grad_out;     // may be null
     double *energy_out;   // may be null
@@ -158,12 +163,12 @@ struct LaunchArgs {
 cudaError_t launch_coef(const Work &w, const double *theta, int64_t total_params, cudaStream_t st);
 cudaError_t launch_forward(const Work &w, const Group &g, int precision, int want_eta, cudaStream_t st);
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
-                           cudaStream_t st);
+                           int metric_im, cudaStream_t st);
 cudaError_t launch_finish(const Work &w, int count, int max_P, const LaunchArgs &a, cudaStream_t st);
 cudaError_t launch_solve(const Work &w, int count, int max_P, int cl, const LaunchArgs &a, cudaStream_t st);
 size_t solve_smem_bytes(int P, int cl);
 cudaError_t prepare_solve(size_t smem);
 int resident_clusters(const Group &g, int precision);
-cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col);
+cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col, size_t smem_col_im);
 
 }  // namespace qng

@@ -317,26 +317,30 @@ template <int AX, int BETA, typename T2> __device__ __forceinline__ T2 sig(T2 xm
     else if constexpr (AX == kAxisY) return BETA ? T2{-xo.y, xo.x} : T2{xo.y, -xo.x};
     else return BETA ? T2{-xm.x, -xm.y} : xm;
 }
-// part += Re(conj(a) s) (IM = 0) or Im(conj(a) s) (IM = 1)
-template <int IM, typename RA, typename T2> __device__ __forceinline__ RA ipacc(RA part, T2 a, T2 s) {
-    if constexpr (IM) return fma(a.x, s.y, fma(-a.y, s.x, part));
-    else return fma(a.x, s.x, fma(a.y, s.y, part));
+// Partial inner products of one step: re = Re<a|s>, im = Im<a|s> (only the parts IM asks for).
+template <typename RA> struct RI {
+    RA re, im;
+};
+// IM = 0: Re(conj(a) s); IM = 1: Im(conj(a) s); IM = 2: both
+template <int IM, typename RA, typename T2> __device__ __forceinline__ void ipacc(RI<RA> &part, T2 a, T2 s) {
+    if constexpr (IM != 1) part.re = fma(a.x, s.x, fma(a.y, s.y, part.re));
+    if constexpr (IM != 0) part.im = fma(a.x, s.y, fma(-a.y, s.x, part.im));
 }
 
 // One fused step of a column on a local X/Y qubit: inner product with sigma on the pairs,
 // then the adjoint rotation R^dag on the same pairs, then the diagonal fixed block F^dag.
 template <typename R, int AX, int IM, int CB>
-__device__ __forceinline__ R col_pairs(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on, const RotC<R, CB> &rot,
-                                       bool post, const DevParam &pi, const DevDiag *dt) {
+__device__ __forceinline__ RI<R> col_pairs(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on,
+                                           const RotC<R, CB> &rot, bool post, const DevParam &pi, const DevDiag *dt) {
     using cx = typename CX<R>::T;
-    R part = 0;
+    RI<R> part = {0, 0};
     const uint32_t bit = 1u << q, half = e.Nl >> 1;
     for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
         const uint32_t l0 = ins0(p, q), l1 = l0 | bit;
         const cx x0 = e.buf[l0], x1 = e.buf[l1];
         const cx a0 = a[e.base | l0], a1 = a[e.base | l1];
-        part = ipacc<IM>(part, a0, sig<AX, 0>(x0, x1));
-        part = ipacc<IM>(part, a1, sig<AX, 1>(x1, x0));
+        ipacc<IM>(part, a0, sig<AX, 0>(x0, x1));
+        ipacc<IM>(part, a1, sig<AX, 1>(x1, x0));
         if (rot_on) {
             cx y0 = rot.apply(x0, isig<AX, 0>(x0, x1));
             cx y1 = rot.apply(x1, isig<AX, 1>(x1, x0));
@@ -353,14 +357,15 @@ __device__ __forceinline__ R col_pairs(Eng<R> &e, const typename CX<R>::T *a, in
 
 // The same step on a distributed X/Y qubit, this CTA holding the BETA half of every pair.
 template <typename R, int AX, int IM, int BETA, int CB>
-__device__ __forceinline__ R col_dist(Eng<R> &e, const typename CX<R>::T *rv, const typename CX<R>::T *a, bool rot_on,
-                                      const RotC<R, CB> &rot, bool post, const DevParam &pi, const DevDiag *dt) {
+__device__ __forceinline__ RI<R> col_dist(Eng<R> &e, const typename CX<R>::T *rv, const typename CX<R>::T *a,
+                                          bool rot_on, const RotC<R, CB> &rot, bool post, const DevParam &pi,
+                                          const DevDiag *dt) {
     using cx = typename CX<R>::T;
-    R part = 0;
+    RI<R> part = {0, 0};
     for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
         const uint64_t kk = e.base | l;
         const cx xm = e.buf[l], xo = rv[l];
-        part = ipacc<IM>(part, a[kk], sig<AX, BETA>(xm, xo));
+        ipacc<IM>(part, a[kk], sig<AX, BETA>(xm, xo));
         if (rot_on) {
             cx y = rot.apply(xm, isig<AX, BETA>(xm, xo));
             if (post) y = flip2(y, diag_parity(kk, pi, dt));
@@ -372,15 +377,15 @@ __device__ __forceinline__ R col_dist(Eng<R> &e, const typename CX<R>::T *rv, co
 
 // The same step for a Z rotation (diagonal: any qubit, no pairing).
 template <typename R, int IM, int CB>
-__device__ __forceinline__ R col_diag(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on, const RotC<R, CB> &rot,
-                                      bool post, const DevParam &pi, const DevDiag *dt) {
+__device__ __forceinline__ RI<R> col_diag(Eng<R> &e, const typename CX<R>::T *a, int q, bool rot_on,
+                                          const RotC<R, CB> &rot, bool post, const DevParam &pi, const DevDiag *dt) {
     using cx = typename CX<R>::T;
-    R part = 0;
+    RI<R> part = {0, 0};
     for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
         const uint64_t kk = e.base | l;
         const int beta = (int)((kk >> q) & 1);
         const cx x = e.buf[l];
-        part = ipacc<IM>(part, flip2(a[kk], beta), x);  // (Z x)_beta = (-1)^beta x
+        ipacc<IM>(part, flip2(a[kk], beta), x);  // (Z x)_beta = (-1)^beta x
         if (rot_on) {
             const cx v = {flip(x.y, beta ^ 1), flip(x.x, beta)};  // (i Z x)_beta
             cx y = rot.apply(x, v);
@@ -392,9 +397,9 @@ __device__ __forceinline__ R col_diag(Eng<R> &e, const typename CX<R>::T *a, int
 }
 
 template <typename R, int IM, int CB>
-__device__ __forceinline__ R col_step_cb(Eng<R> &e, const typename CX<R>::T *a, const DevParam &pi, bool rot_on,
-                                         const RotC<R, CB> &rot, bool post, const DevDiag *dt) {
-    R part;
+__device__ __forceinline__ RI<R> col_step_cb(Eng<R> &e, const typename CX<R>::T *a, const DevParam &pi, bool rot_on,
+                                             const RotC<R, CB> &rot, bool post, const DevDiag *dt) {
+    RI<R> part;
     if (pi.axis == kAxisZ) {
         part = col_diag<R, IM, CB>(e, a, pi.q, rot_on, rot, post, pi, dt);
     } else if (pi.q < e.nl) {
@@ -415,8 +420,8 @@ __device__ __forceinline__ R col_step_cb(Eng<R> &e, const typename CX<R>::T *a, 
 }
 
 template <typename R, int IM>
-__device__ __forceinline__ R col_step(Eng<R> &e, const typename CX<R>::T *a, const DevParam &pi, bool rot_on,
-                                      const Rot<R> &rot, bool post, const DevDiag *dt) {
+__device__ __forceinline__ RI<R> col_step(Eng<R> &e, const typename CX<R>::T *a, const DevParam &pi, bool rot_on,
+                                          const Rot<R> &rot, bool post, const DevDiag *dt) {
     if (std::is_same<R, double>::value && rot.caseB)
         return col_step_cb<R, IM, 1>(e, a, pi, rot_on, RotC<R, 1>{rot.c, rot.s, rot.t}, post, dt);
     return col_step_cb<R, IM, 0>(e, a, pi, rot_on, RotC<R, 0>{rot.c, rot.s, rot.t}, post, dt);
@@ -699,17 +704,18 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
 
 // ------------------------------------------------------------------------------------------
 // k_columns: one cluster per work item (instance, column).
-template <typename R>
+template <typename R, int MIM>
 __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int cl, int max_P, unsigned char *smem);
 
 // One cluster per work item, or (queue != nullptr) a persistent grid of clusters that take work
-// items, longest first, from a device counter until all num_work are done.
-template <typename R>
-__global__ void __launch_bounds__(256, 3) k_columns(Work w, int work_first, int cl, int max_P, int *queue, int num_work) {
+// items, longest first, from a device counter until all num_work are done. MIM = 1: metric
+// columns take Im L_ij as well (into w.Lim); their partial sums need Group::smem_col_im bytes.
+template <typename R, int MIM>
+__global__ void __launch_bounds__(256, MIM ? 2 : 3) k_columns(Work w, int work_first, int cl, int max_P, int *queue, int num_work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int item_sh;
     if (!queue) {
-        column_item<R>(w, w.work[work_first + (blockIdx.x >> cl)], cl, max_P, smem);
+        column_item<R, MIM>(w, w.work[work_first + (blockIdx.x >> cl)], cl, max_P, smem);
         return;
     }
     for (;;) {
@@ -719,18 +725,18 @@ __global__ void __launch_bounds__(256, 3) k_columns(Work w, int work_first, int 
             const int item = *cg::this_cluster().map_shared_rank(&item_sh, 0);
             cg::this_cluster().sync();  // rank 0 keeps item_sh until every CTA has read it
             if (item >= num_work) return;
-            column_item<R>(w, w.work[work_first + item], cl, max_P, smem);
+            column_item<R, MIM>(w, w.work[work_first + item], cl, max_P, smem);
         } else {
             __syncthreads();
             const int item = item_sh;
             __syncthreads();
             if (item >= num_work) return;
-            column_item<R>(w, w.work[work_first + item], cl, max_P, smem);
+            column_item<R, MIM>(w, w.work[work_first + item], cl, max_P, smem);
         }
     }
 }
 
-template <typename R>
+template <typename R, int MIM>
 __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int cl, int max_P, unsigned char *smem) {
     using cx = typename CX<R>::T;
     using RA = R;  // per-thread partial sums; float64 from the warp level on
@@ -739,6 +745,7 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
     const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double *red = reinterpret_cast<double *>(e.buf + (cl ? 3 : 1) * e.Nl);  // [(max_P + 1) * nw]
     double *fac = red + (size_t)(max_P + 1) * nw;                              // [max_P + 1]
+    double *red_im = fac + (max_P + 1);  // [(max_P + 1) * nw], metric_im only
     const uint64_t N = 1ull << in.n;
     const cx *ckpt = reinterpret_cast<const cx *>(w.ckpt) + in.ckpt_off;
     const double *scales = w.scale + in.scale_off;
@@ -824,8 +831,9 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
         __syncthreads();
     }
 
-    const bool want_im = grad_col;
-    RA acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // acc[k]: this thread's partial sum of step s - k
+    // 0: Re <a|sigma b> (metric), 1: Im (gradient column), 2: both (metric with Im L)
+    const int mode = grad_col ? 1 : (MIM ? 2 : 0);
+    RA acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // acc[k]: partial sum of step s - k (mode 2: re/im of step s - k/2)
     int cnt = 0;
     constexpr bool kScaled = std::is_same<R, double>::value;
     __shared__ int rn_flag[2];  // renormalise b after step s (written by thread 0, parity of s)
@@ -846,8 +854,9 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
             }
         }
         const bool post = rot_on && (pi.diag_count > 0 || pi.zmask != 0);
-        const RA part = want_im ? col_step<R, 1>(e, a, pi, rot_on, rot, post, w.diag)
-                                : col_step<R, 0>(e, a, pi, rot_on, rot, post, w.diag);
+        RI<RA> part;
+        if (mode == 1) part = col_step<R, 1>(e, a, pi, rot_on, rot, post, w.diag);
+        else part = col_step<R, MIM ? 2 : 0>(e, a, pi, rot_on, rot, post, w.diag);
         if (rot_on) {
             if (pi.diag_count < 0) {
                 for (int f = pi.fix_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[pi.fix_begin + f], scale_b);
@@ -867,16 +876,31 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
                 }
             }
         }
+        if (!MIM || mode != 2) {
 #pragma unroll
-        for (int k = 7; k > 0; --k) acc[k] = acc[k - 1];
-        acc[0] = part;
-        if (++cnt == 8 || s == nsteps - 1) {
-            const int idx = (lane >> 2) & 7;
-            const double pw = (double)warp_sum8(acc, lane);
-            if ((lane & 3) == 0 && idx < cnt) red[(size_t)(s - idx) * nw + wid] = pw;
+            for (int k = 7; k > 0; --k) acc[k] = acc[k - 1];
+            acc[0] = mode ? part.im : part.re;
+            if (++cnt == 8 || s == nsteps - 1) {
+                const int idx = (lane >> 2) & 7;
+                const double pw = (double)warp_sum8(acc, lane);
+                if ((lane & 3) == 0 && idx < cnt) red[(size_t)(s - idx) * nw + wid] = pw;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = 0;
-            cnt = 0;
+                for (int k = 0; k < 8; ++k) acc[k] = 0;
+                cnt = 0;
+            }
+        } else {
+#pragma unroll
+            for (int k = 7; k > 1; --k) acc[k] = acc[k - 2];
+            acc[0] = part.re;
+            acc[1] = part.im;
+            if (++cnt == 4 || s == nsteps - 1) {
+                const int idx = (lane >> 2) & 7, off = idx >> 1;
+                const double pw = (double)warp_sum8(acc, lane);
+                if ((lane & 3) == 0 && off < cnt) ((idx & 1) ? red_im : red)[(size_t)(s - off) * nw + wid] = pw;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] = 0;
+                cnt = 0;
+            }
         }
     }
 
@@ -898,6 +922,14 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
                 w.gradraw[in.param_off + (i0 - s)] = -tot;
             } else if (s < nsteps) {
                 w.L[in.metric_off + (int64_t)(i0 - s) * P + wk.col] = 0.25 * tot;
+                if (MIM) {
+                    double ti = 0.0;
+                    for (int r = 0; r < C; ++r) {
+                        const double *rr = cl ? cg::this_cluster().map_shared_rank(red_im, r) : red_im;
+                        for (int ww = 0; ww < nw; ++ww) ti += rr[(size_t)row * nw + ww];
+                    }
+                    w.Lim[in.metric_off + (int64_t)(i0 - s) * P + wk.col] = 0.25 * ti * fac[row];
+                }
             } else {
                 w.sigma[in.param_off + wk.col] = tot;
             }
@@ -928,6 +960,13 @@ __global__ void __launch_bounds__(512) k_finish(Work w, LaunchArgs a) {
             else v = L[(int64_t)j * P + i] - 0.25 * sg[i] * sg[j];
             if (a.g_out) a.g_out[in.metric_off + idx] = v;
             if (a.jobs & kJobSolve) A[idx] = v + (i == j ? a.lambda : 0.0);
+        }
+        if ((a.jobs & kJobMetricIm) && a.gim_out) {  // Im G = Im L: T_i^* T_j is real; Hermitian
+            const double *Li = w.Lim + in.metric_off;
+            for (int64_t idx = threadIdx.x; idx < (int64_t)P * P; idx += blockDim.x) {
+                const int i = (int)(idx / P), j = (int)(idx % P);
+                a.gim_out[in.metric_off + idx] = i < j ? Li[(int64_t)i * P + j] : (i > j ? -Li[(int64_t)j * P + i] : 0.0);
+            }
         }
         if (a.sigma_out)
             for (int k = threadIdx.x; k < P; k += blockDim.x) a.sigma_out[in.param_off + k] = sg[k];
@@ -1246,14 +1285,16 @@ template <typename K> static cudaError_t set_attrs(K kern, size_t smem) {
 }
 
 // smem_fwd / smem_col: the largest dynamic shared memory any group launches the kernels with
-cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col) {
+cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col, size_t smem_col_im) {
     cudaError_t e;
     if (precision == QNG_C128) {
         if ((e = set_attrs(k_forward<double>, smem_fwd)) != cudaSuccess) return e;
-        return set_attrs(k_columns<double>, smem_col);
+        if ((e = set_attrs(k_columns<double, 0>, smem_col)) != cudaSuccess) return e;
+        return set_attrs(k_columns<double, 1>, smem_col_im);
     }
     if ((e = set_attrs(k_forward<float>, smem_fwd)) != cudaSuccess) return e;
-    return set_attrs(k_columns<float>, smem_col);
+    if ((e = set_attrs(k_columns<float, 0>, smem_col)) != cudaSuccess) return e;
+    return set_attrs(k_columns<float, 1>, smem_col_im);
 }
 
 cudaError_t launch_coef(const Work &w, const double *theta, int64_t total, cudaStream_t st) {
@@ -1272,7 +1313,7 @@ cudaError_t launch_forward(const Work &w, const Group &g, int precision, int wan
 }
 
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
-                           cudaStream_t st) {
+                           int metric_im, cudaStream_t st) {
     int first, num;
     if (with_metric && with_grad) { first = g.first_work; num = g.num_work; }
     else if (with_metric)         { first = g.first_met; num = g.num_met; }
@@ -1287,9 +1328,16 @@ cudaError_t launch_columns(const Work &w, const Group &g, int precision, int wit
         if (e != cudaSuccess) return e;
     }
     const int grid = clusters << g.cl;
+    if (metric_im) {
+        if (precision == QNG_C128)
+            return launch_cluster(k_columns<double, 1>, grid, g.threads, g.smem_col_im, g.cl, st, w, first, g.cl, g.max_P,
+                                  queue, num);
+        return launch_cluster(k_columns<float, 1>, grid, g.threads, g.smem_col_im, g.cl, st, w, first, g.cl, g.max_P,
+                              queue, num);
+    }
     if (precision == QNG_C128)
-        return launch_cluster(k_columns<double>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P, queue, num);
-    return launch_cluster(k_columns<float>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P, queue, num);
+        return launch_cluster(k_columns<double, 0>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P, queue, num);
+    return launch_cluster(k_columns<float, 0>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P, queue, num);
 }
 
 // Clusters of this group's column kernel that fit on the GPU at once (0 if unknown).
@@ -1306,8 +1354,8 @@ int resident_clusters(const Group &g, int precision) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    cudaError_t e = (precision == QNG_C128) ? cudaOccupancyMaxActiveClusters(&n, k_columns<double>, &cfg)
-                                            : cudaOccupancyMaxActiveClusters(&n, k_columns<float>, &cfg);
+    cudaError_t e = (precision == QNG_C128) ? cudaOccupancyMaxActiveClusters(&n, k_columns<double, 0>, &cfg)
+                                            : cudaOccupancyMaxActiveClusters(&n, k_columns<float, 0>, &cfg);
     if (e != cudaSuccess) { cudaGetLastError(); return 0; }
     return n;
 }

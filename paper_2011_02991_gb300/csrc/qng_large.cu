@@ -66,14 +66,20 @@ __device__ __forceinline__ int gbit(const TileCtx &tc, uint32_t l, int q) {
 }
 
 
+// Partial inner product of one step: re and/or im as IM asks (0: Re, 1: Im, 2: both).
+template <typename R> struct Acc2 {
+    R re, im;
+};
+
 // One recurrence step on the registers A (left) and B (right) in one sweep of the tile: the inner
 // product with sigma on the pairs of qubit lb (compile-time axis AX and part IM), then, when ROT,
 // the adjoint rotation of the same axis on both registers. Every sign folds into an FMA operand.
 template <typename R, int AX, int IM, bool ROT, int CB>
-__device__ __forceinline__ R step_pairs(typename CX2<R>::T *A, typename CX2<R>::T *B, uint32_t T, int lb, R c, R s, R t) {
+__device__ __forceinline__ Acc2<R> step_pairs(typename CX2<R>::T *A, typename CX2<R>::T *B, uint32_t T, int lb, R c,
+                                              R s, R t) {
     using cx = typename CX2<R>::T;
     constexpr bool kScaled = std::is_same<R, double>::value;
-    R acc = 0;
+    Acc2<R> acc = {0, 0};
     const uint32_t bit = 1u << lb;
     auto rot = [&](cx x, cx v) -> cx {
         cx y;
@@ -91,8 +97,8 @@ __device__ __forceinline__ R step_pairs(typename CX2<R>::T *A, typename CX2<R>::
         cx s0, s1;  // (sigma b)_0, (sigma b)_1
         if constexpr (AX == kAxisX) { s0 = b1; s1 = b0; }
         else { s0 = cx{b1.y, -b1.x}; s1 = cx{-b0.y, b0.x}; }
-        if constexpr (IM) acc = fma(a0.x, s0.y, fma(-a0.y, s0.x, fma(a1.x, s1.y, fma(-a1.y, s1.x, acc))));
-        else acc = fma(a0.x, s0.x, fma(a0.y, s0.y, fma(a1.x, s1.x, fma(a1.y, s1.y, acc))));
+        if constexpr (IM != 0) acc.im = fma(a0.x, s0.y, fma(-a0.y, s0.x, fma(a1.x, s1.y, fma(-a1.y, s1.x, acc.im))));
+        if constexpr (IM != 1) acc.re = fma(a0.x, s0.x, fma(a0.y, s0.y, fma(a1.x, s1.x, fma(a1.y, s1.y, acc.re))));
         if constexpr (ROT) {
             // (i sigma x)_0, (i sigma x)_1
             if constexpr (AX == kAxisX) {
@@ -108,17 +114,17 @@ __device__ __forceinline__ R step_pairs(typename CX2<R>::T *A, typename CX2<R>::
 }
 
 template <typename R, int IM, bool ROT, int CB>
-__device__ __forceinline__ R step_diag(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int q, R c, R s,
-                                       R t) {
+__device__ __forceinline__ Acc2<R> step_diag(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int q, R c,
+                                             R s, R t) {
     using cx = typename CX2<R>::T;
     constexpr bool kScaled = std::is_same<R, double>::value;
-    R acc = 0;
+    Acc2<R> acc = {0, 0};
     for (uint32_t l = threadIdx.x; l < tc.T; l += blockDim.x) {
         const int beta = gbit(tc, l, q);
         const cx a = A[l], b = B[l];
         const cx af = lflip2(a, beta);  // (Z b)_beta = (-1)^beta b, folded into a
-        if constexpr (IM) acc = fma(af.x, b.y, fma(-af.y, b.x, acc));
-        else acc = fma(af.x, b.x, fma(af.y, b.y, acc));
+        if constexpr (IM != 0) acc.im = fma(af.x, b.y, fma(-af.y, b.x, acc.im));
+        if constexpr (IM != 1) acc.re = fma(af.x, b.x, fma(af.y, b.y, acc.re));
         if constexpr (ROT) {
             const cx va = {lflip(a.y, beta ^ 1), lflip(a.x, beta)}, vb = {lflip(b.y, beta ^ 1), lflip(b.x, beta)};
             cx ya, yb;
@@ -142,8 +148,8 @@ __device__ __forceinline__ R step_diag(const TileCtx &tc, typename CX2<R>::T *A,
 }
 
 template <typename R, int IM, int CB>
-__device__ __forceinline__ R step_dispatch_cb(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int ax, int q,
-                                              bool rot, R c, R s, R t) {
+__device__ __forceinline__ Acc2<R> step_dispatch_cb(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B,
+                                                    int ax, int q, bool rot, R c, R s, R t) {
     if (ax == kAxisZ)
         return rot ? step_diag<R, IM, true, CB>(tc, A, B, q, c, s, t) : step_diag<R, IM, false, CB>(tc, A, B, q, c, s, t);
     const int lb = tc.lbit[q];
@@ -155,13 +161,15 @@ __device__ __forceinline__ R step_dispatch_cb(const TileCtx &tc, typename CX2<R>
 }
 
 template <typename R, int IM>
-__device__ __forceinline__ R step_dispatch(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int ax, int q,
-                                           bool rot, R c, R s, R t, int caseB) {
+__device__ __forceinline__ Acc2<R> step_dispatch(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B, int ax,
+                                                 int q, bool rot, R c, R s, R t, int caseB) {
     if (std::is_same<R, double>::value && caseB) return step_dispatch_cb<R, IM, 1>(tc, A, B, ax, q, rot, c, s, t);
     return step_dispatch_cb<R, IM, 0>(tc, A, B, ax, q, rot, c, s, t);
 }
 
-template <typename R>
+// MIM = 1: the pass may hold steps that take both parts of the inner product (adjoint = 2, slots
+// slot and slot + 1); a separate instantiation keeps the registers of the other passes unchanged.
+template <typename R, int MIM>
 __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
     using cx = typename CX2<R>::T;
     constexpr bool kScaled = std::is_same<R, double>::value;
@@ -383,11 +391,20 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
                     const DevCoef co = pa.coef[op.param];  // adjoint rotation: s' = +s
                     c = (R)co.c; sv = (R)co.s; tv = (R)co.t; caseB = co.caseB; f = co.f;
                 }
-                const R acc = op.adjoint
-                    ? step_dispatch<R, 1>(tc, tile[op.r0], tile[op.r1], op.axis, op.q0, rot, c, sv, tv, caseB)
-                    : step_dispatch<R, 0>(tc, tile[op.r0], tile[op.r1], op.axis, op.q0, rot, c, sv, tv, caseB);
-                part[op.slot] += (double)acc;
-                if (blockIdx.x == 0 && threadIdx.x == 0 && tile_id == 0) pa.slotfac[pd.slot_base + op.slot] = sc[op.r0] * sc[op.r1];
+                if (MIM && op.adjoint == 2) {
+                    const Acc2<R> acc = step_dispatch<R, 2>(tc, tile[op.r0], tile[op.r1], op.axis, op.q0, rot, c, sv, tv, caseB);
+                    part[op.slot] += (double)acc.re;
+                    part[op.slot + 1] += (double)acc.im;
+                    if (blockIdx.x == 0 && threadIdx.x == 0 && tile_id == 0)
+                        pa.slotfac[pd.slot_base + op.slot] = pa.slotfac[pd.slot_base + op.slot + 1] = sc[op.r0] * sc[op.r1];
+                } else {
+                    const Acc2<R> acc = op.adjoint
+                        ? step_dispatch<R, 1>(tc, tile[op.r0], tile[op.r1], op.axis, op.q0, rot, c, sv, tv, caseB)
+                        : step_dispatch<R, 0>(tc, tile[op.r0], tile[op.r1], op.axis, op.q0, rot, c, sv, tv, caseB);
+                    part[op.slot] += (double)(op.adjoint ? acc.im : acc.re);
+                    if (blockIdx.x == 0 && threadIdx.x == 0 && tile_id == 0)
+                        pa.slotfac[pd.slot_base + op.slot] = sc[op.r0] * sc[op.r1];
+                }
                 if (kScaled && rot) { sc[op.r0] *= f; sc[op.r1] *= f; }
                 break;
             }
@@ -496,13 +513,25 @@ __global__ void k_reduce(const double *partial, const double *slotfac, int nctas
 
 // ------------------------------------------------------------------------------------------
 cudaError_t prepare_pass(int precision, size_t smem) {
-    return precision == QNG_C128 ? cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                                 : cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if (precision == QNG_C128) {
+        if ((e = cudaFuncSetAttribute(k_pass<double, 0>, attr, (int)smem)) != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_pass<double, 1>, attr, (int)smem);
+    }
+    if ((e = cudaFuncSetAttribute(k_pass<float, 0>, attr, (int)smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_pass<float, 1>, attr, (int)smem);
 }
 
-cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, cudaStream_t st) {
-    if (precision == QNG_C128) k_pass<double><<<grid, threads, smem, st>>>(pa);
-    else k_pass<float><<<grid, threads, smem, st>>>(pa);
+cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, int metric_im,
+                        cudaStream_t st) {
+    if (precision == QNG_C128) {
+        if (metric_im) k_pass<double, 1><<<grid, threads, smem, st>>>(pa);
+        else k_pass<double, 0><<<grid, threads, smem, st>>>(pa);
+    } else {
+        if (metric_im) k_pass<float, 1><<<grid, threads, smem, st>>>(pa);
+        else k_pass<float, 0><<<grid, threads, smem, st>>>(pa);
+    }
     return cudaGetLastError();
 }
 

@@ -23,8 +23,9 @@ enum OpKind : int32_t {
     kOpIp = 5,         // slot += Re (adjoint = 0) or Im (adjoint = 1) of <r0| sigma_{axis}(q0) |r1>; axis -1: no sigma
     kOpRecordFac = 6,  // slotfac[slot] <- scale(r0) * scale(r1)
     kOpSetScale = 7,   // scale(r1) <- scale(r0) (no data)
-    kOpStep = 8,       // one recurrence step in one sweep: slot += Re/Im <r0|sigma_{axis}(q0)|r1>, then, if
-                       // param >= 0, the adjoint rotation of param (same axis and qubit) on r0 and r1
+    kOpStep = 8,       // one recurrence step in one sweep: slot += Re/Im <r0|sigma_{axis}(q0)|r1> (adjoint
+                       // 0/1; 2: Re into slot and Im into slot + 1), then, if param >= 0, the adjoint
+                       // rotation of param (same axis and qubit) on r0 and r1
 };
 
 struct PassOp {
@@ -68,7 +69,8 @@ struct PassArgs {
 };
 
 cudaError_t prepare_pass(int precision, size_t smem);
-cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, int metric_im,
+                        cudaStream_t st);
 cudaError_t launch_hpsi(const void *in, void *out, const DevTerm *terms, int nterms, int n, int precision,
                         double *partial, int grid, cudaStream_t st);
 cudaError_t launch_reduce(const double *partial, const double *slotfac, int nctas, const ReduceItem *items, int nitems,
@@ -80,10 +82,11 @@ struct Launch {
     int pass = -1;             // index into the pass table
     int item_begin = 0, nitems = 0;
     int use_fac = 1;
-    int segment = 0;           // kSegForward, kSegEnergy, kSegAdjoint, kSegMetric
+    int segment = 0;           // kSegForward, kSegEnergy, kSegAdjoint, kSegMetric, kSegMetricIm
 };
-enum Segment { kSegForward = 0, kSegEnergy = 1, kSegAdjoint = 2, kSegMetric = 3 };
-enum Region { kRegionSigma = 0, kRegionL = 1, kRegionGrad = 2, kRegionEnergy = 3 };
+// kSegMetricIm repeats kSegMetric with both parts of every inner product; a call runs one of the two.
+enum Segment { kSegForward = 0, kSegEnergy = 1, kSegAdjoint = 2, kSegMetric = 3, kSegMetricIm = 4 };
+enum Region { kRegionSigma = 0, kRegionL = 1, kRegionGrad = 2, kRegionEnergy = 3, kRegionLim = 4 };
 
 // A reduce destination before the workspace address is known.
 struct RedSpec {

@@ -9,6 +9,7 @@
 //   metric   for every column j: a <- psi, b <- F_j^dag sigma_j F_j psi, <sigma_j> = <F psi|sigma|F psi>,
 //            psi <- U_j psi; then for i = j-1..0: L_ij = (1/4) Re <a|sigma_i|b>, a, b <- U_i^dag
 //            (Algorithm 1's inner loop with phi = b and lambda = a, each step one adjoint gate on both)
+//   metric (complex)  the same with Im <a|sigma_i|b> as well (the complex-metric call's segment)
 // Consecutive steps of a segment share a pass while the qubits their non-diagonal operations act on
 // fit in the tile window and their inner products fit in the slot budget.
 #include <algorithm>
@@ -98,7 +99,8 @@ struct Builder {
         o.q0 = g.q0;
         gr.ops.push_back(o);
     }
-    // one recurrence step: inner product of (r0, r1) with sigma_k, then R_k^dag on both when rot
+    // one recurrence step: inner product of (r0, r1) with sigma_k, then R_k^dag on both when rot;
+    // im = 2 takes both parts, the imaginary one into kRegionLim at the same index
     void add_step(Group &gr, int k, int r0, int r1, int im, bool rot, double mul, int region, int64_t index) {
         const qng_gate &g = gates[rot_at[k]];
         PassOp o = mk(kOpStep);
@@ -112,6 +114,7 @@ struct Builder {
         o.slot = (int)gr.reds.size();
         gr.ops.push_back(o);
         gr.reds.push_back(RedSpec{o.slot, mul, region, index});
+        if (im == 2) gr.reds.push_back(RedSpec{o.slot + 1, mul, kRegionLim, index});
     }
     void add_ip(Group &gr, int k_axis_param, int r0, int r1, int im, double mul, int region, int64_t index, bool sigma = true) {
         PassOp o = mk(kOpIp);
@@ -132,7 +135,7 @@ struct Builder {
     // qubits their non-diagonal parts act on fit in the tile window and its inner products fit in
     // the slot budget (a step may span several passes). Then launch the segment's reduction.
     void emit(std::vector<Group> &groups, int segment, int dead_at_end) {
-        struct Item { PassOp op; int need; bool has_red; RedSpec red; };
+        struct Item { PassOp op; int need; int nred; RedSpec red[2]; };
         std::vector<Item> items;
         for (Group &g : groups) {
             for (const PassOp &o : g.ops) {
@@ -146,8 +149,8 @@ struct Builder {
                     else if (o.fixed_kind != QNG_GATE_CZ && o.fixed_kind != QNG_GATE_Z) it.need = o.q0;
                 }
                 if (it.need >= 0 && it.need < low) it.need = -1;
-                it.has_red = (o.kind == kOpIp || o.kind == kOpStep);
-                if (it.has_red) it.red = g.reds[o.slot];
+                it.nred = (o.kind == kOpIp || o.kind == kOpStep) ? (o.kind == kOpStep && o.adjoint == 2 ? 2 : 1) : 0;
+                for (int r = 0; r < it.nred; ++r) it.red[r] = g.reds[o.slot + r];
                 items.push_back(it);
             }
         }
@@ -162,14 +165,14 @@ struct Builder {
             while (i1 < items.size()) {
                 const Item &it = items[i1];
                 const bool new_q = it.need >= 0 && !win_set.count(it.need);
-                if (i1 > i0 && ((new_q && (int)win_set.size() >= win) || (it.has_red && (int)reds.size() >= kMaxSlots))) break;
+                if (i1 > i0 && ((new_q && (int)win_set.size() >= win) || ((int)reds.size() + it.nred > kMaxSlots))) break;
                 if (new_q) win_set.insert(it.need);
                 PassOp o = it.op;
-                if (it.has_red) {
-                    o.slot = (int)reds.size();
-                    RedSpec r = it.red;
-                    r.slot = o.slot;
-                    reds.push_back(r);
+                if (it.nred) o.slot = (int)reds.size();
+                for (int r = 0; r < it.nred; ++r) {
+                    RedSpec rs = it.red[r];
+                    rs.slot = o.slot + r;
+                    reds.push_back(rs);
                 }
                 ops.push_back(o);
                 ++i1;
@@ -298,7 +301,8 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
         }
         B.emit(gs, kSegAdjoint, PSI | A);
     }
-    // metric columns
+    // metric columns (segment kSegMetric, Re L), then the same with Im L (kSegMetricIm)
+    for (const int im : {0, 2}) {
     B.parity = 0;
     for (int j = 0; j < P; ++j) {
         std::vector<Group> gs(j + 1);
@@ -331,11 +335,12 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
         for (int s = 1; s <= j; ++s) {
             const int i = j - s;
             Group &g = gs[s];
-            B.add_step(g, i, kRegA, kRegB, 0, i > 0, 0.25, kRegionL, (int64_t)i * P + j);
+            B.add_step(g, i, kRegA, kRegB, im, i > 0, 0.25, kRegionL, (int64_t)i * P + j);
             if (i > 0)
                 for (int f = (int)B.fixed_of[i].size() - 1; f >= 0; --f) B.add_fixed(g, B.fixed_of[i][f], A | Bm);
         }
-        B.emit(gs, kSegMetric, A | Bm);
+        B.emit(gs, im ? kSegMetricIm : kSegMetric, A | Bm);
+    }
     }
 }
 

@@ -143,7 +143,8 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     const int nw = grp.threads / 32;
     grp.smem_fwd = state + 64 * sizeof(double);
     grp.smem_col = state + (size_t)(P + 1) * nw * sizeof(double) + (size_t)(P + 1) * sizeof(double);
-    if (grp.smem_col > 227 * 1024) return QNG_ERR_UNSUPPORTED;
+    grp.smem_col_im = grp.smem_col;  // this entry point takes Re G only
+    if (grp.smem_col > kMaxSmem) return QNG_ERR_UNSUPPORTED;
 
     DevInst in = {};
     in.n = n;
@@ -187,7 +188,7 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     put(o_work, work, sizeof(DevWork) * P);
     put(o_ginst, &ginst, sizeof(ginst));
     if (e != cudaSuccess) return QNG_ERR_CUDA;
-    if (prepare_kernels(precision, grp.smem_fwd, grp.smem_col) != cudaSuccess) return QNG_ERR_CUDA;
+    if (prepare_kernels(precision, grp.smem_fwd, grp.smem_col, grp.smem_col) != cudaSuccess) return QNG_ERR_CUDA;
 
     Work w;
     w.status = reinterpret_cast<int32_t *>(base + o_status);
@@ -214,7 +215,7 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     a.jobs = kJobMetric;
     if (launch_coef(w, theta, P, st) != cudaSuccess) return QNG_ERR_CUDA;
     if (launch_forward(w, grp, precision, 0, st) != cudaSuccess) return QNG_ERR_CUDA;
-    if (launch_columns(w, grp, precision, 1, 0, st) != cudaSuccess) return QNG_ERR_CUDA;
+    if (launch_columns(w, grp, precision, 1, 0, 0, st) != cudaSuccess) return QNG_ERR_CUDA;
     if (launch_finish(w, 1, P, a, st) != cudaSuccess) return QNG_ERR_CUDA;
     return QNG_OK;
 }

@@ -54,6 +54,7 @@ SYMBOLS = {
     "qng_set_workspace": [_vp, _vp, ctypes.c_size_t, _vp],
     "qng_set_stream": [_vp, _vp],
     "qng_metric": [_vp, _vp, _vp, _vp],
+    "qng_metric_complex": [_vp, _vp, _vp, _vp, _vp],
     "qng_gradient": [_vp, _vp, _vp, _vp],
     "qng_energy": [_vp, _vp, _vp],
     "qng_energy_backward": [_vp, _vp, _vp, _vp],
@@ -208,6 +209,15 @@ class Context:
         sg = self._f64(self.total_params) if want_sigma else None
         _chk(load().qng_metric(self._h, _ptr(theta), _ptr(g), _ptr(sg)), "qng_metric")
         return (g, sg) if want_sigma else g
+
+    def metric_complex(self, theta, want_sigma: bool = False):
+        """The quantum geometric tensor G = g + i Im G as a complex128 tensor (flat, like metric)."""
+        theta = self._theta(theta)
+        g, gi = self._f64(self.total_metric), self._f64(self.total_metric)
+        sg = self._f64(self.total_params) if want_sigma else None
+        _chk(load().qng_metric_complex(self._h, _ptr(theta), _ptr(g), _ptr(gi), _ptr(sg)), "qng_metric_complex")
+        G = torch.complex(g, gi)
+        return (G, sg) if want_sigma else G
 
     def gradient(self, theta):
         theta = self._theta(theta)

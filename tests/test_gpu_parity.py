@@ -303,3 +303,78 @@ def test_autotune_keeps_results(qng, oracle):
     for n in {p.n for p in probs}:
         cl, th, fth = ctx.get_tuning(n)
         assert 0 <= cl <= 3 and th in (64, 128, 256) and fth in (64, 128, 256, 512)
+
+
+def check_complex(qng, oracle, probs, precision, shape=None):
+    """qng_metric_complex against the oracle's G (Eq. 4), Re and Im, every instance."""
+    probs = probs if isinstance(probs, list) else [probs]
+    ctx = qng.Context(probs if len(probs) > 1 else probs[0], precision=precision)
+    if shape is not None:
+        ctx.set_shape(*shape)
+    G, sg = ctx.metric_complex(ctx.theta0(), want_sigma=True)
+    ctx.sync()
+    Gs = ctx.split_metric(G) if len(probs) > 1 else [G.reshape(probs[0].P, probs[0].P)]
+    for b, p in enumerate(probs):
+        ref = oracle.qng_step(p)["G"]
+        Gb = Gs[b].cpu().numpy().reshape(p.P, p.P)
+        err = float(np.abs(Gb - ref).max() / np.abs(ref).max())
+        assert err <= TOL[precision], f"{p.name}: {err}"
+        assert np.all(Gb.imag == -Gb.imag.T) and np.all(np.diag(Gb.imag) == 0.0)
+    return ctx
+
+
+def test_metric_complex_closed_form(qng):
+    """RY(a) RZ(b) on one qubit: G_01 = i sin(a)/4."""
+    bld = W._CircuitBuilder(1)
+    bld.rot(W.RY, 0)
+    bld.rot(W.RZ, 0)
+    p = W.Problem("ryrz", bld.build(), W.hamiltonian_from_terms([(1.0, {0: "Z"})]), np.array([0.7, -1.3]))
+    ctx = qng.Context(p, precision=W.C128)
+    G = ctx.metric_complex(ctx.theta0()).reshape(2, 2).cpu().numpy()
+    ctx.sync()
+    assert abs(G[0, 1] - 0.25j * np.sin(0.7)) < 1e-15
+
+
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+def test_metric_complex_configs(qng, oracle, precision):
+    check_complex(qng, oracle, W.config_tfim4(), precision)
+    check_complex(qng, oracle, W.config_rand12(precision=precision), precision)
+
+
+@pytest.mark.parametrize("cl", [0, 1, 2, 3])
+def test_metric_complex_every_gate_kind_distributed(qng, oracle, cl):
+    """Every gate kind, with 0..3 of the qubits distributed over the cluster."""
+    p = W.random_problem(7, 90, 10, 910 + cl, W.C128)
+    check_complex(qng, oracle, p, W.C128, shape=(7, cl, 64, 64))
+
+
+def test_metric_complex_renormalisation(qng, oracle):
+    check_complex(qng, oracle, W.z_run_problem(7, 600, 6, W.C128, near_half_pi=True), W.C128, shape=(7, 0, 64, 64))
+
+
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+def test_metric_complex_batch(qng, oracle, precision):
+    """A batch with several launch shapes, through the persistent column launch."""
+    probs = [p for p in W.config_batch(count=12, precision=precision)]
+    ctx = check_complex(qng, oracle, probs, precision)
+    # the real part is qng_metric's metric up to the grouping of the warp sums (4 steps per
+    # reduction instead of 8), i.e. float32 rounding for complex64
+    g = ctx.metric(ctx.theta0())
+    G = ctx.metric_complex(ctx.theta0())
+    ctx.sync()
+    assert rel(G.real.cpu(), g.cpu()) <= (1e-13 if precision == W.C128 else 1e-5)
+
+
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+@pytest.mark.parametrize("n,seed", [(6, 1), (13, 3)])
+def test_metric_complex_streaming(qng, oracle, precision, n, seed):
+    """The streaming path's complex schedule: every gate kind, 1 and 4 tiles (two slots per step)."""
+    p = W.random_problem(n, 50 + 4 * n, 10, 3000 + seed, precision)
+    ctx = qng.Context(p, precision=precision, path=2)
+    G = ctx.metric_complex(ctx.theta0()).reshape(p.P, p.P).cpu().numpy()
+    g = ctx.metric(ctx.theta0()).reshape(p.P, p.P).cpu().numpy()  # the real-only schedule after it
+    ctx.sync()
+    ref = oracle.qng_step(p)["G"]
+    assert float(np.abs(G - ref).max() / np.abs(ref).max()) <= TOL[precision]
+    assert np.all(G.imag == -G.imag.T)
+    assert rel(g, ref.real) <= TOL[precision]

@@ -256,6 +256,27 @@ def test_hermitian_psd(oracle):
     assert np.linalg.eigvalsh(G).min() > -1e-13
 
 
+@pytest.mark.parametrize("a,b", [(0.7, -1.3), (2.9, 0.4), (-2.2, 3.0)])
+def test_imaginary_part_closed_form(oracle, a, b):
+    """RY(a) then RZ(b) on |0>: with phi = RY(a)|0> real, <d_0 psi|d_1 psi> = (1/4)<phi|Y Z|phi> =
+    (i/4)<phi|X|phi> = (i/4) sin a, and <psi|d_0 psi> = 0, so G_01 = i sin(a)/4 (Re 0); a conjugated
+    or reversed inner product gives the opposite sign."""
+    bld = W._CircuitBuilder(1)
+    bld.rot(W.RY, 0)
+    bld.rot(W.RZ, 0)
+    G, _ = oracle.qgt(bld.build(), np.array([a, b]))
+    assert abs(G[0, 1] - 0.25j * np.sin(a)) < 1e-15
+    assert abs(G[1, 0] + 0.25j * np.sin(a)) < 1e-15
+
+
+def test_imaginary_part_present(oracle):
+    """On a generic circuit Im G is antisymmetric and far from zero (the Hermitian pin is not vacuous)."""
+    p = W.random_problem(5, 60, 6, 31)
+    G, _ = oracle.qgt(p.circuit, p.theta)
+    assert np.abs(G.imag).max() > 0.05
+    np.testing.assert_allclose(G.imag, -G.imag.T, atol=1e-15)
+
+
 def test_fidelity_expansion(oracle):
     """1 - |<psi(theta)|psi(theta + eps)>|^2 = eps^T g eps + O(eps^3)."""
     p = W.config_tfim4()

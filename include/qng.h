@@ -153,6 +153,13 @@ qng_status qng_energy_backward(qng_ctx *ctx, const double *theta, const double *
  * (Eq. 3) by a float64 Cholesky factorisation. g_opt, grad_opt, energy_opt (device, may be NULL)
  * also receive the metric, the gradient and the energy. lambda >= 0; a non-positive pivot sets
  * QNG_ERR_NOT_SPD, reported by qng_sync. */
+/* The natural-gradient descent loop (Eq. 3, Sec. 1): iters times, one qng_step at theta followed by
+ * theta <- theta + dtheta, all on the context's stream. theta (device, sum P_b float64) is read and
+ * updated in place; energies (device, iters * count float64, may be NULL) receives <E> of every
+ * instance at the start of each iteration (row t = iteration t). A device-side error (e.g.
+ * QNG_ERR_NOT_SPD) freezes theta at its last good value and is reported by qng_sync. */
+qng_status qng_optimize(qng_ctx *ctx, double *theta, double dt, double lambda, int iters, double *energies);
+
 qng_status qng_step(qng_ctx *ctx, const double *theta, double dt, double lambda, double *dtheta, double *g_opt,
                     double *grad_opt, double *energy_opt);
 

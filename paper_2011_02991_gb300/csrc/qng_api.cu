@@ -742,6 +742,29 @@ qng_status qng_step(qng_ctx *c, const double *theta, double dt, double lambda, d
     return run(c, kJobSolve | kJobGradient | kJobEnergy | kJobMetric, a);
 }
 
+qng_status qng_optimize(qng_ctx *c, double *theta, double dt, double lambda, int iters, double *energies) {
+    if (!c || iters < 0 || (!theta && c->total_params > 0)) return QNG_ERR_ARG;
+    if (!std::isfinite(dt) || !std::isfinite(lambda) || lambda < 0) return QNG_ERR_ARG;
+    if (!c->ws || !c->prepared) return QNG_ERR_WORKSPACE;
+    double *dth = reinterpret_cast<double *>(c->ws + c->o_io_dtheta);
+    int64_t launches = 0;
+    for (int t = 0; t < iters; ++t) {
+        LaunchArgs a = {};
+        a.theta = theta;
+        a.dtheta_out = dth;
+        a.energy_out = energies ? energies + (int64_t)t * c->count : nullptr;
+        a.dt = dt;
+        a.lambda = lambda;
+        const qng_status s = run(c, kJobSolve | kJobGradient | kJobEnergy | kJobMetric, a);
+        if (s != QNG_OK) return s;
+        launches += c->last_launches + 1;
+        const cudaError_t e = timed(c, 0, [&] { return launch_theta_update(c->work(), theta, dth, c->total_params, c->stream); });
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    c->last_launches = launches;
+    return QNG_OK;
+}
+
 qng_status qng_step_host(qng_ctx *c, const double *theta_host, double dt, double lambda, double *dtheta_host,
                          double *g_host, double *grad_host, double *energy_host) {
     if (!c || !dtheta_host || (!theta_host && c->total_params > 0)) return QNG_ERR_ARG;

@@ -161,6 +161,7 @@ struct LaunchArgs {
 
 // Kernel-side launchers (qng_kernels.cu). Return cudaSuccess or the launch error.
 cudaError_t launch_coef(const Work &w, const double *theta, int64_t total_params, cudaStream_t st);
+cudaError_t launch_theta_update(const Work &w, double *theta, const double *dtheta, int64_t total, cudaStream_t st);
 cudaError_t launch_forward(const Work &w, const Group &g, int precision, int want_eta, cudaStream_t st);
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
                            int metric_im, cudaStream_t st);

@@ -1297,6 +1297,21 @@ cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col, siz
     return set_attrs(k_columns<float, 1>, smem_col_im);
 }
 
+// theta <- theta + dtheta (the parameter update of Eq. 3), skipped once the device status word
+// holds an error so that a failed solve leaves theta at its last good value.
+__global__ void k_theta_update(double *theta, const double *dtheta, int64_t total, const int32_t *status) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total || *status != 0) return;
+    theta[k] += dtheta[k];
+}
+
+cudaError_t launch_theta_update(const Work &w, double *theta, const double *dtheta, int64_t total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    const int t = 256;
+    k_theta_update<<<(unsigned)((total + t - 1) / t), t, 0, st>>>(theta, dtheta, total, w.status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_coef(const Work &w, const double *theta, int64_t total, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     const int t = 256;

@@ -55,6 +55,7 @@ SYMBOLS = {
     "qng_set_stream": [_vp, _vp],
     "qng_metric": [_vp, _vp, _vp, _vp],
     "qng_metric_complex": [_vp, _vp, _vp, _vp, _vp],
+    "qng_optimize": [_vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp],
     "qng_gradient": [_vp, _vp, _vp, _vp],
     "qng_energy": [_vp, _vp, _vp],
     "qng_energy_backward": [_vp, _vp, _vp, _vp],
@@ -247,6 +248,16 @@ class Context:
         _chk(load().qng_step(self._h, _ptr(theta), float(dt), float(lam), _ptr(o["dtheta"]), _ptr(o.get("g")),
                              _ptr(o.get("grad")), _ptr(o.get("energy"))), "qng_step")
         return o
+
+    def optimize(self, theta: torch.Tensor, dt: float = 0.1, lam: float = 1e-3, iters: int = 100):
+        """QNG descent on the device: theta (a float64 tensor on this context's device, contiguous)
+        is updated in place iters times; returns <E> per iteration, shape (iters, count)."""
+        if not (isinstance(theta, torch.Tensor) and theta.dtype == torch.float64 and theta.is_contiguous()
+                and theta.device == self.workspace.device and theta.numel() == self.total_params):
+            raise ValueError("theta must be a contiguous float64 tensor on the context's device with total_params entries")
+        en = torch.empty((int(iters), self.count), dtype=torch.float64, device=self.device)
+        _chk(load().qng_optimize(self._h, _ptr(theta), float(dt), float(lam), int(iters), _ptr(en)), "qng_optimize")
+        return en
 
     def step_host(self, theta_host: np.ndarray, dt: float = 0.1, lam: float = 1e-3, out: dict | None = None,
                   want_all: bool = True):

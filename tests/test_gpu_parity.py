@@ -378,3 +378,63 @@ def test_metric_complex_streaming(qng, oracle, precision, n, seed):
     assert float(np.abs(G - ref).max() / np.abs(ref).max()) <= TOL[precision]
     assert np.all(G.imag == -G.imag.T)
     assert rel(g, ref.real) <= TOL[precision]
+
+
+def test_optimize_matches_oracle_loop(qng, oracle):
+    """qng_optimize's trajectory = the oracle's step iterated on the CPU (10 steps, tfim4)."""
+    p = W.config_tfim4()
+    ctx = qng.Context(p, precision=W.C128)
+    th = ctx.theta0().clone()
+    en = ctx.optimize(th, p.dt, p.lam, 10)
+    ctx.sync()
+    t_ref = p.theta.copy()
+    e_ref = []
+    for _ in range(10):
+        r = oracle.qng_step(W.Problem(p.name, p.circuit, p.hamiltonian, t_ref, p.dt, p.lam))
+        e_ref.append(r["E"])
+        t_ref = t_ref + r["dtheta"]
+    assert rel(th.cpu(), t_ref) <= 1e-10
+    assert rel(en[:, 0].cpu(), e_ref) <= 1e-10
+
+
+def test_optimize_batch_matches_steps(qng):
+    """In a batch every instance follows its own qng_step iteration (host loop vs device loop)."""
+    probs = [p for p in W.config_batch(count=6, precision=W.C128)]
+    ctx = qng.Context(probs, precision=W.C128)
+    th = ctx.theta0().clone()
+    en = ctx.optimize(th, 0.1, 1e-3, 4)
+    t2 = ctx.theta0().clone()
+    e2 = []
+    for _ in range(4):
+        out = ctx.step(t2, 0.1, 1e-3)
+        e2.append(out["energy"].clone())
+        t2 = t2 + out["dtheta"]
+    ctx.sync()
+    assert torch.equal(th, t2)
+    assert torch.equal(en, torch.stack(e2))
+
+
+@pytest.mark.parametrize("n,layers,iters,rel_gap", [(6, 4, 300, 2e-3), (10, 5, 200, 5e-3), (12, 6, 300, 1e-2)])
+def test_optimize_tfim_reaches_ground_energy(qng, oracle, n, layers, iters, rel_gap):
+    """Natural-gradient descent on the open TFIM chain (J = 1, h = 0.7) from small angles reaches
+    the exact ground energy (Lanczos on the oracle's H|v>) to within the ansatz's reach."""
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    ham = W.tfim_chain(n, 1.0, 0.7)
+    N = 1 << n
+    op = LinearOperator((N, N), matvec=lambda v: oracle.hamiltonian_apply(np.asarray(v, complex).ravel(), ham),
+                        dtype=complex)
+    E0 = float(eigsh(op, k=1, which="SA")[0][0])
+    c = W.layered_ansatz(n, layers)
+    rng = np.random.Generator(np.random.PCG64(5))
+    p = W.Problem(f"vqe_tfim{n}", c, ham, rng.uniform(-0.2, 0.2, c.num_params))
+    ctx = qng.Context(p, precision=W.C128)
+    th = ctx.theta0().clone()
+    en = ctx.optimize(th, 0.1, 1e-3, iters)[:, 0].cpu().numpy()
+    ctx.sync()
+    assert en[0] > 0.0 > E0
+    assert en[-1] >= E0 - 1e-9  # variational bound
+    assert (en[-1] - E0) / abs(E0) <= rel_gap
+    # the final energy is the energy of the final parameters
+    e_fin = ctx.energy(th)
+    ctx.sync()
+    assert abs(float(e_fin[0]) - oracle.energy(c, ham, th.cpu().numpy())) <= 1e-10 * abs(E0)

@@ -150,7 +150,9 @@ qng_status qng_energy(qng_ctx *ctx, const double *theta, double *energy);
 qng_status qng_energy_backward(qng_ctx *ctx, const double *theta, const double *grad_out, double *grad_theta);
 
 /* One natural-gradient step: dtheta (device, sum P_b) solves (g + lambda I) dtheta = -dt grad<E>
- * (Eq. 3) by a float64 Cholesky factorisation. g_opt, grad_opt, energy_opt (device, may be NULL)
+ * (Eq. 3) by a float64 Cholesky factorisation: one kernel per instance when the rows fit in the
+ * shared memory of a cluster (P up to about 330), else, for a single instance, one launch per
+ * 16-column block with the factor in global memory (P up to about 1300), else one CTA. g_opt, grad_opt, energy_opt (device, may be NULL)
  * also receive the metric, the gradient and the energy. lambda >= 0; a non-positive pivot sets
  * QNG_ERR_NOT_SPD, reported by qng_sync. */
 /* The natural-gradient descent loop (Eq. 3, Sec. 1): iters times, one qng_step at theta followed by

@@ -77,7 +77,8 @@ struct qng_ctx {
     size_t o_status = 0, o_inst = 0, o_param = 0, o_fixed = 0, o_diag = 0, o_term = 0, o_work = 0, o_ginst = 0;
     size_t o_coef = 0, o_sigma = 0, o_scale = 0, o_L = 0, o_grad = 0, o_energy = 0, o_chol = 0, o_ckpt = 0, o_eta = 0;
     size_t o_io_theta = 0, o_io_dtheta = 0, o_io_g = 0, o_io_grad = 0, o_io_energy = 0;
-    size_t ws_bytes = 0;
+    size_t ws_bytes = 0;      // bytes the current plan needs
+    size_t ws_cap = 0;        // bytes of the workspace the caller set
     unsigned char *ws = nullptr;
     cudaStream_t stream = nullptr;
     bool prepared = false;
@@ -91,6 +92,10 @@ struct qng_ctx {
     size_t o_reg[large::kRegs] = {0, 0, 0};
     size_t o_regscale = 0, o_partial = 0, o_slotfac = 0, o_pdesc = 0, o_pops = 0, o_red = 0;
     size_t o_queue = 0;
+    // block solve (one instance whose P is beyond the cluster solve's shared memory)
+    bool bsolve = false;
+    int bs_C = 1;
+    size_t o_srhs = 0, o_sy = 0, o_sdinv = 0;
     // CUDA graph of one captured qng_step
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -141,6 +146,9 @@ struct qng_ctx {
         w.energy = reinterpret_cast<double *>(ws + o_energy);
         w.chol = reinterpret_cast<double *>(ws + o_chol);
         w.Lim = w.chol;
+        w.srhs = reinterpret_cast<double *>(ws + o_srhs);
+        w.sy = reinterpret_cast<double *>(ws + o_sy);
+        w.sdinv = reinterpret_cast<double *>(ws + o_sdinv);
         w.ckpt = ws + o_ckpt;
         w.eta = ws + o_eta;
         return w;
@@ -150,6 +158,8 @@ struct qng_ctx {
 namespace {
 
 size_t amp_bytes(int precision) { return precision == QNG_C128 ? 16 : 8; }
+
+int solve_cluster_log2(int max_P);
 
 int default_cl(int n, int precision) {
     const int base = 9;  // measured best for both precisions at 12 qubits: 8 CTAs of 512 amplitudes
@@ -167,6 +177,15 @@ int default_threads(int nl) {
     if (Nl <= 256) return 64;
     if (Nl <= 1024) return 128;
     return 256;
+}
+
+// Block-solve scratch (right-hand side, y, inverse diagonal blocks), empty without the block solve.
+template <class Take> void take_block_solve(qng_ctx *c, Take &take) {
+    const int P = c->bsolve ? c->inst[0].P : 0;
+    const int nblk = (P + kSolveBlock - 1) / kSolveBlock;
+    c->o_srhs = take(sizeof(double) * P);
+    c->o_sy = take(sizeof(double) * P);
+    c->o_sdinv = take(sizeof(double) * nblk * kSolveBlock * kSolveBlock);
 }
 
 // Streaming path: schedule of passes and the workspace layout (no checkpoints).
@@ -200,6 +219,7 @@ qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
     c->o_io_g = take(sizeof(double) * c->total_metric);
     c->o_io_grad = take(sizeof(double) * c->total_params);
     c->o_io_energy = take(sizeof(double) * c->count);
+    take_block_solve(c, take);
     c->o_regscale = take(sizeof(double) * 2 * large::kRegs);
     c->o_partial = take(sizeof(double) * (size_t)c->sched.max_slots * c->l_grid);
     c->o_slotfac = take(sizeof(double) * (size_t)c->sched.max_slots);
@@ -301,6 +321,13 @@ qng_status plan(qng_ctx *c) {
     c->total_params = c->param_off[c->count];
     c->total_metric = c->metric_off[c->count];
     c->streaming = c->count == 1 && (c->path == 2 || (c->path == 0 && c->inst[0].n > kMaxQubitsSmall));
+    // the block solve takes over where the cluster solve's rows no longer fit in shared memory
+    c->bsolve = false;
+    if (c->count == 1 && c->inst[0].P >= kBlockSolveMinP && solve_cluster_log2(c->inst[0].P) < 0 &&
+        sblock_smem_bytes(c->inst[0].P, 8) <= kMaxSmem) {
+        c->bsolve = true;
+        c->bs_C = 8;
+    }
     if (c->streaming) return plan_streaming(c, scale_n);
 
     // groups: instances sharing (cluster size, column CTA size, forward CTA size)
@@ -384,6 +411,7 @@ qng_status plan(qng_ctx *c) {
     c->o_io_grad = take(sizeof(double) * c->total_params);
     c->o_io_energy = take(sizeof(double) * c->count);
     c->o_queue = take(256 * std::max<size_t>(c->groups.size(), 1));
+    take_block_solve(c, take);
     c->o_ckpt = take(ab * (size_t)ckpt_amps);
     c->o_eta = take(ab * (size_t)eta_amps);
     c->ws_bytes = align256(off);
@@ -447,6 +475,7 @@ qng_status upload(qng_ctx *c) {
         if ((e = large::prepare_pass(c->precision, std::max<size_t>(pass_smem, 1))) != cudaSuccess) return cuda_status(e);
         const int scl = solve_cluster_log2(c->max_P);
         if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
+        if (c->bsolve && (e = prepare_sblock(c->inst[0].P, c->bs_C)) != cudaSuccess) return cuda_status(e);
         c->prepared = true;
         return QNG_OK;
     }
@@ -459,6 +488,7 @@ qng_status upload(qng_ctx *c) {
     if ((e = prepare_kernels(c->precision, sf, sc, sci)) != cudaSuccess) return cuda_status(e);
     const int scl = solve_cluster_log2(c->max_P);
     if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
+    if (c->bsolve && (e = prepare_sblock(c->inst[0].P, c->bs_C)) != cudaSuccess) return cuda_status(e);
     // batched contexts: persistent column launches fed by a device work counter per group
     for (size_t k = 0; k < c->groups.size(); ++k) {
         Group &g = c->groups[k];
@@ -560,6 +590,8 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
         if (e != cudaSuccess) return cuda_status(e);
         launches += 1;
     }
+    LaunchArgs a = args;
+    a.jobs = jobs;
     if (need_cols) {
         const int wm = (jobs & (kJobMetric | kJobSolve)) ? 1 : 0;
         const int wg = (jobs & (kJobGradient | kJobSolve)) ? 1 : 0;
@@ -571,15 +603,23 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
             launches += 1;
         }
     }
-    LaunchArgs a = args;
-    a.jobs = jobs;
     const int scl = solve_cluster_log2(c->max_P);
-    if ((jobs & kJobSolve) && scl >= 0)
+    if ((jobs & kJobSolve) && c->bsolve) {
+        const int P = c->inst[0].P, nblk = (P + kSolveBlock - 1) / kSolveBlock;
+        e = timed(c, 3, [&] {
+            cudaError_t r = cudaSuccess;
+            for (int K = 0; K < nblk && r == cudaSuccess; ++K) r = launch_sblock(w, a, P, c->bs_C, K, c->stream);
+            return r == cudaSuccess ? launch_sback(w, a, P, c->stream) : r;
+        });
+        launches += nblk + 1;
+    } else if ((jobs & kJobSolve) && scl >= 0) {
         e = timed(c, 3, [&] { return launch_solve(w, c->count, c->max_P, scl, a, c->stream); });
-    else
+        launches += 1;
+    } else {
         e = timed(c, 3, [&] { return launch_finish(w, c->count, c->max_P, a, c->stream); });
+        launches += 1;
+    }
     if (e != cudaSuccess) return cuda_status(e);
-    launches += 1;
     c->last_launches = launches;
     return QNG_OK;
 }
@@ -650,6 +690,7 @@ qng_status qng_set_workspace(qng_ctx *c, void *workspace, size_t bytes, void *st
     if (!c) return QNG_ERR_ARG;
     if (!workspace || bytes < c->ws_bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return QNG_ERR_WORKSPACE;
     c->ws = static_cast<unsigned char *>(workspace);
+    c->ws_cap = bytes;
     c->stream = static_cast<cudaStream_t>(stream);
     return upload(c);
 }
@@ -668,9 +709,8 @@ qng_status qng_set_tuning(qng_ctx *c, int min_qubits, int cluster_log2, int thre
     c->tune_min_qubits = min_qubits;
     c->tune_cl = cluster_log2 == 0 && threads == 0 && min_qubits == 0 ? -1 : cluster_log2;
     c->tune_threads = threads;
-    const size_t old_bytes = c->ws_bytes;
     qng_status s = plan(c);
-    if (s != QNG_OK || c->ws_bytes > old_bytes) {
+    if (s != QNG_OK || (c->ws && c->ws_bytes > c->ws_cap)) {
         c->tune_min_qubits = old_min; c->tune_cl = old_cl; c->tune_threads = old_th;
         plan(c);
         if (c->ws) upload(c);
@@ -815,10 +855,9 @@ qng_status qng_set_path(qng_ctx *c, int path) {
     if (path == 1 && c->count == 1 && c->inst[0].n > kMaxQubitsSmall) return QNG_ERR_UNSUPPORTED;
     if (path == 2 && c->count != 1) return QNG_ERR_UNSUPPORTED;
     const int old = c->path;
-    const size_t old_bytes = c->ws_bytes;
     c->path = path;
     qng_status s = plan(c);
-    if (s != QNG_OK || (c->ws && c->ws_bytes > old_bytes)) {
+    if (s != QNG_OK || (c->ws && c->ws_bytes > c->ws_cap)) {
         c->path = old;
         plan(c);
         if (c->ws) upload(c);
@@ -865,7 +904,7 @@ qng_status qng_autotune(qng_ctx *c, const double *theta, int reps, int64_t *repo
     if (c->streaming) return QNG_OK;  // the streaming path has a single shape here
     if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
     if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
-    const size_t bytes = c->ws_bytes;
+    const size_t bytes = c->ws_cap;  // shapes must fit the workspace the caller set
     double *scratch_out = reinterpret_cast<double *>(c->ws + c->o_io_dtheta);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return QNG_ERR_CUDA;
@@ -955,9 +994,8 @@ qng_status qng_set_shape(qng_ctx *c, int n_qubits, int cluster_log2, int threads
     c->tuned_cl[n_qubits] = cluster_log2;
     c->tuned_threads[n_qubits] = threads;
     c->tuned_fwd[n_qubits] = forward_threads;
-    const size_t old_bytes = c->ws_bytes;
     qng_status s = plan(c);
-    if (s != QNG_OK || (c->ws && c->ws_bytes > old_bytes)) {
+    if (s != QNG_OK || (c->ws && c->ws_bytes > c->ws_cap)) {
         c->tuned_cl[n_qubits] = ocl;
         c->tuned_threads[n_qubits] = oth;
         c->tuned_fwd[n_qubits] = ofth;

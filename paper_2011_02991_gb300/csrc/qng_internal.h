@@ -84,6 +84,8 @@ struct DevWork {
     int32_t inst;
     int32_t col;  // 0..P-1: metric column; P: gradient (adjoint) column
 };
+constexpr int kSolveBlock = 16;      // block width of the block solve
+constexpr int kBlockSolveMinP = 48;  // smaller instances use k_finish
 
 // Coefficients of parameter k (float64): c = cos(theta/2), s = sin(theta/2), and the scaled
 // form of the adjoint rotation R^dag = c I + i s sigma = f (I + i t sigma) (|c| >= |s|) or
@@ -112,6 +114,9 @@ struct Work {
     double *energy;           // <E>
     double *chol;             // P*P per instance
     double *Lim;              // (1/4) Im L_ij, i < j (complex metric calls only; shares chol's region)
+    double *srhs;             // block solve: running right-hand side (P)
+    double *sy;               // block solve: y (P)
+    double *sdinv;            // block solve: inverses of the diagonal blocks (nblk x 16 x 16)
     void *ckpt;               // checkpoint amplitudes
     void *eta;                // adjoint seeds
 };
@@ -166,6 +171,18 @@ cudaError_t launch_forward(const Work &w, const Group &g, int precision, int wan
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
                            int metric_im, cudaStream_t st);
 cudaError_t launch_finish(const Work &w, int count, int max_P, const LaunchArgs &a, cudaStream_t st);
+// block solve (qng_solve.cu). Largest own-row count of a CTA over all block columns: CTA 0
+// holds the 16 diagonal-block rows (all P rows when it is alone); a CTA of rank >= 1 holds at most
+// ceil((P - 16) / (C - 1)) rows below the block (block 0 is the worst case).
+__host__ __device__ inline int sblock_rows_max(int P, int C) {
+    if (C == 1) return P;
+    const int per = (P - kSolveBlock + C - 2) / (C - 1);
+    return per > kSolveBlock ? per : kSolveBlock;
+}
+size_t sblock_smem_bytes(int P, int C);
+cudaError_t prepare_sblock(int P, int C);
+cudaError_t launch_sblock(const Work &w, const LaunchArgs &a, int P, int C, int K, cudaStream_t st);
+cudaError_t launch_sback(const Work &w, const LaunchArgs &a, int P, cudaStream_t st);
 cudaError_t launch_solve(const Work &w, int count, int max_P, int cl, const LaunchArgs &a, cudaStream_t st);
 size_t solve_smem_bytes(int P, int cl);
 cudaError_t prepare_solve(size_t smem);

@@ -750,13 +750,14 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
     const cx *ckpt = reinterpret_cast<const cx *>(w.ckpt) + in.ckpt_off;
     const double *scales = w.scale + in.scale_off;
     const int P = in.P;
-    const bool grad_col = (wk.col == P);
+    const int col = wk.col;
+    const bool grad_col = col == P;
 
     double scale_b;
     int nsteps, i0;
     if (!grad_col) {
         // b = F_j^dag sigma_j F_j Psi[j] = U_j^dag sigma_j Psi[j+1]; e_j = <Psi[j]|b>
-        const int j = wk.col;
+        const int j = col;
         const DevParam pj = w.param[in.param_tab + j];
         const cx *psi = ckpt + (uint64_t)j * N;
         scale_b = scales[j];
@@ -921,17 +922,17 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
             if (grad_col) {
                 w.gradraw[in.param_off + (i0 - s)] = -tot;
             } else if (s < nsteps) {
-                w.L[in.metric_off + (int64_t)(i0 - s) * P + wk.col] = 0.25 * tot;
+                w.L[in.metric_off + (int64_t)(i0 - s) * P + col] = 0.25 * tot;
                 if (MIM) {
                     double ti = 0.0;
                     for (int r = 0; r < C; ++r) {
                         const double *rr = cl ? cg::this_cluster().map_shared_rank(red_im, r) : red_im;
                         for (int ww = 0; ww < nw; ++ww) ti += rr[(size_t)row * nw + ww];
                     }
-                    w.Lim[in.metric_off + (int64_t)(i0 - s) * P + wk.col] = 0.25 * ti * fac[row];
+                    w.Lim[in.metric_off + (int64_t)(i0 - s) * P + col] = 0.25 * ti * fac[row];
                 }
             } else {
-                w.sigma[in.param_off + wk.col] = tot;
+                w.sigma[in.param_off + col] = tot;
             }
         }
     }

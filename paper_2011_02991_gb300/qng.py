@@ -7,7 +7,9 @@ call raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
+import weakref
 import os
 from typing import Sequence
 
@@ -76,6 +78,20 @@ SYMBOLS = {
     "qng_destroy": [_vp],
     "qng_status_string": [ctypes.c_int],
 }
+
+
+# Contexts still open at interpreter exit are closed by an atexit hook: the library releases its
+# CUDA streams and events then, before the CUDA runtime itself shuts down.
+_live: "weakref.WeakSet" = weakref.WeakSet()
+
+
+@atexit.register
+def _close_live_contexts():
+    for ctx in list(_live):
+        try:
+            ctx.close()
+        except Exception:
+            pass
 
 
 def load(path: str = LIB_PATH):
@@ -157,6 +173,7 @@ class Context:
                     k += 1
             _chk(L.qng_create_batch(len(self.problems), nq.ctypes.data_as(_i32p), ga, ngs.ctypes.data_as(_i32p), ta,
                                     nts.ctypes.data_as(_i32p), self.precision, ctypes.byref(self._h)), "qng_create_batch")
+        _live.add(self)
         cnt = ctypes.c_int32()
         tp, tm = ctypes.c_int64(), ctypes.c_int64()
         _chk(L.qng_get_sizes(self._h, ctypes.byref(cnt), ctypes.byref(tp), ctypes.byref(tm)), "qng_get_sizes")
@@ -353,6 +370,7 @@ class Context:
         if self._h:
             load().qng_destroy(self._h)
             self._h = _vp()
+            _live.discard(self)
 
     def __del__(self):
         try:

@@ -33,6 +33,10 @@ METRIC = "QNG steps/s (g,∇E,Δθ) per config; HBM GB/s vs GB300 peak; max err 
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 HBM_PEAK_GBS = 6669.2  # measured copy bandwidth of this GPU pool
+# DRAM bytes (read + write) per launch of the timed kernel, from one ncu capture of this build's
+# kernel on the workload (profiles/rand12_p192_c128_step.md); None where no capture of the current
+# kernel exists. At 12 qubits only the first read of the checkpoints reaches DRAM.
+TRAFFIC = {"rand12_p192_c128": 12894976}
 
 
 def workloads():
@@ -365,7 +369,7 @@ def run_ours(args, name, problems, kind, rank, world, local_rank):
         peak = FP64_PEAK_TFLOPS if prec64 else FP32_PEAK_TFLOPS
         achieved = flops_step * args.steps / (col_ms / 1e3) / 1e12 if col_ms > 0 else 0.0
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_columns (recurrence + gradient sweep)",
+                "traffic": TRAFFIC.get(name), "kernel": "k_columns (recurrence + gradient sweep)",
                 "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz" if prec64 else
                                "derived: float32 128 FMA/clk/SM x 152 SMs x 2.07 GHz",
                 "kernel_avg_ms": col_avg_s * 1e3, "flops_per_launch": flops,

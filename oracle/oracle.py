@@ -47,7 +47,7 @@ def lib():
             path = build()
             L = ctypes.CDLL(path)
             L.oracle_apply_gate.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                            ctypes.c_double, ctypes.c_int]
+                                            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int]
             L.oracle_apply_pauli.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_uint64, ctypes.c_uint64]
             L.oracle_hamiltonian_apply.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _u64p, _u64p]
             L.oracle_state.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, _dp]
@@ -72,8 +72,20 @@ def _p(a, t):
     return a.ctypes.data_as(t)
 
 
+# one gate record of the C oracle: kind, q0, q1, param (int32), then the Pauli string of RP/CRP
+_GATE_DTYPE = np.dtype([("kind", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("param", "<i4"),
+                        ("xmask", "<u8"), ("zmask", "<u8")])
+
+
 def _gates(circuit):
-    return np.ascontiguousarray(circuit.gates, dtype=np.int32)
+    g = np.ascontiguousarray(circuit.gates, dtype=np.int32).reshape(-1, 4)
+    out = np.zeros(len(g), dtype=_GATE_DTYPE)
+    for f, name in enumerate(("kind", "q0", "q1", "param")):
+        out[name] = g[:, f]
+    masks = circuit.gate_masks() if hasattr(circuit, "gate_masks") else np.zeros((len(g), 2), np.uint64)
+    out["xmask"] = masks[:, 0]
+    out["zmask"] = masks[:, 1]
+    return out
 
 
 def _check(rc):
@@ -90,11 +102,13 @@ def set_num_threads(t: int) -> None:
 
 
 # single operations ----------------------------------------------------------------------
-def apply_gate(psi: np.ndarray, kind: int, q0: int, q1: int = -1, theta: float = 0.0, mode: int = 0) -> np.ndarray:
-    """Return gate(psi); mode 0 gate, 1 adjoint, 2 derivative, 3 adjoint of the derivative."""
+def apply_gate(psi: np.ndarray, kind: int, q0: int, q1: int = -1, theta: float = 0.0, mode: int = 0,
+               xmask: int = 0, zmask: int = 0) -> np.ndarray:
+    """Return gate(psi); mode 0 gate, 1 adjoint, 2 derivative, 3 adjoint of the derivative.
+    xmask/zmask give the Pauli string of RP/CRP gates."""
     out = np.array(psi, dtype=np.complex128, copy=True)
     n = int(np.log2(out.size))
-    lib().oracle_apply_gate(n, _p(out.view(np.float64), _dp), kind, q0, q1, float(theta), mode)
+    lib().oracle_apply_gate(n, _p(out.view(np.float64), _dp), kind, q0, q1, int(xmask), int(zmask), float(theta), mode)
     return out
 
 

@@ -13,7 +13,10 @@
  *   - <E> = sum_k c_k <psi|sigma_k|psi> and d<E>/d theta_i = 2 Re <psi|H|d_i psi> (Eq. 2 with
  *     the product rule; the paper gives no gradient algorithm).
  * Gate matrices are the textbook ones written entry by entry; derivatives are the entry-wise
- * derivatives of those matrices. Pauli strings are applied one single-qubit Pauli matrix at a
+ * derivatives of those matrices. Generalised rotations (Sec. 2's remark on multi-qubit and
+ * controlled Pauli-string rotations): CR_sigma = |0><0|_c (x) 1 + |1><1|_c (x) R_sigma, and
+ * R_S = exp(-i theta S / 2) = cos(theta/2) 1 - i sin(theta/2) S for a Pauli string S, optionally
+ * controlled; their derivatives are written from the same closed forms. Pauli strings are applied one single-qubit Pauli matrix at a
  * time. None of this shares code with the CUDA path.
  *
  * It also holds literal CPU transcriptions of the paper's recurrences (Alg. 1 and Appendix A's
@@ -36,7 +39,15 @@
 
 typedef double complex cplx;
 
-enum { K_RX = 0, K_RY = 1, K_RZ = 2, K_CZ = 3, K_CNOT = 4, K_X = 5, K_Y = 6, K_Z = 7, K_H = 8 };
+enum { K_RX = 0, K_RY = 1, K_RZ = 2, K_CZ = 3, K_CNOT = 4, K_X = 5, K_Y = 6, K_Z = 7, K_H = 8,
+       K_CRX = 9, K_CRY = 10, K_CRZ = 11, K_RP = 12, K_CRP = 13 };
+
+/* One gate: kind, qubits, parameter index (-1 for fixed gates) and, for K_RP / K_CRP, the Pauli
+ * string S as (xmask, zmask): bit q of xmask/zmask = X/Z part on qubit q, both = Y. */
+typedef struct {
+    int32_t kind, q0, q1, param;
+    uint64_t xmask, zmask;
+} ogate_t;
 
 /* ------------------------------------------------------------------------------------ */
 /* primitives: "apply gate", "clone state", "inner product" (Appendix A, the three operations) */
@@ -74,6 +85,24 @@ static void apply_cnot(cplx *psi, int n, int control, int target) {
     }
 }
 
+/* A 2x2 matrix on qubit t, only on the amplitudes whose control qubit c is 1. With zero_rest the
+ * amplitudes whose control is 0 are set to 0 (the derivative of the identity part). */
+static void apply_c1q(cplx *psi, int n, int c, int t, cplx m00, cplx m01, cplx m10, cplx m11, int zero_rest) {
+    const int64_t N = (int64_t)1 << n;
+    const int64_t cb = (int64_t)1 << c, tb = (int64_t)1 << t;
+#pragma omp parallel for schedule(static) if (N >= 65536)
+    for (int64_t k = 0; k < N; ++k) {
+        if (k & tb) continue;
+        if (!(k & cb)) {
+            if (zero_rest) { psi[k] = 0; psi[k | tb] = 0; }
+            continue;
+        }
+        cplx a = psi[k], b = psi[k | tb];
+        psi[k] = m00 * a + m01 * b;
+        psi[k | tb] = m10 * a + m11 * b;
+    }
+}
+
 static void clone_state(cplx *dst, const cplx *src, int n) {
     memcpy(dst, src, sizeof(cplx) * ((size_t)1 << n));
 }
@@ -95,12 +124,70 @@ static void zero_state(cplx *psi, int n) {
     psi[0] = 1.0;
 }
 
+static void apply_pauli_string(cplx *out, const cplx *psi, int n, uint64_t xm, uint64_t zm);
+
+/*
+ * exp(-i theta S / 2) = cos(theta/2) 1 - i sin(theta/2) S for a Pauli string S (S^2 = 1), on the
+ * amplitudes whose control qubit (ctrl >= 0) is 1; the others keep their value for the gate and
+ * its adjoint and become 0 for the derivatives. With c = cos(theta/2), s = sin(theta/2):
+ *   mode 0: c psi - i s S psi        mode 1 (adjoint): c psi + i s S psi
+ *   mode 2: -(s/2) psi - (i c/2) S psi   (d/dtheta)   mode 3: -(s/2) psi + (i c/2) S psi
+ * S does not act on the control qubit, so S maps the control-1 subspace onto itself.
+ */
+static void apply_pauli_rotation(cplx *psi, int n, int ctrl, uint64_t xm, uint64_t zm, double theta, int mode) {
+    const int64_t N = (int64_t)1 << n;
+    const double c = cos(0.5 * theta), s = sin(0.5 * theta);
+    cplx *sp = (cplx *)malloc(sizeof(cplx) * (size_t)N);
+    if (!sp) return;
+    apply_pauli_string(sp, psi, n, xm, zm);
+    cplx a, b;
+    switch (mode) {
+    case 0: a = c; b = -I * s; break;
+    case 1: a = c; b = I * s; break;
+    case 2: a = -0.5 * s; b = -0.5 * I * c; break;
+    default: a = -0.5 * s; b = 0.5 * I * c; break;
+    }
+    const int64_t cb = ctrl >= 0 ? (int64_t)1 << ctrl : 0;
+    for (int64_t k = 0; k < N; ++k) {
+        if (cb && !(k & cb)) {
+            if (mode >= 2) psi[k] = 0;
+            continue;
+        }
+        psi[k] = a * psi[k] + b * sp[k];
+    }
+    free(sp);
+}
+
 /* mode: 0 = the gate, 1 = its adjoint, 2 = d/dtheta of the gate, 3 = adjoint of the derivative */
-static void apply_gate_mode(cplx *psi, int n, const int32_t *g, double theta, int mode) {
-    const int kind = g[0], q0 = g[1], q1 = g[2];
+static void apply_gate_mode(cplx *psi, int n, const ogate_t *g, double theta, int mode) {
+    const int kind = g->kind, q0 = g->q0, q1 = g->q1;
     const double c = cos(0.5 * theta), s = sin(0.5 * theta);
     cplx m00, m01, m10, m11;
+    int controlled = 0, target = q0;
     switch (kind) {
+    case K_RP: apply_pauli_rotation(psi, n, -1, g->xmask, g->zmask, theta, mode); return;
+    case K_CRP: apply_pauli_rotation(psi, n, q0, g->xmask, g->zmask, theta, mode); return;
+    case K_CRX: case K_CRY: case K_CRZ: {
+        /* |0><0|_c (x) 1 + |1><1|_c (x) R_sigma(theta): R_sigma's matrix (as below) on the target,
+           where the control is 1; its derivative is |1><1|_c (x) dR_sigma/dtheta */
+        const int axis = kind - K_CRX + K_RX;
+        const double cc = c, ss = s;
+        cplx t[4];
+        if (axis == K_RX) {
+            if (mode < 2) { t[0] = cc; t[1] = -I * ss; t[2] = -I * ss; t[3] = cc; }
+            else          { t[0] = -0.5 * ss; t[1] = -0.5 * I * cc; t[2] = -0.5 * I * cc; t[3] = -0.5 * ss; }
+        } else if (axis == K_RY) {
+            if (mode < 2) { t[0] = cc; t[1] = -ss; t[2] = ss; t[3] = cc; }
+            else          { t[0] = -0.5 * ss; t[1] = -0.5 * cc; t[2] = 0.5 * cc; t[3] = -0.5 * ss; }
+        } else {
+            if (mode < 2) { t[0] = cc - I * ss; t[1] = 0; t[2] = 0; t[3] = cc + I * ss; }
+            else          { t[0] = -0.5 * I * (cc - I * ss); t[1] = 0; t[2] = 0; t[3] = 0.5 * I * (cc + I * ss); }
+        }
+        m00 = t[0]; m01 = t[1]; m10 = t[2]; m11 = t[3];
+        controlled = 1;
+        target = q1;
+        break;
+    }
     case K_RX: /* exp(-i t X/2) = [[c, -i s], [-i s, c]] */
         if (mode < 2) { m00 = c; m01 = -I * s; m10 = -I * s; m11 = c; }
         else          { m00 = -0.5 * s; m01 = -0.5 * I * c; m10 = -0.5 * I * c; m11 = -0.5 * s; }
@@ -125,18 +212,20 @@ static void apply_gate_mode(cplx *psi, int n, const int32_t *g, double theta, in
         cplx t = m01;
         m00 = conj(m00); m11 = conj(m11); m01 = conj(m10); m10 = conj(t);
     }
-    apply_1q(psi, n, q0, m00, m01, m10, m11);
+    if (controlled) apply_c1q(psi, n, q0, target, m00, m01, m10, m11, mode >= 2);
+    else apply_1q(psi, n, target, m00, m01, m10, m11);
 }
 
-static int is_rot(int kind) { return kind == K_RX || kind == K_RY || kind == K_RZ; }
+static int is_rot(int kind) { return (kind >= K_RX && kind <= K_RZ) || (kind >= K_CRX && kind <= K_CRP); }
 
 /* ------------------------------------------------------------------------------------ */
 /* exported single operations (for the gate-level pins) */
 
 /* Apply one gate (mode as above) to psi (interleaved complex, 2^n entries). */
-int oracle_apply_gate(int n, double *psi, int kind, int q0, int q1, double theta, int mode) {
-    int32_t g[4] = {kind, q0, q1, -1};
-    apply_gate_mode((cplx *)psi, n, g, theta, mode);
+int oracle_apply_gate(int n, double *psi, int kind, int q0, int q1, uint64_t xmask, uint64_t zmask, double theta,
+                      int mode) {
+    const ogate_t g = {kind, q0, q1, -1, xmask, zmask};
+    apply_gate_mode((cplx *)psi, n, &g, theta, mode);
     return 0;
 }
 
@@ -145,12 +234,12 @@ static void apply_pauli_string(cplx *out, const cplx *psi, int n, uint64_t xm, u
     clone_state(out, psi, n);
     for (int q = 0; q < n; ++q) {
         int x = (int)((xm >> q) & 1u), z = (int)((zm >> q) & 1u);
-        int32_t g[4] = {-1, q, -1, -1};
-        if (x && z) g[0] = K_Y;
-        else if (x) g[0] = K_X;
-        else if (z) g[0] = K_Z;
+        ogate_t g = {-1, q, -1, -1, 0, 0};
+        if (x && z) g.kind = K_Y;
+        else if (x) g.kind = K_X;
+        else if (z) g.kind = K_Z;
         else continue;
-        apply_gate_mode(out, n, g, 0.0, 0);
+        apply_gate_mode(out, n, &g, 0.0, 0);
     }
 }
 
@@ -184,26 +273,26 @@ int oracle_hamiltonian_apply(int n, const double *psi, double *out, int T, const
 /* circuit-level definitions */
 
 /* psi = W U_P ... U_1 |0>: every gate of the list in order (Sec. 2). */
-static void run_circuit(cplx *psi, int n, const int32_t *gates, int G, const double *theta, int deriv_param) {
+static void run_circuit(cplx *psi, int n, const ogate_t *gates, int G, const double *theta, int deriv_param) {
     zero_state(psi, n);
     for (int k = 0; k < G; ++k) {
-        const int32_t *g = gates + 4 * k;
-        if (is_rot(g[0])) {
-            const int mode = (g[3] == deriv_param) ? 2 : 0;
-            apply_gate_mode(psi, n, g, theta[g[3]], mode);
+        const ogate_t *g = gates + k;
+        if (is_rot(g->kind)) {
+            const int mode = (g->param == deriv_param) ? 2 : 0;
+            apply_gate_mode(psi, n, g, theta[g->param], mode);
         } else {
             apply_gate_mode(psi, n, g, 0.0, 0);
         }
     }
 }
 
-int oracle_state(int n, const int32_t *gates, int G, const double *theta, double *psi_out) {
+int oracle_state(int n, const ogate_t *gates, int G, const double *theta, double *psi_out) {
     run_circuit((cplx *)psi_out, n, gates, G, theta, -1);
     return 0;
 }
 
 /* |d_p psi>: the circuit with parametric gate p replaced by its derivative (Alg. 7). */
-int oracle_deriv_state(int n, const int32_t *gates, int G, const double *theta, int p, double *out) {
+int oracle_deriv_state(int n, const ogate_t *gates, int G, const double *theta, int p, double *out) {
     run_circuit((cplx *)out, n, gates, G, theta, p);
     return 0;
 }
@@ -215,7 +304,7 @@ int oracle_deriv_state(int n, const int32_t *gates, int G, const double *theta, 
  *   psi_out (optional, 2^n complex):  the circuit state
  * Every derivative state is built from |0> on its own, so memory is (m + 1) states.
  */
-int oracle_qgt(int n, const int32_t *gates, int G, const double *theta, const int32_t *idx, int m,
+int oracle_qgt(int n, const ogate_t *gates, int G, const double *theta, const int32_t *idx, int m,
                double *G_out, double *T_out, double *psi_out) {
     const size_t N = (size_t)1 << n;
     cplx *psi = (cplx *)malloc(sizeof(cplx) * N);
@@ -236,7 +325,7 @@ int oracle_qgt(int n, const int32_t *gates, int G, const double *theta, const in
 }
 
 /* <E> = sum_k c_k <psi|sigma_k|psi> for the circuit state (Eq. 2's objective). */
-int oracle_energy(int n, const int32_t *gates, int G, const double *theta, int T, const double *coeff,
+int oracle_energy(int n, const ogate_t *gates, int G, const double *theta, int T, const double *coeff,
                   const uint64_t *xm, const uint64_t *zm, double *E_out) {
     const size_t N = (size_t)1 << n;
     cplx *psi = (cplx *)malloc(sizeof(cplx) * N);
@@ -251,7 +340,7 @@ int oracle_energy(int n, const int32_t *gates, int G, const double *theta, int T
 }
 
 /* d<E>/d theta_{idx a} = 2 Re <psi|H|d_{idx a} psi> for a = 0..m-1 (product rule on Eq. 2). */
-int oracle_gradient(int n, const int32_t *gates, int G, const double *theta, int T, const double *coeff,
+int oracle_gradient(int n, const ogate_t *gates, int G, const double *theta, int T, const double *coeff,
                     const uint64_t *xm, const uint64_t *zm, const int32_t *idx, int m, double *grad_out,
                     double *E_out) {
     const size_t N = (size_t)1 << n;
@@ -283,25 +372,25 @@ int oracle_gradient(int n, const int32_t *gates, int G, const double *theta, int
  */
 typedef struct {
     int n, G, P;
-    const int32_t *gates;
+    const ogate_t *gates;
     const double *theta;
     int32_t *first; /* first[k] = index in gates[] of the first fixed gate belonging to U_k */
     int32_t *rot;   /* rot[k] = index in gates[] of rotation k */
     int64_t counts[3];
 } circ_t;
 
-static int circ_init(circ_t *c, int n, const int32_t *gates, int G, const double *theta) {
+static int circ_init(circ_t *c, int n, const ogate_t *gates, int G, const double *theta) {
     c->n = n; c->G = G; c->gates = gates; c->theta = theta;
     c->counts[0] = c->counts[1] = c->counts[2] = 0;
     int P = 0;
-    for (int k = 0; k < G; ++k) P += is_rot(gates[4 * k]);
+    for (int k = 0; k < G; ++k) P += is_rot(gates[k].kind);
     c->P = P;
     c->first = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P + 1));
     c->rot = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P + 1));
     if (!c->first || !c->rot) return -1;
     int p = 0, start = 0;
     for (int k = 0; k < G; ++k) {
-        if (is_rot(gates[4 * k])) { c->first[p] = start; c->rot[p] = k; ++p; start = k + 1; }
+        if (is_rot(gates[k].kind)) { c->first[p] = start; c->rot[p] = k; ++p; start = k + 1; }
     }
     return 0;
 }
@@ -310,15 +399,15 @@ static void circ_free(circ_t *c) { free(c->first); free(c->rot); }
 
 /* k is 0-based here: U_{k+1} in the paper's 1-based notation. mode: 0 U, 1 U^dag, 2 dU, 3 dU^dag */
 static void op_U(circ_t *c, cplx *psi, int k, int mode) {
-    const int32_t *rg = c->gates + 4 * c->rot[k];
-    const double th = c->theta[rg[3]];
+    const ogate_t *rg = c->gates + c->rot[k];
+    const double th = c->theta[rg->param];
     c->counts[0]++;
     if (mode == 0 || mode == 2) {
-        for (int f = c->first[k]; f < c->rot[k]; ++f) apply_gate_mode(psi, c->n, c->gates + 4 * f, 0.0, 0);
+        for (int f = c->first[k]; f < c->rot[k]; ++f) apply_gate_mode(psi, c->n, c->gates + f, 0.0, 0);
         apply_gate_mode(psi, c->n, rg, th, mode == 0 ? 0 : 2);
     } else {
         apply_gate_mode(psi, c->n, rg, th, mode == 1 ? 1 : 3);
-        for (int f = c->rot[k] - 1; f >= c->first[k]; --f) apply_gate_mode(psi, c->n, c->gates + 4 * f, 0.0, 1);
+        for (int f = c->rot[k] - 1; f >= c->first[k]; --f) apply_gate_mode(psi, c->n, c->gates + f, 0.0, 1);
     }
 }
 
@@ -332,7 +421,7 @@ static void op_clone_in(circ_t *c, cplx *dst) { c->counts[1]++; zero_state(dst, 
  * counts. With skip_diag = 1 the diagonal is taken a priori as 1/4 (Eq. L_diag_when_single_pauli)
  * instead of <phi|phi>. psi_out (optional) receives register psi = U_P ... U_1 |in>.
  */
-int oracle_alg1(int n, const int32_t *gates, int G, const double *theta, int skip_diag, double *L_out,
+int oracle_alg1(int n, const ogate_t *gates, int G, const double *theta, int skip_diag, double *L_out,
                 double *T_out, int64_t *counts, double *psi_out) {
     circ_t c;
     if (circ_init(&c, n, gates, G, theta)) { circ_free(&c); return -1; }
@@ -379,7 +468,7 @@ int oracle_alg1(int n, const int32_t *gates, int G, const double *theta, int ski
  * L_ij = <in|phi> after phi := |in>, U_1..U_{j-1}, dU_j, U_j^dag..U_{i+1}^dag, dU_i^dag,
  * U_{i-1}^dag..U_1^dag.
  */
-int oracle_alg3(int n, const int32_t *gates, int G, const double *theta, double *L_out, int64_t *counts) {
+int oracle_alg3(int n, const ogate_t *gates, int G, const double *theta, double *L_out, int64_t *counts) {
     circ_t c;
     if (circ_init(&c, n, gates, G, theta)) { circ_free(&c); return -1; }
     const int P = c.P;
@@ -411,7 +500,7 @@ int oracle_alg3(int n, const int32_t *gates, int G, const double *theta, double 
  * skip_last = 1 omits the update phi <- U_1^dag at i = 1, whose result is never read; Table 1's
  * gate count for this algorithm assumes it is omitted.
  */
-int oracle_alg6(int n, const int32_t *gates, int G, const double *theta, int skip_last, double *L_out,
+int oracle_alg6(int n, const ogate_t *gates, int G, const double *theta, int skip_last, double *L_out,
                 int64_t *counts) {
     circ_t c;
     if (circ_init(&c, n, gates, G, theta)) { circ_free(&c); return -1; }
@@ -446,7 +535,7 @@ int oracle_alg6(int n, const int32_t *gates, int G, const double *theta, int ski
  * Appendix A, Alg. 8: every derivative state in its own register, from a rolling suffix;
  * then L_ij = <phi_i|phi_j> for i <= j. (P + 1 registers.)
  */
-int oracle_alg8(int n, const int32_t *gates, int G, const double *theta, double *L_out, int64_t *counts) {
+int oracle_alg8(int n, const ogate_t *gates, int G, const double *theta, double *L_out, int64_t *counts) {
     circ_t c;
     if (circ_init(&c, n, gates, G, theta)) { circ_free(&c); return -1; }
     const int P = c.P;
@@ -487,7 +576,7 @@ void oracle_set_num_threads(int t) { (void)t; }
  *   G_out (m x m complex, Eq. 4), T_out (m complex), grad_out (m, 2 Re <psi|H|d psi>), E_out.
  * Memory: m + 2 states.
  */
-int oracle_sampled(int n, const int32_t *gates, int G, const double *theta, int T, const double *coeff,
+int oracle_sampled(int n, const ogate_t *gates, int G, const double *theta, int T, const double *coeff,
                    const uint64_t *xm, const uint64_t *zm, const int32_t *idx, int m, double *G_out, double *T_out,
                    double *grad_out, double *E_out) {
     const size_t N = (size_t)1 << n;

@@ -11,6 +11,10 @@ Encoding (the C-ABI in ``include/qng.h`` declares the same numbers):
   index of their angle in theta. The paper assumes one unique parameter per gate, applied in
   circuit order (Sec. 2, the definition of U(theta) as U_P ... U_1), so the k-th parametric
   gate of a circuit carries ``param == k``. Fixed gates carry ``param == -1``.
+* Generalised rotations (Sec. 2's remark on multi-qubit and controlled Pauli-string rotations):
+  CRX/CRY/CRZ are |0><0|_c (x) 1 + |1><1|_c (x) R_sigma(theta) with control q0 and target q1;
+  RP is exp(-i theta S / 2) for a Pauli string S; CRP is RP controlled by q0. The string of an
+  RP/CRP gate is the gate's row of ``Circuit.masks`` (xmask, zmask), as for Hamiltonian terms.
 * Qubit q is bit q of a basis-state index (q0 is the least significant bit).
 * A Pauli string is ``(coeff, xmask, zmask)``: bit q of ``xmask``/``zmask`` set means the
   factor on qubit q has an X/Z part; both set means Y; neither means identity.
@@ -30,10 +34,14 @@ import numpy as np
 RX, RY, RZ = 0, 1, 2
 CZ, CNOT = 3, 4
 X, Y, Z, H = 5, 6, 7, 8
-ROTATIONS = (RX, RY, RZ)
+CRX, CRY, CRZ, RP, CRP = 9, 10, 11, 12, 13
+ROTATIONS = (RX, RY, RZ, CRX, CRY, CRZ, RP, CRP)
+SIMPLE_ROTATIONS = (RX, RY, RZ)
+GENERAL_ROTATIONS = (CRX, CRY, CRZ, RP, CRP)
 FIXED_ONE_QUBIT = (X, Y, Z, H)
 FIXED_TWO_QUBIT = (CZ, CNOT)
-KIND_NAMES = {RX: "RX", RY: "RY", RZ: "RZ", CZ: "CZ", CNOT: "CNOT", X: "X", Y: "Y", Z: "Z", H: "H"}
+KIND_NAMES = {RX: "RX", RY: "RY", RZ: "RZ", CZ: "CZ", CNOT: "CNOT", X: "X", Y: "Y", Z: "Z", H: "H",
+              CRX: "CRX", CRY: "CRY", CRZ: "CRZ", RP: "RP", CRP: "CRP"}
 
 # precisions ----------------------------------------------------------------------------
 C64, C128 = 0, 1
@@ -43,10 +51,22 @@ BASE_SEED = 20110299
 
 @dataclass
 class Circuit:
-    """A gate list on ``n`` qubits; ``gates`` is an (G, 4) int32 array of (kind, q0, q1, param)."""
+    """A gate list on ``n`` qubits; ``gates`` is an (G, 4) int32 array of (kind, q0, q1, param);
+    ``masks`` (G, 2) uint64 holds the (xmask, zmask) Pauli string of RP/CRP gates (zeros
+    elsewhere; None when the circuit has none)."""
 
     n: int
     gates: np.ndarray
+    masks: np.ndarray | None = None
+
+    def gate_masks(self) -> np.ndarray:
+        if self.masks is None:
+            return np.zeros((len(self.gates), 2), dtype=np.uint64)
+        return np.ascontiguousarray(self.masks, dtype=np.uint64).reshape(-1, 2)
+
+    @property
+    def has_general(self) -> bool:
+        return bool(np.isin(self.gates[:, 0], GENERAL_ROTATIONS).any())
 
     @property
     def num_params(self) -> int:
@@ -96,18 +116,35 @@ class _CircuitBuilder:
     def __init__(self, n: int):
         self.n = n
         self.rows: list[tuple[int, int, int, int]] = []
+        self.mrows: list[tuple[int, int]] = []
         self.P = 0
 
     def rot(self, kind: int, q: int) -> None:
         self.rows.append((kind, q, -1, self.P))
+        self.mrows.append((0, 0))
+        self.P += 1
+
+    def crot(self, kind: int, control: int, target: int) -> None:
+        """CRX/CRY/CRZ: rotation of target, controlled by control."""
+        self.rows.append((kind, control, target, self.P))
+        self.mrows.append((0, 0))
+        self.P += 1
+
+    def prot(self, labels: dict[int, str], control: int = -1) -> None:
+        """RP (or CRP with a control) of the Pauli string {qubit: 'X'|'Y'|'Z'}."""
+        x, z = _pauli_masks(labels)
+        self.rows.append((RP if control < 0 else CRP, control, -1, self.P))
+        self.mrows.append((x, z))
         self.P += 1
 
     def fixed(self, kind: int, q0: int, q1: int = -1) -> None:
         self.rows.append((kind, q0, q1, -1))
+        self.mrows.append((0, 0))
 
     def build(self) -> Circuit:
         g = np.array(self.rows, dtype=np.int32).reshape(-1, 4)
-        return Circuit(self.n, g)
+        m = np.array(self.mrows, dtype=np.uint64).reshape(-1, 2)
+        return Circuit(self.n, g, m if m.any() else None)
 
 
 def layered_ansatz(n: int, layers: int, rotation_kinds=(RY, RZ), entangler: int = CZ) -> Circuit:
@@ -139,7 +176,7 @@ def random_circuit(n: int, num_gates: int, rng: np.random.Generator, p_fixed: fl
             else:
                 b.fixed(kind, int(rng.integers(n)))
         else:
-            b.rot(int(rng.choice(ROTATIONS)), int(rng.integers(n)))
+            b.rot(int(rng.choice(SIMPLE_ROTATIONS)), int(rng.integers(n)))
     return b.build()
 
 
@@ -282,6 +319,39 @@ def z_run_problem(n: int, num_params: int, seed: int, precision: int = C128, max
         theta = np.pi / 2 + rng.uniform(-0.3, 0.3, c.num_params)
     h = random_pauli_hamiltonian(n, 2 * n, rng)
     return Problem(f"zrun_n{n}_p{num_params}", c, h, theta, precision=precision, meta={"seed": seed})
+
+
+def general_problem(n: int, num_params: int, seed: int, precision: int = C128, max_weight: int = 3) -> Problem:
+    """Every parametric kind, generalised ones included (test and benchmark workload): RX/RY/RZ,
+    CRX/CRY/CRZ with random control and target, RP and CRP of random Pauli strings of weight
+    1..max_weight (the control outside the string), and CZ/CNOT/H fixed gates in between."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = _CircuitBuilder(n)
+    while b.P < num_params:
+        r = rng.random()
+        if r < 0.15 and n >= 2:
+            q0, q1 = rng.choice(n, size=2, replace=False)
+            b.fixed(int(rng.choice([CZ, CNOT])), int(q0), int(q1))
+        elif r < 0.2:
+            b.fixed(H, int(rng.integers(n)))
+        elif r < 0.4:
+            b.rot(int(rng.choice([RX, RY, RZ])), int(rng.integers(n)))
+        elif r < 0.6 and n >= 2:
+            c, t = rng.choice(n, size=2, replace=False)
+            b.crot(int(rng.choice([CRX, CRY, CRZ])), int(c), int(t))
+        else:
+            ctrl = -1
+            pool = list(range(n))
+            if rng.random() < 0.4 and n >= 2:
+                ctrl = int(rng.integers(n))
+                pool.remove(ctrl)
+            w = int(rng.integers(1, min(max_weight, len(pool)) + 1))
+            qs = rng.choice(pool, size=w, replace=False)
+            b.prot({int(q): "XYZ"[int(rng.integers(3))] for q in qs}, ctrl)
+    c = b.build()
+    theta = uniform_theta(c.num_params, rng)
+    h = random_pauli_hamiltonian(n, 2 * n, rng)
+    return Problem(f"general_n{n}_p{num_params}", c, h, theta, precision=precision, meta={"seed": seed})
 
 
 def random_problem(n: int, num_gates: int, num_terms: int, seed: int, precision: int = C128) -> Problem:

@@ -47,14 +47,39 @@ def embed(ops: dict, n: int) -> np.ndarray:
     return out
 
 
-def dense_gate(row, n, theta, sign=-1.0, deriv=False):
-    kind, q0, q1, p = (int(v) for v in row)
+def pauli_ops(x: int, z: int, n: int) -> dict:
+    ops = {}
+    for q in range(n):
+        xb, zb = (x >> q) & 1, (z >> q) & 1
+        if xb or zb:
+            ops[q] = PY if (xb and zb) else (PX if xb else PZ)
+    return ops
+
+
+def generator(kind, q0, q1, x, z, n):
+    """K of a parametric gate exp(-i theta K / 2): sigma on q0; P1 (control q0) x sigma on q1;
+    the Pauli string S; P1 (control q0) x S."""
     if kind in SIGMA:
-        s = SIGMA[kind]
-        R = sla.expm(sign * 1j * theta[p] / 2 * s)
+        return embed({q0: SIGMA[kind]}, n)
+    if kind in (W.CRX, W.CRY, W.CRZ):
+        return embed({q0: P1, q1: SIGMA[kind - W.CRX + W.RX]}, n)
+    if kind == W.RP:
+        return embed(pauli_ops(x, z, n), n)
+    if kind == W.CRP:
+        ops = pauli_ops(x, z, n)
+        ops[q0] = P1
+        return embed(ops, n)
+    raise ValueError(kind)
+
+
+def dense_gate(row, n, theta, sign=-1.0, deriv=False, mask=(0, 0)):
+    kind, q0, q1, p = (int(v) for v in row)
+    if kind in W.ROTATIONS:
+        K = generator(kind, q0, q1, int(mask[0]), int(mask[1]), n)
+        R = sla.expm(sign * 1j * theta[p] / 2 * K)
         if deriv:
-            R = (sign * 1j / 2) * s @ R
-        return embed({q0: R}, n)
+            R = (sign * 1j / 2) * K @ R
+        return R
     if kind in FIXED1:
         return embed({q0: FIXED1[kind]}, n)
     if kind == W.CZ:
@@ -68,8 +93,8 @@ def dense_state(circuit, theta, deriv_param=-1, sign=-1.0):
     n = circuit.n
     psi = np.zeros(1 << n, dtype=complex)
     psi[0] = 1
-    for row in circuit.gates:
-        psi = dense_gate(row, n, theta, sign, deriv=(row[3] == deriv_param and row[3] >= 0)) @ psi
+    for row, m in zip(circuit.gates, circuit.gate_masks()):
+        psi = dense_gate(row, n, theta, sign, deriv=(row[3] == deriv_param and row[3] >= 0), mask=m) @ psi
     return psi
 
 
@@ -146,6 +171,47 @@ def test_pauli_strings_and_hamiltonian_vs_dense(oracle):
     np.testing.assert_allclose(oracle.hamiltonian_apply(psi, ham), dense_hamiltonian(ham, n) @ psi, atol=1e-13)
 
 
+@pytest.mark.parametrize("kind", [W.CRX, W.CRY, W.CRZ])
+@pytest.mark.parametrize("c,t", [(0, 1), (2, 0), (1, 2)])
+def test_controlled_rotations_vs_dense(oracle, kind, c, t):
+    """|0><0|_c (x) 1 + |1><1|_c (x) R_sigma(theta) = exp(-i theta (P1 (x) sigma) / 2) (Sec. 2's
+    controlled rotations); derivative (-i/2) K U, also against a finite difference in theta."""
+    rng = np.random.default_rng(500 + 10 * kind + 3 * c + t)
+    n, theta = 3, np.array([rng.uniform(0, 2 * np.pi)])
+    psi = rand_state(n, rng)
+    row = (kind, c, t, 0)
+    U, dU = dense_gate(row, n, theta), dense_gate(row, n, theta, deriv=True)
+    # the exponential of P1 (x) sigma is the block form, written out
+    blk = embed({c: P0}, n) + embed({c: P1, t: sla.expm(-1j * theta[0] / 2 * SIGMA[kind - W.CRX + W.RX])}, n)
+    np.testing.assert_allclose(U, blk, atol=1e-14)
+    for mode, M in ((0, U), (1, U.conj().T), (2, dU), (3, dU.conj().T)):
+        np.testing.assert_allclose(oracle.apply_gate(psi, kind, c, t, theta[0], mode), M @ psi, atol=1e-14)
+    h = 1e-6
+    fd = (oracle.apply_gate(psi, kind, c, t, theta[0] + h, 0) - oracle.apply_gate(psi, kind, c, t, theta[0] - h, 0)) / (2 * h)
+    np.testing.assert_allclose(oracle.apply_gate(psi, kind, c, t, theta[0], 2), fd, atol=1e-9)
+
+
+@pytest.mark.parametrize("labels,control", [({0: "X", 1: "X"}, -1), ({0: "Y", 2: "Z"}, -1), ({0: "X", 1: "Y", 2: "Z"}, -1),
+                                            ({1: "Y"}, 0), ({0: "Z", 2: "X"}, 1), ({1: "Y", 2: "Y"}, 0)])
+def test_pauli_string_rotations_vs_dense(oracle, labels, control):
+    """exp(-i theta S / 2) of a Pauli string (Sec. 2's multi-qubit rotations), optionally
+    controlled: against scipy's matrix exponential of the dense generator."""
+    rng = np.random.default_rng(len(labels) * 7 + control + 40)
+    n, theta = 3, np.array([rng.uniform(0, 2 * np.pi)])
+    psi = rand_state(n, rng)
+    x, z = W._pauli_masks(labels)
+    kind = W.RP if control < 0 else W.CRP
+    row = (kind, control, -1, 0)
+    U = dense_gate(row, n, theta, mask=(x, z))
+    dU = dense_gate(row, n, theta, deriv=True, mask=(x, z))
+    for mode, M in ((0, U), (1, U.conj().T), (2, dU), (3, dU.conj().T)):
+        got = oracle.apply_gate(psi, kind, control, -1, theta[0], mode, xmask=x, zmask=z)
+        np.testing.assert_allclose(got, M @ psi, atol=1e-14)
+    # S^2 = 1: the uncontrolled rotation by 2 pi is -1
+    if control < 0:
+        np.testing.assert_allclose(oracle.apply_gate(psi, kind, -1, -1, 2 * np.pi, 0, xmask=x, zmask=z), -psi, atol=1e-14)
+
+
 # ------------------------------------------------------------------------------------------
 # circuit level
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
@@ -155,6 +221,62 @@ def test_state_and_derivatives_vs_dense(oracle, seed):
     for k in range(p.P):
         np.testing.assert_allclose(oracle.deriv_state(p.circuit, p.theta, k),
                                    dense_state(p.circuit, p.theta, k), atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_general_circuits_vs_dense(oracle, seed):
+    """States, derivative states and the whole tensor G with every generalised kind (n = 3)."""
+    p = W.general_problem(3, 12, 600 + seed)
+    np.testing.assert_allclose(oracle.state(p.circuit, p.theta), dense_state(p.circuit, p.theta), atol=1e-13)
+    for k in range(p.P):
+        np.testing.assert_allclose(oracle.deriv_state(p.circuit, p.theta, k), dense_state(p.circuit, p.theta, k),
+                                   atol=1e-13)
+    G, T = oracle.qgt(p.circuit, p.theta)
+    Gd, Td = dense_qgt(p.circuit, p.theta)
+    np.testing.assert_allclose(G, Gd, atol=1e-13)
+    np.testing.assert_allclose(T, Td, atol=1e-13)
+
+
+def test_general_derivative_states_vs_finite_differences(oracle):
+    p = W.general_problem(4, 20, 611)
+    h = 1e-5
+    for k in range(p.P):
+        tp, tm = p.theta.copy(), p.theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (oracle.state(p.circuit, tp) - oracle.state(p.circuit, tm)) / (2 * h)
+        np.testing.assert_allclose(oracle.deriv_state(p.circuit, p.theta, k), fd, atol=2e-10)
+
+
+def test_controlled_diagonal_closed_form(oracle):
+    """Sec. 2: a controlled rotation's diagonal is L_ii = (1/4) Prob(control = 1), not 1/4.
+    H on the control gives Prob = 1/2: CRY on |+>|0> has <P1 (x) Y> = 0, so G = 1/8; CRZ has
+    <P1 (x) Z> = 1/2, T = -i/4 and G = 1/8 - 1/16 = 1/16. A control left in |0> gives G = 0."""
+    for kind, expect in ((W.CRY, 1 / 8), (W.CRZ, 1 / 16)):
+        b = W._CircuitBuilder(2)
+        b.fixed(W.H, 0)
+        b.crot(kind, 0, 1)
+        G, _ = oracle.qgt(b.build(), np.array([0.9]))
+        assert abs(G[0, 0] - expect) < 1e-15
+    b = W._CircuitBuilder(2)
+    b.crot(W.CRX, 0, 1)
+    G, _ = oracle.qgt(b.build(), np.array([0.9]))
+    assert abs(G[0, 0]) < 1e-16
+
+
+def test_pauli_string_rotation_closed_forms(oracle):
+    """RP(ZZ) on |00> (an eigenstate): G = 0; RP(XX) on |00>: <XX> = 0 and L = 1/4, so G = 1/4;
+    two RP(XX), RP(YY) on |00>: XX and YY commute, G_01 = <XX YY>/4 - <XX><YY>/4 = -1/4."""
+    for labels, expect in (({0: "Z", 1: "Z"}, 0.0), ({0: "X", 1: "X"}, 0.25)):
+        b = W._CircuitBuilder(2)
+        b.prot(labels)
+        G, _ = oracle.qgt(b.build(), np.array([0.3]))
+        assert abs(G[0, 0] - expect) < 1e-15
+    b = W._CircuitBuilder(2)
+    b.prot({0: "X", 1: "X"})
+    b.prot({0: "Y", 1: "Y"})
+    G, _ = oracle.qgt(b.build(), np.array([0.0, 0.0]))
+    assert abs(G[0, 1] - (-0.25)) < 1e-15
 
 
 def test_derivative_states_vs_finite_differences(oracle):
@@ -370,6 +492,25 @@ def test_recurrences_agree_with_definition(oracle, maker):
     for fn in (oracle.alg3, oracle.alg6, oracle.alg8):
         L, _ = fn(p.circuit, p.theta)
         np.testing.assert_allclose(oracle.hermitian_from_upper(L), L_def, atol=1e-14)
+
+
+def test_recurrences_with_generalised_rotations(oracle):
+    """Alg. 1 (diagonal by simulation), 3, 6 and 8 with controlled and Pauli-string rotations agree
+    with the definition; with a control the a-priori diagonal 1/4 is wrong where Prob(control=1)
+    differs from 1 (Sec. 2), and equals (1/4) Prob(control = 1) there."""
+    p = W.general_problem(4, 24, 71)
+    G, T = oracle.qgt(p.circuit, p.theta)
+    L_def = G + np.outer(T.conj(), T)
+    L1, T1, _, _ = oracle.alg1(p.circuit, p.theta, skip_diag=False)
+    np.testing.assert_allclose(T1, T, atol=1e-14)
+    np.testing.assert_allclose(oracle.hermitian_from_upper(L1), L_def, atol=1e-14)
+    for fn in (oracle.alg3, oracle.alg6, oracle.alg8):
+        L, _ = fn(p.circuit, p.theta)
+        np.testing.assert_allclose(oracle.hermitian_from_upper(L), L_def, atol=1e-14)
+    kinds = p.circuit.param_gates()[:, 0]
+    ctl = np.isin(kinds, [W.CRX, W.CRY, W.CRZ, W.CRP])
+    assert ctl.any() and np.abs(np.diag(L_def).real[ctl] - 0.25).max() > 1e-3
+    np.testing.assert_allclose(np.diag(L_def).real[~ctl], 0.25, atol=1e-14)
 
 
 def test_operation_counts_table1(oracle):

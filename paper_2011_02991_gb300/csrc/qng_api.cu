@@ -17,27 +17,46 @@ namespace {
 
 struct HostInst {
     int n = 0, P = 0;
+    bool general = false;          // has generalised rotations (CRX..CRP)
     std::vector<qng_gate> gates;
+    std::vector<uint64_t> masks;   // (xmask, zmask) per gate
     std::vector<qng_pauli> terms;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-bool is_rot(int k) { return k == QNG_GATE_RX || k == QNG_GATE_RY || k == QNG_GATE_RZ; }
+bool is_gen(int k) { return k >= QNG_GATE_CRX && k <= QNG_GATE_CRP; }
+bool is_rot(int k) { return k == QNG_GATE_RX || k == QNG_GATE_RY || k == QNG_GATE_RZ || is_gen(k); }
 bool is_fixed(int k) { return k >= QNG_GATE_CZ && k <= QNG_GATE_H; }
 bool is_two_qubit(int k) { return k == QNG_GATE_CZ || k == QNG_GATE_CNOT; }
 
-qng_status validate(int n, const qng_gate *gates, int n_gates, const qng_pauli *terms, int n_terms, HostInst &out) {
+qng_status validate(int n, const qng_gate *gates, int n_gates, const uint64_t *masks, const qng_pauli *terms,
+                    int n_terms, HostInst &out) {
     if (n < 1 || n > kMaxQubits || n_gates < 0 || n_terms < 0) return QNG_ERR_ARG;
     if ((n_gates > 0 && !gates) || (n_terms > 0 && !terms)) return QNG_ERR_ARG;
+    const uint64_t full = (n == 64) ? ~0ull : ((1ull << n) - 1);
     out.n = n;
     out.P = 0;
+    out.general = false;
+    out.masks.assign(2 * (size_t)n_gates, 0);
     for (int g = 0; g < n_gates; ++g) {
         const qng_gate &x = gates[g];
-        if (x.q0 < 0 || x.q0 >= n) return QNG_ERR_ARG;
+        const bool string = x.kind == QNG_GATE_RP || x.kind == QNG_GATE_CRP;
+        if (x.kind == QNG_GATE_RP ? x.q0 != -1 : (x.q0 < 0 || x.q0 >= n)) return QNG_ERR_ARG;
+        if (string) {
+            if (!masks) return QNG_ERR_ARG;
+            const uint64_t xm = masks[2 * g], zm = masks[2 * g + 1];
+            if ((xm & ~full) || (zm & ~full)) return QNG_ERR_ARG;
+            if (x.kind == QNG_GATE_CRP && ((xm | zm) >> x.q0) & 1) return QNG_ERR_ARG;  // S must leave the control
+            out.masks[2 * g] = xm;
+            out.masks[2 * g + 1] = zm;
+        }
+        if (x.kind >= QNG_GATE_CRX && x.kind <= QNG_GATE_CRZ && (x.q1 < 0 || x.q1 >= n || x.q1 == x.q0))
+            return QNG_ERR_ARG;
         if (is_rot(x.kind)) {
             if (x.param != out.P) return QNG_ERR_ARG;  // one unique parameter per gate, in circuit order
             out.P++;
+            out.general = out.general || is_gen(x.kind);
         } else if (is_fixed(x.kind)) {
             if (x.param != -1) return QNG_ERR_ARG;
             if (is_two_qubit(x.kind) && (x.q1 < 0 || x.q1 >= n || x.q1 == x.q0)) return QNG_ERR_ARG;
@@ -45,7 +64,6 @@ qng_status validate(int n, const qng_gate *gates, int n_gates, const qng_pauli *
             return QNG_ERR_ARG;
         }
     }
-    const uint64_t full = (n == 64) ? ~0ull : ((1ull << n) - 1);
     for (int t = 0; t < n_terms; ++t) {
         if (!std::isfinite(terms[t].coeff)) return QNG_ERR_ARG;
         if ((terms[t].xmask & ~full) || (terms[t].zmask & ~full)) return QNG_ERR_ARG;
@@ -64,6 +82,7 @@ struct qng_ctx {
     // device-table images (host copies, uploaded by qng_set_workspace)
     std::vector<DevInst> t_inst;
     std::vector<DevParam> t_param;
+    std::vector<DevGen> t_gen;  // one per parameter, like t_param
     std::vector<DevFixed> t_fixed;
     std::vector<DevDiag> t_diag;
     std::vector<DevTerm> t_term;
@@ -75,6 +94,7 @@ struct qng_ctx {
     std::vector<int64_t> param_off, metric_off;
     // workspace layout (byte offsets)
     size_t o_status = 0, o_inst = 0, o_param = 0, o_fixed = 0, o_diag = 0, o_term = 0, o_work = 0, o_ginst = 0;
+    size_t o_pctrl = 0, o_gen = 0;
     size_t o_coef = 0, o_sigma = 0, o_scale = 0, o_L = 0, o_grad = 0, o_energy = 0, o_chol = 0, o_ckpt = 0, o_eta = 0;
     size_t o_io_theta = 0, o_io_dtheta = 0, o_io_g = 0, o_io_grad = 0, o_io_energy = 0;
     size_t ws_bytes = 0;      // bytes the current plan needs
@@ -133,6 +153,7 @@ struct qng_ctx {
         w.status = reinterpret_cast<int32_t *>(ws + o_status);
         w.inst = reinterpret_cast<const DevInst *>(ws + o_inst);
         w.param = reinterpret_cast<const DevParam *>(ws + o_param);
+        w.gen = reinterpret_cast<const DevGen *>(ws + o_gen);
         w.fixed = reinterpret_cast<const DevFixed *>(ws + o_fixed);
         w.diag = reinterpret_cast<const DevDiag *>(ws + o_diag);
         w.term = reinterpret_cast<const DevTerm *>(ws + o_term);
@@ -140,6 +161,7 @@ struct qng_ctx {
         w.group_inst = reinterpret_cast<const int32_t *>(ws + o_ginst);
         w.coef = reinterpret_cast<DevCoef *>(ws + o_coef);
         w.sigma = reinterpret_cast<double *>(ws + o_sigma);
+        w.pctrl = reinterpret_cast<double *>(ws + o_pctrl);
         w.scale = reinterpret_cast<double *>(ws + o_scale);
         w.L = reinterpret_cast<double *>(ws + o_L);
         w.gradraw = reinterpret_cast<double *>(ws + o_grad);
@@ -202,6 +224,7 @@ qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
     c->o_status = take(256);
     c->o_inst = take(sizeof(DevInst) * c->t_inst.size());
     c->o_param = take(sizeof(DevParam) * std::max<size_t>(c->t_param.size(), 1));
+    c->o_gen = take(sizeof(DevGen) * std::max<size_t>(c->t_gen.size(), 1));
     c->o_fixed = take(sizeof(DevFixed) * std::max<size_t>(c->t_fixed.size(), 1));
     c->o_diag = take(sizeof(DevDiag) * std::max<size_t>(c->t_diag.size(), 1));
     c->o_term = take(sizeof(DevTerm) * std::max<size_t>(c->t_term.size(), 1));
@@ -209,6 +232,7 @@ qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
     c->o_ginst = take(8);
     c->o_coef = take(sizeof(DevCoef) * c->total_params);
     c->o_sigma = take(sizeof(double) * c->total_params);
+    c->o_pctrl = take(sizeof(double) * c->total_params);
     c->o_scale = take(sizeof(double) * scale_n);
     c->o_L = take(sizeof(double) * c->total_metric);
     c->o_grad = take(sizeof(double) * c->total_params);
@@ -236,7 +260,7 @@ qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
 
 // Build the device-table images, the launch groups and the workspace layout.
 qng_status plan(qng_ctx *c) {
-    c->t_inst.clear(); c->t_param.clear(); c->t_fixed.clear(); c->t_diag.clear(); c->t_term.clear();
+    c->t_inst.clear(); c->t_param.clear(); c->t_gen.clear(); c->t_fixed.clear(); c->t_diag.clear(); c->t_term.clear();
     c->t_work.clear(); c->t_group_inst.clear(); c->groups.clear();
     c->param_off.assign(c->count + 1, 0);
     c->metric_off.assign(c->count + 1, 0);
@@ -293,13 +317,32 @@ qng_status plan(qng_ctx *c) {
             }
             pending.clear();
         };
-        for (const qng_gate &g : h.gates) {
+        for (size_t gi = 0; gi < h.gates.size(); ++gi) {
+            const qng_gate &g = h.gates[gi];
             if (is_rot(g.kind)) {
                 DevParam p = {};
-                p.axis = g.kind == QNG_GATE_RX ? kAxisX : (g.kind == QNG_GATE_RY ? kAxisY : kAxisZ);
-                p.q = g.q0;
+                DevGen gg = {};
+                if (is_gen(g.kind)) {
+                    // K = C (x) S: a Pauli on the target (CRX..CRZ) or the gate's string (RP, CRP)
+                    p.axis = kAxisGen;
+                    p.q = 0;
+                    if (g.kind == QNG_GATE_RP || g.kind == QNG_GATE_CRP) {
+                        gg.gx = h.masks[2 * gi];
+                        gg.gz = h.masks[2 * gi + 1];
+                    } else {
+                        const uint64_t t = 1ull << g.q1;
+                        gg.gx = g.kind == QNG_GATE_CRZ ? 0 : t;
+                        gg.gz = g.kind == QNG_GATE_CRX ? 0 : t;
+                    }
+                    gg.gctrl = g.kind == QNG_GATE_RP ? 0 : 1ull << g.q0;
+                    gg.gny = __builtin_popcountll(gg.gx & gg.gz) & 3;
+                } else {
+                    p.axis = g.kind == QNG_GATE_RX ? kAxisX : (g.kind == QNG_GATE_RY ? kAxisY : kAxisZ);
+                    p.q = g.q0;
+                }
                 flush_into(p);
                 c->t_param.push_back(p);
+                c->t_gen.push_back(gg);
             } else {
                 pending.push_back(&g);
             }
@@ -321,6 +364,7 @@ qng_status plan(qng_ctx *c) {
     c->total_params = c->param_off[c->count];
     c->total_metric = c->metric_off[c->count];
     c->streaming = c->count == 1 && (c->path == 2 || (c->path == 0 && c->inst[0].n > kMaxQubitsSmall));
+    if (c->streaming && c->inst[0].general) return QNG_ERR_UNSUPPORTED;  // generalised rotations: on-chip only
     // the block solve takes over where the cluster solve's rows no longer fit in shared memory
     c->bsolve = false;
     if (c->count == 1 && c->inst[0].P >= kBlockSolveMinP && solve_cluster_log2(c->inst[0].P) < 0 &&
@@ -359,6 +403,7 @@ qng_status plan(qng_ctx *c) {
         for (int b = 0; b < c->count; ++b) {
             if (shape[b] != key) continue;
             c->t_group_inst.push_back(b);
+            g.general = g.general || c->inst[b].general;
             g.max_n = std::max(g.max_n, c->inst[b].n);
             g.max_P = std::max(g.max_P, c->inst[b].P);
             if (c->inst[b].P > 0)
@@ -393,6 +438,7 @@ qng_status plan(qng_ctx *c) {
     c->o_status = take(256);
     c->o_inst = take(sizeof(DevInst) * c->t_inst.size());
     c->o_param = take(sizeof(DevParam) * c->t_param.size());
+    c->o_gen = take(sizeof(DevGen) * c->t_gen.size());
     c->o_fixed = take(sizeof(DevFixed) * c->t_fixed.size());
     c->o_diag = take(sizeof(DevDiag) * c->t_diag.size());
     c->o_term = take(sizeof(DevTerm) * c->t_term.size());
@@ -400,6 +446,7 @@ qng_status plan(qng_ctx *c) {
     c->o_ginst = take(sizeof(int32_t) * c->t_group_inst.size());
     c->o_coef = take(sizeof(DevCoef) * c->total_params);
     c->o_sigma = take(sizeof(double) * c->total_params);
+    c->o_pctrl = take(sizeof(double) * c->total_params);
     c->o_scale = take(sizeof(double) * scale_n);
     c->o_L = take(sizeof(double) * c->total_metric);
     c->o_grad = take(sizeof(double) * c->total_params);
@@ -442,6 +489,7 @@ qng_status upload(qng_ctx *c) {
     if ((e = cudaMemsetAsync(c->ws + c->o_status, 0, 256, c->stream)) != cudaSuccess) return cuda_status(e);
     if ((e = put(c->o_inst, c->t_inst.data(), sizeof(DevInst) * c->t_inst.size())) != cudaSuccess) return cuda_status(e);
     if ((e = put(c->o_param, c->t_param.data(), sizeof(DevParam) * c->t_param.size())) != cudaSuccess) return cuda_status(e);
+    if ((e = put(c->o_gen, c->t_gen.data(), sizeof(DevGen) * c->t_gen.size())) != cudaSuccess) return cuda_status(e);
     if ((e = put(c->o_fixed, c->t_fixed.data(), sizeof(DevFixed) * c->t_fixed.size())) != cudaSuccess) return cuda_status(e);
     if ((e = put(c->o_diag, c->t_diag.data(), sizeof(DevDiag) * c->t_diag.size())) != cudaSuccess) return cuda_status(e);
     if ((e = put(c->o_term, c->t_term.data(), sizeof(DevTerm) * c->t_term.size())) != cudaSuccess) return cuda_status(e);
@@ -631,11 +679,23 @@ extern "C" {
 qng_status qng_create(int n_qubits, const qng_gate *gates, int n_gates, const qng_pauli *terms, int n_terms,
                       int precision, qng_ctx **out) {
     const int32_t nq = n_qubits, ng = n_gates, nt = n_terms;
-    return qng_create_batch(1, &nq, gates, &ng, terms, &nt, precision, out);
+    return qng_create_batch_ex(1, &nq, gates, &ng, nullptr, terms, &nt, precision, out);
+}
+
+qng_status qng_create_ex(int n_qubits, const qng_gate *gates, int n_gates, const uint64_t *gate_masks,
+                         const qng_pauli *terms, int n_terms, int precision, qng_ctx **out) {
+    const int32_t nq = n_qubits, ng = n_gates, nt = n_terms;
+    return qng_create_batch_ex(1, &nq, gates, &ng, gate_masks, terms, &nt, precision, out);
 }
 
 qng_status qng_create_batch(int count, const int32_t *n_qubits, const qng_gate *gates, const int32_t *n_gates,
                             const qng_pauli *terms, const int32_t *n_terms, int precision, qng_ctx **out) {
+    return qng_create_batch_ex(count, n_qubits, gates, n_gates, nullptr, terms, n_terms, precision, out);
+}
+
+qng_status qng_create_batch_ex(int count, const int32_t *n_qubits, const qng_gate *gates, const int32_t *n_gates,
+                               const uint64_t *gate_masks, const qng_pauli *terms, const int32_t *n_terms,
+                               int precision, qng_ctx **out) {
     if (!out) return QNG_ERR_ARG;
     *out = nullptr;
     if (count < 1 || !n_qubits || !n_gates || !n_terms) return QNG_ERR_ARG;
@@ -652,8 +712,9 @@ qng_status qng_create_batch(int count, const int32_t *n_qubits, const qng_gate *
     }
     int64_t go = 0, to = 0;
     for (int b = 0; b < count; ++b) {
-        qng_status s = validate(n_qubits[b], gates ? gates + go : nullptr, n_gates[b], terms ? terms + to : nullptr,
-                                n_terms[b], c->inst[b]);
+        qng_status s = validate(n_qubits[b], gates ? gates + go : nullptr, n_gates[b],
+                                gate_masks ? gate_masks + 2 * go : nullptr, terms ? terms + to : nullptr, n_terms[b],
+                                c->inst[b]);
         if (s != QNG_OK) { delete c; return s; }
         go += n_gates[b];
         to += n_terms[b];

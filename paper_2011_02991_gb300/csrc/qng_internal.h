@@ -16,6 +16,7 @@ constexpr int kMaxQubits = 30;         // any single instance
 constexpr int kMaxQubitsSmall = 16;    // instances run by the on-chip (cluster-resident) path
 constexpr int kMaxClusterLog2 = 3;     // 8 CTAs per cluster (the portable maximum)
 constexpr int kAxisX = 0, kAxisY = 1, kAxisZ = 2;
+constexpr int kAxisGen = 3;  // generalised rotation: generator K = C (x) S, see DevParam::gx
 
 // One parametric gate k of an instance: U_k = R_k F_k with R_k = exp(-i theta_k sigma / 2).
 struct DevParam {
@@ -27,6 +28,15 @@ struct DevParam {
     int32_t diag_count; //   of the diag table, plus zmask; diag_count = -1 when F_k is not all diagonal
     uint64_t zmask;     //   single-qubit Z factors of F_k
     int32_t zrun;       // Z rotations with diagonal F from k on (this one included, at most kZRunMax); 0 if k is not one
+    int32_t pad;
+};
+
+// Generator of a kAxisGen parameter (same index as its DevParam): K = C (x) S with C the projector
+// onto gctrl's qubits all 1 (gctrl = 0: C = 1) and S = i^gny X^gx Z^gz, so that
+// (S x)[k] = i^gny (-1)^popcount((k ^ gx) & gz) x[k ^ gx].
+struct DevGen {
+    uint64_t gx, gz, gctrl;
+    int32_t gny;
     int32_t pad;
 };
 
@@ -101,6 +111,7 @@ struct Work {
     int32_t *status;          // device status word
     const DevInst *inst;
     const DevParam *param;
+    const DevGen *gen;        // generators of kAxisGen parameters, indexed like param
     const DevFixed *fixed;
     const DevDiag *diag;
     const DevTerm *term;
@@ -114,6 +125,7 @@ struct Work {
     double *energy;           // <E>
     double *chol;             // P*P per instance
     double *Lim;              // (1/4) Im L_ij, i < j (complex metric calls only; shares chol's region)
+    double *pctrl;            // <C_k>: 1 for ordinary rotations, Prob(control = 1) for controlled ones
     double *srhs;             // block solve: running right-hand side (P)
     double *sy;               // block solve: y (P)
     double *sdinv;            // block solve: inverses of the diagonal blocks (nblk x 16 x 16)
@@ -126,6 +138,7 @@ struct Group {
     int cl = 0;
     int threads = 128;      // CTA size of the column kernel
     int fwd_threads = 256;  // CTA size of the checkpoint sweep (k_forward)
+    bool general = false;   // some instance has generalised rotations (GEN kernel instantiations)
     int max_n = 0;
     int max_P = 0;
     int first_inst = 0;   // into group_inst

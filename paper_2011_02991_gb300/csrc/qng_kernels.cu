@@ -169,9 +169,11 @@ template <typename R> struct Eng {
     }
 
     // push my slice to the partner across distributed qubit q; returns my receive buffer
-    __device__ cx *exchange(int q) {
-        const int db = q - nl;
-        const int partner = rank ^ (1 << db);
+    __device__ cx *exchange(int q) { return exchange_rank(rank ^ (1 << (q - nl))); }
+
+    // push my slice to CTA `partner` of the cluster (which pushes its own to me); returns my
+    // receive buffer holding the partner's slice
+    __device__ cx *exchange_rank(int partner) {
         cx *mine = phase ? rv1 : rv0;
         cx *remote = cg::this_cluster().map_shared_rank(mine, partner);
         for (uint32_t l = threadIdx.x; l < Nl; l += blockDim.x) remote[l] = buf[l];
@@ -427,6 +429,116 @@ __device__ __forceinline__ RI<R> col_step(Eng<R> &e, const typename CX<R>::T *a,
     return col_step_cb<R, IM, 0>(e, a, pi, rot_on, RotC<R, 0>{rot.c, rot.s, rot.t}, post, dt);
 }
 
+// ------------------------------------------------------------------------------------------
+// Generalised rotations (Sec. 2: one Pauli string, optionally controlled): generator K = C (x) S,
+// R(theta) = exp(-i theta K / 2) = 1 - C + C (cos(theta/2) - i sin(theta/2) S), dR = (-i/2) K R.
+// Runtime masks and the plain (cos, sin) form: with a control there is no single float64 factor.
+
+// (S x)[k] = i^q x[k ^ gx]: q from S's Y count and the Z signs of the source index
+__device__ __forceinline__ int gen_q(uint64_t k, const DevGen &p) {
+    return (p.gny + 2 * (__popcll((k ^ p.gx) & p.gz) & 1)) & 3;
+}
+// v * i^q by a swap and sign-bit flips (no float64 operation)
+template <typename T2> __device__ __forceinline__ T2 mul_iq(T2 v, int q) {
+    const T2 t = (q & 1) ? T2{v.y, v.x} : v;
+    return T2{flip(t.x, ((q + 1) >> 1) & 1), flip(t.y, (q >> 1) & 1)};
+}
+// c x + ss w, with w = i (S x)[k]: the rotation (ss = -s) or its adjoint (ss = +s)
+template <typename R, typename T2> __device__ __forceinline__ T2 gen_rot(T2 x, T2 w, R c, R ss) {
+    return T2{fma(ss, w.x, c * x.x), fma(ss, w.y, c * x.y)};
+}
+
+// Visit every amplitude of the CTA with its partner under S: f(l, k, x[k], x[k ^ gx]). Partners
+// inside the CTA are visited as pairs by one thread after reading both, so f may write buf[l];
+// a partner in another CTA of the cluster comes from the exchanged copy of that CTA's slice.
+template <typename R, typename F>
+__device__ __forceinline__ void gen_visit(Eng<R> &e, const DevGen &p, F &&f) {
+    using cx = typename CX<R>::T;
+    const uint32_t lx = (uint32_t)(p.gx & (uint64_t)(e.Nl - 1));
+    const int dx = (int)(p.gx >> e.nl);
+    if (dx) {
+        const cx *rv = e.exchange_rank(e.rank ^ dx);
+        for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) f(l, e.base | l, e.buf[l], rv[l ^ lx]);
+    } else if (lx) {
+        const int b = __ffs(lx) - 1;
+        for (uint32_t pr = threadIdx.x; pr < (e.Nl >> 1); pr += blockDim.x) {
+            const uint32_t l0 = ins0(pr, b), l1 = l0 ^ lx;
+            const cx x0 = e.buf[l0], x1 = e.buf[l1];
+            f(l0, e.base | l0, x0, x1);
+            f(l1, e.base | l1, x1, x0);
+        }
+    } else {
+        for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+            const cx x = e.buf[l];
+            f(l, e.base | l, x, x);
+        }
+    }
+}
+
+// Forward generalised rotation (the fixed block F_k has been applied), writing the checkpoint.
+template <typename R>
+__device__ __forceinline__ void fwd_step_gen(Eng<R> &e, typename CX<R>::T *out, const DevGen &p, R c, R s) {
+    using cx = typename CX<R>::T;
+    gen_visit(e, p, [&](uint32_t l, uint64_t kk, cx xm, cx xo) {
+        cx y = xm;
+        if ((kk & p.gctrl) == p.gctrl) y = gen_rot(xm, mul_iq(xo, gen_q(kk, p) + 1), c, -s);
+        e.buf[l] = y;
+        out[kk] = y;
+    });
+    __syncthreads();
+}
+
+// One column step with a generalised rotation: part += <a|K b> (Re / Im / both per IM), then
+// b <- R^dag b when rot_on (F^dag is applied by the caller).
+template <typename R, int IM>
+__device__ __forceinline__ RI<R> col_step_gen(Eng<R> &e, const typename CX<R>::T *a, const DevGen &p, bool rot_on,
+                                              R c, R s) {
+    using cx = typename CX<R>::T;
+    RI<R> part = {0, 0};
+    gen_visit(e, p, [&](uint32_t l, uint64_t kk, cx xm, cx xo) {
+        if ((kk & p.gctrl) != p.gctrl) return;  // K = 0 and R^dag = 1 there
+        const int q = gen_q(kk, p);
+        ipacc<IM>(part, a[kk], mul_iq(xo, q));
+        if (rot_on) e.buf[l] = gen_rot(xm, mul_iq(xo, q + 1), c, s);
+    });
+    __syncthreads();
+    return part;
+}
+
+// Column start of a generalised rotation j (Sec. 2): x = F_j Psi[j]; returns this thread's part of
+// e_j = <x|K x>, leaves b = F_j^dag K x in the state buffer, multiplies scale_b by the float64
+// factors of F_j and F_j^dag and sets escale to that of F_j alone; the warp sums of <x|C x> (the
+// control probability, L_jj = <C_j>/4) go to pcred[warp].
+template <typename R>
+__device__ __forceinline__ R gen_column_start(Eng<R> &e, const Work &w, const DevInst &in, int j,
+                                              const typename CX<R>::T *psi, double *pcred, double &escale,
+                                              double &scale_b) {
+    using cx = typename CX<R>::T;
+    const DevParam pj = w.param[in.param_tab + j];
+    const DevGen gj = w.gen[in.param_tab + j];
+    double sF = 1.0;
+    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) e.buf[l] = psi[e.base | l];
+    __syncthreads();
+    for (int f = 0; f < pj.fix_count; ++f) e.fixed_gate(w.fixed[pj.fix_begin + f], sF);
+    escale = sF;
+    R ep = 0, pc = 0;
+    gen_visit(e, gj, [&](uint32_t l, uint64_t kk, cx xm, cx xo) {
+        cx v = {0, 0};
+        if ((kk & gj.gctrl) == gj.gctrl) {
+            v = mul_iq(xo, gen_q(kk, gj));
+            pc += xm.x * xm.x + xm.y * xm.y;
+        }
+        ep += xm.x * v.x + xm.y * v.y;
+        e.buf[l] = v;
+    });
+    __syncthreads();
+    for (int f = pj.fix_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[pj.fix_begin + f], sF);
+    scale_b *= sF;
+    const double pcw = warp_sum((double)pc);
+    if ((threadIdx.x & 31) == 0) pcred[threadIdx.x >> 5] = pcw;
+    return ep;
+}
+
 // Forward rotation R_k with the diagonal fixed block F_k applied to the inputs (pre), writing
 // both the shared-memory state and the checkpoint out.
 template <typename R, int AX, int CB>
@@ -514,9 +626,10 @@ __device__ __forceinline__ void fwd_step(Eng<R> &e, typename CX<R>::T *out, cons
 }
 
 // ------------------------------------------------------------------------------------------
-__global__ void k_coef(const double *theta, DevCoef *coef, int64_t total, int32_t *status) {
+__global__ void k_coef(const double *theta, DevCoef *coef, double *pctrl, int64_t total, int32_t *status) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= total) return;
+    pctrl[k] = 1.0;  // <C_k> of an uncontrolled rotation; controlled ones are overwritten by their column
     const double th = theta[k];
     if (!isfinite(th)) atomicCAS(status, 0, (int)QNG_ERR_ARG);
     double s, c;
@@ -613,7 +726,9 @@ __device__ __forceinline__ bool fwd_zrun(Eng<R> &e, typename CX<R>::T *ckpt, uin
 
 // ------------------------------------------------------------------------------------------
 // k_forward: one cluster per instance of the group.
-template <typename R>
+// GEN = 1: the group has generalised rotations (a separate instantiation keeps the registers of
+// the ordinary one unchanged).
+template <typename R, int GEN>
 __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl, int want_eta) {
     using cx = typename CX<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -654,6 +769,15 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
         const DevParam pk = pk_n;
         const DevCoef co = co_n;
         if (k + 1 < in.P) { pk_n = w.param[in.param_tab + k + 1]; co_n = w.coef[in.param_off + k + 1]; }
+        if constexpr (GEN) {
+            if (pk.axis == kAxisGen) {  // generalised rotation: F_k gate by gate, then the plain (cos, sin) form
+                for (int f = 0; f < pk.fix_count; ++f) e.fixed_gate(w.fixed[pk.fix_begin + f], scale);
+                fwd_step_gen<R>(e, ckpt + (uint64_t)(k + 1) * N, w.gen[in.param_tab + k], (R)co.c, (R)co.s);
+                if (e.rank == 0 && threadIdx.x == 0) scales[k + 1] = scale;
+                e.maybe_renorm(scale);
+                continue;
+            }
+        }
         if (pk.diag_count < 0)
             for (int f = 0; f < pk.fix_count; ++f) e.fixed_gate(w.fixed[pk.fix_begin + f], scale);
         const bool pre = pk.diag_count > 0 || pk.zmask != 0;
@@ -704,18 +828,20 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
 
 // ------------------------------------------------------------------------------------------
 // k_columns: one cluster per work item (instance, column).
-template <typename R, int MIM>
+template <typename R, int MIM, int GEN>
 __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int cl, int max_P, unsigned char *smem);
 
 // One cluster per work item, or (queue != nullptr) a persistent grid of clusters that take work
 // items, longest first, from a device counter until all num_work are done. MIM = 1: metric
 // columns take Im L_ij as well (into w.Lim); their partial sums need Group::smem_col_im bytes.
-template <typename R, int MIM>
-__global__ void __launch_bounds__(256, MIM ? 2 : 3) k_columns(Work w, int work_first, int cl, int max_P, int *queue, int num_work) {
+// GEN = 1: the group has generalised rotations.
+template <typename R, int MIM, int GEN>
+__global__ void __launch_bounds__(256, (MIM || GEN) ? 2 : 3) k_columns(Work w, int work_first, int cl, int max_P, int *queue,
+                                                                       int num_work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int item_sh;
     if (!queue) {
-        column_item<R, MIM>(w, w.work[work_first + (blockIdx.x >> cl)], cl, max_P, smem);
+        column_item<R, MIM, GEN>(w, w.work[work_first + (blockIdx.x >> cl)], cl, max_P, smem);
         return;
     }
     for (;;) {
@@ -725,18 +851,18 @@ __global__ void __launch_bounds__(256, MIM ? 2 : 3) k_columns(Work w, int work_f
             const int item = *cg::this_cluster().map_shared_rank(&item_sh, 0);
             cg::this_cluster().sync();  // rank 0 keeps item_sh until every CTA has read it
             if (item >= num_work) return;
-            column_item<R, MIM>(w, w.work[work_first + item], cl, max_P, smem);
+            column_item<R, MIM, GEN>(w, w.work[work_first + item], cl, max_P, smem);
         } else {
             __syncthreads();
             const int item = item_sh;
             __syncthreads();
             if (item >= num_work) return;
-            column_item<R, MIM>(w, w.work[work_first + item], cl, max_P, smem);
+            column_item<R, MIM, GEN>(w, w.work[work_first + item], cl, max_P, smem);
         }
     }
 }
 
-template <typename R, int MIM>
+template <typename R, int MIM, int GEN>
 __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int cl, int max_P, unsigned char *smem) {
     using cx = typename CX<R>::T;
     using RA = R;  // per-thread partial sums; float64 from the warp level on
@@ -755,6 +881,8 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
 
     double scale_b;
     int nsteps, i0;
+    bool gen_start = false;     // generalised rotation: <C_j> is reduced too
+    __shared__ double pcred[8]; // per-warp partial sums of <C_j> (at most 8 warps)
     if (!grad_col) {
         // b = F_j^dag sigma_j F_j Psi[j] = U_j^dag sigma_j Psi[j+1]; e_j = <Psi[j]|b>
         const int j = col;
@@ -763,7 +891,10 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
         scale_b = scales[j];
         double escale = 1.0;  // scale of F_j Psi[j] relative to Psi[j] (float64 form with H gates)
         RA ep = 0;
-        if (pj.diag_count >= 0) {
+        if (GEN && pj.axis == kAxisGen) {
+            gen_start = true;
+            if constexpr (GEN) ep = gen_column_start<R>(e, w, in, j, psi, pcred, escale, scale_b);
+        } else if (pj.diag_count >= 0) {
             const uint64_t m = (pj.axis == kAxisZ) ? 0ull : (1ull << pj.q);
             const bool diag = pj.diag_count > 0 || pj.zmask != 0;
             for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
@@ -844,8 +975,11 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
         const double sci = scales[i + 1];
         const cx *a = ckpt + (uint64_t)(i + 1) * N;
         const bool rot_on = (i > 0);
+        const bool gen = GEN && pi.axis == kAxisGen;  // generalised rotation: plain (cos, sin) form, factor 1
         double fs = 1.0;
-        const Rot<R> rot = make_rot<R>(w.coef[in.param_off + i], true, fs);
+        const DevCoef co = w.coef[in.param_off + i];
+        const Rot<R> rot = make_rot<R>(co, true, fs);
+        if (gen) fs = 1.0;
         if (threadIdx.x == 0) {  // thread 0 owns the scale of b
             fac[s] = sci * scale_b;
             rn_flag[s & 1] = 0;
@@ -854,12 +988,21 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
                 rn_flag[s & 1] = ((int)((__double_as_longlong(scale_b) >> 52) & 0x7ff) < 1023 - 200);
             }
         }
-        const bool post = rot_on && (pi.diag_count > 0 || pi.zmask != 0);
+        const bool post = !gen && rot_on && (pi.diag_count > 0 || pi.zmask != 0);
         RI<RA> part;
-        if (mode == 1) part = col_step<R, 1>(e, a, pi, rot_on, rot, post, w.diag);
-        else part = col_step<R, MIM ? 2 : 0>(e, a, pi, rot_on, rot, post, w.diag);
+        if (GEN && gen) {
+            if constexpr (GEN) {
+                const DevGen gi = w.gen[in.param_tab + i];
+                part = (mode == 1) ? col_step_gen<R, 1>(e, a, gi, rot_on, (R)co.c, (R)co.s)
+                                   : col_step_gen<R, MIM ? 2 : 0>(e, a, gi, rot_on, (R)co.c, (R)co.s);
+            }
+        } else if (mode == 1) {
+            part = col_step<R, 1>(e, a, pi, rot_on, rot, post, w.diag);
+        } else {
+            part = col_step<R, MIM ? 2 : 0>(e, a, pi, rot_on, rot, post, w.diag);
+        }
         if (rot_on) {
-            if (pi.diag_count < 0) {
+            if (pi.diag_count < 0 || gen) {  // F_i^dag gate by gate
                 for (int f = pi.fix_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[pi.fix_begin + f], scale_b);
                 if (threadIdx.x == 0 && kScaled)
                     rn_flag[s & 1] = ((int)((__double_as_longlong(scale_b) >> 52) & 0x7ff) < 1023 - 200);
@@ -935,6 +1078,14 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
                 w.sigma[in.param_off + col] = tot;
             }
         }
+        if (GEN && gen_start && threadIdx.x == 0) {  // <C_j> = <x|C x> with the same float64 factor as e_j
+            double t = 0.0;
+            for (int r = 0; r < C; ++r) {
+                const double *pr = cl ? cg::this_cluster().map_shared_rank(pcred, r) : pcred;
+                for (int ww = 0; ww < nw; ++ww) t += pr[ww];
+            }
+            w.pctrl[in.param_off + col] = t * fac[max_P];
+        }
     }
     if (cl) cg::this_cluster().sync();
 }
@@ -949,6 +1100,7 @@ __global__ void __launch_bounds__(512) k_finish(Work w, LaunchArgs a) {
     const DevInst in = w.inst[b];
     const int P = in.P;
     const double *sg = w.sigma + in.param_off;
+    const double *pc = w.pctrl + in.param_off;  // <C_i>: the diagonal L_ii = <C_i>/4 (Sec. 2)
     const double *L = w.L + in.metric_off;
     const bool metric = a.jobs & (kJobMetric | kJobSolve);
     double *A = w.chol + in.metric_off;
@@ -956,7 +1108,7 @@ __global__ void __launch_bounds__(512) k_finish(Work w, LaunchArgs a) {
         for (int64_t idx = threadIdx.x; idx < (int64_t)P * P; idx += blockDim.x) {
             const int i = (int)(idx / P), j = (int)(idx % P);
             double v;
-            if (i == j) v = 0.25 * (1.0 - sg[i] * sg[i]);
+            if (i == j) v = 0.25 * (pc[i] - sg[i] * sg[i]);
             else if (i < j) v = L[(int64_t)i * P + j] - 0.25 * sg[i] * sg[j];
             else v = L[(int64_t)j * P + i] - 0.25 * sg[i] * sg[j];
             if (a.g_out) a.g_out[in.metric_off + idx] = v;
@@ -1078,6 +1230,7 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     const int R = (P + C - 1) / C;
     SolveSmem sm = solve_smem(smem, R, P, C);
     const double *sg = w.sigma + in.param_off;
+    const double *pc = w.pctrl + in.param_off;  // <C_i>: the diagonal L_ii = <C_i>/4 (Sec. 2)
     const double *L = w.L + in.metric_off;
     const double *gr = w.gradraw + in.param_off;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5, tid = threadIdx.x;
@@ -1096,7 +1249,7 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     for (int t = tid; t < nown * P; t += blockDim.x) {
         const int il = t / P, j = t % P, i = il * C + rank;
         double v;
-        if (i == j) v = 0.25 * (1.0 - sg[i] * sg[i]);
+        if (i == j) v = 0.25 * (pc[i] - sg[i] * sg[i]);
         else if (i < j) v = L[(int64_t)i * P + j] - 0.25 * sg[i] * sg[j];
         else v = L[(int64_t)j * P + i] - 0.25 * sg[i] * sg[j];
         if (a.g_out) a.g_out[in.metric_off + (int64_t)i * P + j] = v;
@@ -1289,13 +1442,19 @@ template <typename K> static cudaError_t set_attrs(K kern, size_t smem) {
 cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col, size_t smem_col_im) {
     cudaError_t e;
     if (precision == QNG_C128) {
-        if ((e = set_attrs(k_forward<double>, smem_fwd)) != cudaSuccess) return e;
-        if ((e = set_attrs(k_columns<double, 0>, smem_col)) != cudaSuccess) return e;
-        return set_attrs(k_columns<double, 1>, smem_col_im);
+        if ((e = set_attrs(k_forward<double, 0>, smem_fwd)) != cudaSuccess) return e;
+        if ((e = set_attrs(k_forward<double, 1>, smem_fwd)) != cudaSuccess) return e;
+        if ((e = set_attrs(k_columns<double, 0, 0>, smem_col)) != cudaSuccess) return e;
+        if ((e = set_attrs(k_columns<double, 0, 1>, smem_col)) != cudaSuccess) return e;
+        if ((e = set_attrs(k_columns<double, 1, 0>, smem_col_im)) != cudaSuccess) return e;
+        return set_attrs(k_columns<double, 1, 1>, smem_col_im);
     }
-    if ((e = set_attrs(k_forward<float>, smem_fwd)) != cudaSuccess) return e;
-    if ((e = set_attrs(k_columns<float, 0>, smem_col)) != cudaSuccess) return e;
-    return set_attrs(k_columns<float, 1>, smem_col_im);
+    if ((e = set_attrs(k_forward<float, 0>, smem_fwd)) != cudaSuccess) return e;
+    if ((e = set_attrs(k_forward<float, 1>, smem_fwd)) != cudaSuccess) return e;
+    if ((e = set_attrs(k_columns<float, 0, 0>, smem_col)) != cudaSuccess) return e;
+    if ((e = set_attrs(k_columns<float, 0, 1>, smem_col)) != cudaSuccess) return e;
+    if ((e = set_attrs(k_columns<float, 1, 0>, smem_col_im)) != cudaSuccess) return e;
+    return set_attrs(k_columns<float, 1, 1>, smem_col_im);
 }
 
 // theta <- theta + dtheta (the parameter update of Eq. 3), skipped once the device status word
@@ -1316,7 +1475,7 @@ cudaError_t launch_theta_update(const Work &w, double *theta, const double *dthe
 cudaError_t launch_coef(const Work &w, const double *theta, int64_t total, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     const int t = 256;
-    k_coef<<<(unsigned)((total + t - 1) / t), t, 0, st>>>(theta, w.coef, total, w.status);
+    k_coef<<<(unsigned)((total + t - 1) / t), t, 0, st>>>(theta, w.coef, w.pctrl, total, w.status);
     return cudaGetLastError();
 }
 
@@ -1324,8 +1483,10 @@ cudaError_t launch_forward(const Work &w, const Group &g, int precision, int wan
     if (g.num_inst == 0) return cudaSuccess;
     const int grid = g.num_inst << g.cl;
     if (precision == QNG_C128)
-        return launch_cluster(k_forward<double>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
-    return launch_cluster(k_forward<float>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
+        return g.general ? launch_cluster(k_forward<double, 1>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta)
+                         : launch_cluster(k_forward<double, 0>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
+    return g.general ? launch_cluster(k_forward<float, 1>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta)
+                     : launch_cluster(k_forward<float, 0>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
 }
 
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
@@ -1344,16 +1505,15 @@ cudaError_t launch_columns(const Work &w, const Group &g, int precision, int wit
         if (e != cudaSuccess) return e;
     }
     const int grid = clusters << g.cl;
-    if (metric_im) {
-        if (precision == QNG_C128)
-            return launch_cluster(k_columns<double, 1>, grid, g.threads, g.smem_col_im, g.cl, st, w, first, g.cl, g.max_P,
-                                  queue, num);
-        return launch_cluster(k_columns<float, 1>, grid, g.threads, g.smem_col_im, g.cl, st, w, first, g.cl, g.max_P,
-                              queue, num);
+    const size_t smem = metric_im ? g.smem_col_im : g.smem_col;
+#define QNG_COLS(RT, M, G) launch_cluster(k_columns<RT, M, G>, grid, g.threads, smem, g.cl, st, w, first, g.cl, g.max_P, queue, num)
+    if (precision == QNG_C128) {
+        if (metric_im) return g.general ? QNG_COLS(double, 1, 1) : QNG_COLS(double, 1, 0);
+        return g.general ? QNG_COLS(double, 0, 1) : QNG_COLS(double, 0, 0);
     }
-    if (precision == QNG_C128)
-        return launch_cluster(k_columns<double, 0>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P, queue, num);
-    return launch_cluster(k_columns<float, 0>, grid, g.threads, g.smem_col, g.cl, st, w, first, g.cl, g.max_P, queue, num);
+    if (metric_im) return g.general ? QNG_COLS(float, 1, 1) : QNG_COLS(float, 1, 0);
+    return g.general ? QNG_COLS(float, 0, 1) : QNG_COLS(float, 0, 0);
+#undef QNG_COLS
 }
 
 // Clusters of this group's column kernel that fit on the GPU at once (0 if unknown).
@@ -1370,8 +1530,13 @@ int resident_clusters(const Group &g, int precision) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    cudaError_t e = (precision == QNG_C128) ? cudaOccupancyMaxActiveClusters(&n, k_columns<double, 0>, &cfg)
-                                            : cudaOccupancyMaxActiveClusters(&n, k_columns<float, 0>, &cfg);
+    cudaError_t e;
+    if (precision == QNG_C128)
+        e = g.general ? cudaOccupancyMaxActiveClusters(&n, k_columns<double, 0, 1>, &cfg)
+                      : cudaOccupancyMaxActiveClusters(&n, k_columns<double, 0, 0>, &cfg);
+    else
+        e = g.general ? cudaOccupancyMaxActiveClusters(&n, k_columns<float, 0, 1>, &cfg)
+                      : cudaOccupancyMaxActiveClusters(&n, k_columns<float, 0, 0>, &cfg);
     if (e != cudaSuccess) { cudaGetLastError(); return 0; }
     return n;
 }

@@ -67,6 +67,7 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     int P = 0, nfix = 0, ndiag = 0, pend_begin = 0;
     for (int k = 0; k < n_gates; ++k) {
         const qng_gate &x = gates[k];
+        if (x.kind >= QNG_GATE_CRX && x.kind <= QNG_GATE_CRP) return QNG_ERR_UNSUPPORTED;  // qng_metric takes them
         if (x.q0 < 0 || x.q0 >= n) return QNG_ERR_ARG;
         if (rot_kind(x.kind)) {
             if (x.param != P) return QNG_ERR_ARG;
@@ -163,7 +164,8 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     const size_t o_status = take(256), o_inst = take(sizeof(DevInst)), o_param = take(sizeof(DevParam) * P),
                  o_fixed = take(sizeof(DevFixed) * (nfix ? nfix : 1)), o_diag = take(sizeof(DevDiag) * (ndiag ? ndiag : 1)),
                  o_work = take(sizeof(DevWork) * P), o_ginst = take(sizeof(int32_t)), o_coef = take(sizeof(DevCoef) * P),
-                 o_sigma = take(sizeof(double) * P), o_scale = take(sizeof(double) * (P + 2)),
+                 o_sigma = take(sizeof(double) * P), o_pctrl = take(sizeof(double) * P),
+                 o_scale = take(sizeof(double) * (P + 2)),
                  o_L = take(sizeof(double) * (size_t)P * P), o_grad = take(sizeof(double) * P),
                  o_energy = take(sizeof(double)), o_ckpt = take(ab * ((size_t)(P + 1) << n)), o_eta = take(ab << n);
     if (up256(off) > (size_t)QNG_NOALLOC_SCRATCH_BYTES) return QNG_ERR_WORKSPACE;
@@ -194,6 +196,7 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     w.status = reinterpret_cast<int32_t *>(base + o_status);
     w.inst = reinterpret_cast<const DevInst *>(base + o_inst);
     w.param = reinterpret_cast<const DevParam *>(base + o_param);
+    w.gen = nullptr;  // no generalised rotations here
     w.fixed = reinterpret_cast<const DevFixed *>(base + o_fixed);
     w.diag = reinterpret_cast<const DevDiag *>(base + o_diag);
     w.term = nullptr;
@@ -201,11 +204,14 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     w.group_inst = reinterpret_cast<const int32_t *>(base + o_ginst);
     w.coef = reinterpret_cast<DevCoef *>(base + o_coef);
     w.sigma = reinterpret_cast<double *>(base + o_sigma);
+    w.pctrl = reinterpret_cast<double *>(base + o_pctrl);
     w.scale = reinterpret_cast<double *>(base + o_scale);
     w.L = reinterpret_cast<double *>(base + o_L);
     w.gradraw = reinterpret_cast<double *>(base + o_grad);
     w.energy = reinterpret_cast<double *>(base + o_energy);
     w.chol = w.L;  // the metric-only finish never factorises
+    w.Lim = nullptr;
+    w.srhs = w.sy = w.sdinv = nullptr;
     w.ckpt = base + o_ckpt;
     w.eta = base + o_eta;
 

@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(256) k_sblock(Work w, LaunchArgs a, int K) {
     double *yk = Dv + kSb * kSb;                                // [16]: y_K
     double *Lf = w.chol + in.metric_off;
     const double *sg = w.sigma + in.param_off;
+    const double *pc = w.pctrl + in.param_off;  // <C_i>: the diagonal L_ii = <C_i>/4 (Sec. 2)
     const double *L = w.L + in.metric_off;
     const double *gr = w.gradraw + in.param_off;
     double *rv = w.srhs;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(256) k_sblock(Work w, LaunchArgs a, int K) {
         double v = 0.0;
         if (c < g.nb && col <= l) {
             const int i = P - 1 - l, j = P - 1 - col;  // i <= j
-            const double gv = (i == j) ? 0.25 * (1.0 - sg[i] * sg[i]) : L[(int64_t)i * P + j] - 0.25 * sg[i] * sg[j];
+            const double gv = (i == j) ? 0.25 * (pc[i] - sg[i] * sg[i]) : L[(int64_t)i * P + j] - 0.25 * sg[i] * sg[j];
             if (a.g_out) {
                 a.g_out[in.metric_off + (int64_t)i * P + j] = gv;
                 if (i != j) a.g_out[in.metric_off + (int64_t)j * P + i] = gv;

@@ -50,6 +50,10 @@ SYMBOLS = {
                    ctypes.c_int, ctypes.POINTER(_vp)],
     "qng_create_batch": [ctypes.c_int, _i32p, ctypes.POINTER(qng_gate), _i32p, ctypes.POINTER(qng_pauli), _i32p,
                          ctypes.c_int, ctypes.POINTER(_vp)],
+    "qng_create_ex": [ctypes.c_int, ctypes.POINTER(qng_gate), ctypes.c_int, _vp, ctypes.POINTER(qng_pauli),
+                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
+    "qng_create_batch_ex": [ctypes.c_int, _i32p, ctypes.POINTER(qng_gate), _i32p, _vp, ctypes.POINTER(qng_pauli), _i32p,
+                            ctypes.c_int, ctypes.POINTER(_vp)],
     "qng_get_sizes": [_vp, _i32p, _i64p, _i64p],
     "qng_get_offsets": [_vp, _i64p, _i64p],
     "qng_workspace_size": [_vp, ctypes.POINTER(ctypes.c_size_t)],
@@ -155,7 +159,10 @@ class Context:
             p = self.problems[0]
             ga, ng = _gates_array(p.circuit)
             ta, nt = _terms_array(p.hamiltonian)
-            _chk(L.qng_create(p.n, ga, ng, ta, nt, self.precision, ctypes.byref(self._h)), "qng_create")
+            masks = np.ascontiguousarray(p.circuit.gate_masks(), dtype=np.uint64)
+            self._masks = masks  # kept alive for the call
+            _chk(L.qng_create_ex(p.n, ga, ng, ctypes.c_void_p(masks.ctypes.data), ta, nt, self.precision,
+                                 ctypes.byref(self._h)), "qng_create_ex")
         else:
             rows = [np.ascontiguousarray(p.circuit.gates, dtype=np.int32) for p in self.problems]
             allg = np.concatenate(rows) if rows else np.zeros((0, 4), np.int32)
@@ -171,8 +178,12 @@ class Context:
                 for t in range(h.num_terms):
                     ta[k].coeff = float(h.coeffs[t]); ta[k].xmask = int(h.xmask[t]); ta[k].zmask = int(h.zmask[t])
                     k += 1
-            _chk(L.qng_create_batch(len(self.problems), nq.ctypes.data_as(_i32p), ga, ngs.ctypes.data_as(_i32p), ta,
-                                    nts.ctypes.data_as(_i32p), self.precision, ctypes.byref(self._h)), "qng_create_batch")
+            masks = np.ascontiguousarray(np.concatenate([p.circuit.gate_masks() for p in self.problems])
+                                         if self.problems else np.zeros((0, 2)), dtype=np.uint64)
+            self._masks = masks
+            _chk(L.qng_create_batch_ex(len(self.problems), nq.ctypes.data_as(_i32p), ga, ngs.ctypes.data_as(_i32p),
+                                       ctypes.c_void_p(masks.ctypes.data), ta, nts.ctypes.data_as(_i32p), self.precision,
+                                       ctypes.byref(self._h)), "qng_create_batch_ex")
         _live.add(self)
         cnt = ctypes.c_int32()
         tp, tm = ctypes.c_int64(), ctypes.c_int64()

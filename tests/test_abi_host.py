@@ -64,6 +64,35 @@ def test_validation(lib, gates, n, expect):
         lib.qng_destroy(h)
 
 
+def _create_ex(lib, n, gates, masks, terms=(), precision=W.C128):
+    from paper_2011_02991_gb300 import qng
+    ga = (qng.qng_gate * max(len(gates), 1))(*[qng.qng_gate(*g) for g in gates])
+    ta = (qng.qng_pauli * max(len(terms), 1))(*[qng.qng_pauli(*t) for t in terms])
+    m = None if masks is None else (ctypes.c_uint64 * (2 * len(gates)))(*[v for pair in masks for v in pair])
+    h = ctypes.c_void_p()
+    st = lib.qng_create_ex(n, ga, len(gates), m, ta, len(terms), precision, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("gates,masks,n,expect", [
+    ([(W.CRX, 0, 1, 0)], None, 2, 0),                      # controlled rotation: no string needed
+    ([(W.CRY, 1, 1, 0)], None, 2, 1),                      # control = target
+    ([(W.CRZ, 0, 2, 0)], None, 2, 1),                      # target out of range
+    ([(W.RP, -1, -1, 0)], [(0b11, 0b01)], 2, 0),           # exp(-i theta Y0 X1 / 2)
+    ([(W.RP, -1, -1, 0)], None, 2, 1),                     # a string gate needs the masks
+    ([(W.RP, 0, -1, 0)], [(0b11, 0)], 2, 1),               # RP takes no qubit
+    ([(W.RP, -1, -1, 0)], [(0b100, 0)], 2, 1),             # string outside the qubits
+    ([(W.CRP, 0, -1, 0)], [(0b10, 0b10)], 2, 0),           # Y1 controlled by q0
+    ([(W.CRP, 0, -1, 0)], [(0b11, 0)], 2, 1),              # the string acts on the control
+    ([(W.CRX, 0, 1, 0)], None, 17, 7),                     # generalised rotations: on-chip path only
+])
+def test_generalised_validation(lib, gates, masks, n, expect):
+    st, h = _create_ex(lib, n, gates, masks)
+    assert st == expect
+    if st == 0:
+        lib.qng_destroy(h)
+
+
 def test_pauli_validation(lib):
     st, h = _create(lib, 2, [(W.RY, 0, -1, 0)], [(1.0, 0b100, 0)])
     assert st == 1

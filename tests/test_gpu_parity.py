@@ -494,3 +494,59 @@ def test_block_solve_not_spd(qng, oracle):
     ctx.sync()
     ref = oracle.qng_step(W.Problem(p.name, c, p.hamiltonian, p.theta, 0.1, 1e-3))
     assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[W.C128]
+
+
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+@pytest.mark.parametrize("cl", [0, 1, 2, 3])
+def test_generalised_rotations(qng, oracle, precision, cl):
+    """Controlled rotations and (controlled) Pauli-string rotations (Sec. 2's generalised gates):
+    K = C (x) S with the partner k ^ x in the CTA, in another CTA of the cluster (cl up to 3 puts
+    three of the 7 qubits in the rank), or none (diagonal strings); every output against the oracle,
+    the diagonal through <C_k>."""
+    p = W.general_problem(7, 60, 700 + cl, precision)
+    ctx = qng.Context(p, precision=precision)
+    ctx.set_shape(7, cl, 64, 64)
+    out = ctx.step(ctx.theta0(), p.dt, p.lam)
+    G = ctx.metric_complex(ctx.theta0())
+    ctx.sync()
+    ref = oracle.qng_step(p)
+    for key in ("g", "grad"):
+        assert rel(out[key].cpu(), ref[key]) <= TOL[precision], key
+    assert rel(out["energy"].cpu(), [ref["E"]]) <= TOL[precision]
+    if precision == W.C128:
+        assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[precision]
+    Gn = G.cpu().numpy().reshape(p.P, p.P)
+    assert float(np.abs(Gn - ref["G"]).max() / np.abs(ref["G"]).max()) <= TOL[precision]
+
+
+def test_generalised_rotations_larger(qng, oracle):
+    """12 qubits, P = 150, 8-CTA clusters with 128 threads (the default shape)."""
+    p = W.general_problem(12, 150, 777, W.C128)
+    check_problem(qng, oracle, p, W.C128)
+
+
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+def test_generalised_batch(qng, oracle, precision):
+    """A batch mixing generalised and ordinary instances of 5..9 qubits (persistent column launch)."""
+    probs = [W.general_problem(5 + b % 5, 20 + 4 * b, 800 + b, precision) if b % 2 == 0 else
+             W.random_problem(5 + b % 5, 40 + 4 * b, 8, 820 + b, precision) for b in range(8)]
+    ctx = qng.Context(probs, precision=precision)
+    out = ctx.step(ctx.theta0(), 0.1, 1e-3)
+    ctx.sync()
+    gs, grads = ctx.split_metric(out["g"]), ctx.split_params(out["grad"])
+    for b, p in enumerate(probs):
+        ref = oracle.qng_step(p)
+        assert rel(gs[b].cpu(), ref["g"]) <= TOL[precision], b
+        assert rel(grads[b].cpu(), ref["grad"]) <= TOL[precision], b
+
+
+def test_controlled_diagonal_on_gpu(qng):
+    """H on the control, then CRY: g = (1/4) Prob(control = 1) - (1/4)<P1 (x) Y>^2 = 1/8 exactly."""
+    b = W._CircuitBuilder(2)
+    b.fixed(W.H, 0)
+    b.crot(W.CRY, 0, 1)
+    p = W.Problem("h_cry", b.build(), W.tfim_chain(2), np.array([0.9]))
+    ctx = qng.Context(p, precision=W.C128)
+    g = ctx.metric(ctx.theta0())
+    ctx.sync()
+    assert abs(float(g[0]) - 0.125) < 1e-15

@@ -40,7 +40,8 @@ TRAFFIC = {"rand12_p192_c128": 12894976}
 
 
 def workloads():
-    """name -> (problem or list of problems, kind: single | batch | stream)."""
+    """name -> (problem or list of problems, kind: single | batch | stream | loop).
+    loop: one instance, each timed step is one descent iteration (qng_optimize: step + update)."""
     from paper_2011_02991_gb300 import workloads as W
     return {
         "rand12_p192_c128": (lambda: W.config_rand12(precision=W.C128), "single"),
@@ -53,6 +54,8 @@ def workloads():
         "rand28_p252_c128": (lambda: W.config_rand28(precision=W.C128), "stream"),
         "tfim24_p48_c128": (lambda: W.config_tfim26(n=24, layers=1), "stream"),
         "tfim24_p48_c64": (lambda: _c64(W.config_tfim26(n=24, layers=1)), "stream"),
+        "general12_p192_c128": (lambda: W.general_problem(12, 192, W.BASE_SEED + 6), "single"),
+        "vqe_tfim12_p144_c128": (lambda: W.vqe_tfim(12, 6), "loop"),
     }
 
 
@@ -73,6 +76,11 @@ DESCRIPTION = {
     "rand28_p252_c128": "as rand28_p252_c64 in complex128 (4 GiB per state)",
     "tfim24_p48_c128": "24 qubits, 1 x [Ry, Rz, CZ ladder] (P=48), TFIM, complex128 (streaming, profiling case)",
     "tfim24_p48_c64": "as tfim24_p48_c128 in complex64",
+    "general12_p192_c128": "12 qubits, P=192 mixing Rx/Ry/Rz, CRx/CRy/CRz and (controlled) Pauli-string rotations "
+                           "of weight 1-3 with CZ/CNOT/H between them, 24 random Pauli strings, complex128 "
+                           "(roofline flops count the ordinary-rotation work per element)",
+    "vqe_tfim12_p144_c128": "natural-gradient descent (qng_optimize, one iteration per step: step + theta update) "
+                            "on the open TFIM chain, 12 qubits, 6 x [Ry, Rz, CZ ladder] (P=144), complex128",
 }
 
 
@@ -283,9 +291,16 @@ def run_ours(args, name, problems, kind, rank, world, local_rank):
             ctx.sync()
             err = oracle_check(kind, problems, ctx, outs)
 
+        theta_loop = theta.clone()
+        if args.loop:  # one descent iteration per step, theta updated on the device
+            def one_step():
+                ctx.optimize(theta_loop, dt, lam, 1)
+        else:
+            def one_step():
+                ctx.step(theta, dt, lam, outs)
         for _ in range(args.warmup):
             flush.zero_()
-            ctx.step(theta, dt, lam, outs)
+            one_step()
         ctx.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if world > 1:
@@ -299,7 +314,7 @@ def run_ours(args, name, problems, kind, rank, world, local_rank):
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            ctx.step(theta, dt, lam, outs)
+            one_step()
             launches0 += ctx.last_launch_count()
             ev[k][1].record(stream)
         torch.cuda.synchronize(dev)
@@ -428,6 +443,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     name = args.workload
     make, kind = workloads()[name]
+    args.loop = kind == "loop"
+    if args.loop:
+        kind = "single"
     made = make()
     problems = made if isinstance(made, list) else [made]
     args.sharded = False

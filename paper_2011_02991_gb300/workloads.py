@@ -282,6 +282,15 @@ def config_rand28(seed: int = BASE_SEED + 5, precision: int = C64, n: int = 28, 
     return Problem(f"rand{n}_p{c.num_params}_{tag}", c, h, theta, precision=precision, meta={"seed": seed})
 
 
+def vqe_tfim(n: int = 12, layers: int = 6, seed: int = 5, precision: int = C128) -> Problem:
+    """Natural-gradient VQE on the open TFIM chain (J = 1, h = 0.7): layered Ry/Rz/CZ ansatz from
+    small angles, theta ~ U[-0.2, 0.2] (the descent tests and the loop benchmark)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = layered_ansatz(n, layers)
+    return Problem(f"vqe_tfim{n}_l{layers}", c, tfim_chain(n, 1.0, 0.7), rng.uniform(-0.2, 0.2, c.num_params),
+                   precision=precision, meta={"seed": seed})
+
+
 def z_run_problem(n: int, num_params: int, seed: int, precision: int = C128, max_run: int = 24,
                   near_half_pi: bool = False) -> Problem:
     """Runs of RZ rotations (1..max_run long) separated by RX/RY rotations (test workload).

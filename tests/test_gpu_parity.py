@@ -424,9 +424,8 @@ def test_optimize_tfim_reaches_ground_energy(qng, oracle, n, layers, iters, rel_
     op = LinearOperator((N, N), matvec=lambda v: oracle.hamiltonian_apply(np.asarray(v, complex).ravel(), ham),
                         dtype=complex)
     E0 = float(eigsh(op, k=1, which="SA")[0][0])
-    c = W.layered_ansatz(n, layers)
-    rng = np.random.Generator(np.random.PCG64(5))
-    p = W.Problem(f"vqe_tfim{n}", c, ham, rng.uniform(-0.2, 0.2, c.num_params))
+    p = W.vqe_tfim(n, layers)
+    c = p.circuit
     ctx = qng.Context(p, precision=W.C128)
     th = ctx.theta0().clone()
     en = ctx.optimize(th, 0.1, 1e-3, iters)[:, 0].cpu().numpy()

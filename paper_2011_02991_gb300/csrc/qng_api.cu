@@ -112,6 +112,9 @@ struct qng_ctx {
     size_t o_reg[large::kRegs] = {0, 0, 0};
     size_t o_regscale = 0, o_partial = 0, o_slotfac = 0, o_pdesc = 0, o_pops = 0, o_red = 0;
     size_t o_queue = 0;
+    // mixed-precision solve: cluster size (0 = not used: P < 48 or its float32 matrix does not fit)
+    int ir_C = 0;
+    size_t o_irflag = 0;
     // block solve (one instance whose P is beyond the cluster solve's shared memory)
     bool bsolve = false;
     int bs_C = 1;
@@ -171,6 +174,7 @@ struct qng_ctx {
         w.srhs = reinterpret_cast<double *>(ws + o_srhs);
         w.sy = reinterpret_cast<double *>(ws + o_sy);
         w.sdinv = reinterpret_cast<double *>(ws + o_sdinv);
+        w.irflag = reinterpret_cast<int32_t *>(ws + o_irflag);
         w.ckpt = ws + o_ckpt;
         w.eta = ws + o_eta;
         return w;
@@ -203,6 +207,7 @@ int default_threads(int nl) {
 
 // Block-solve scratch (right-hand side, y, inverse diagonal blocks), empty without the block solve.
 template <class Take> void take_block_solve(qng_ctx *c, Take &take) {
+    c->o_irflag = take(sizeof(int32_t) * c->count);
     const int P = c->bsolve ? c->inst[0].P : 0;
     const int nblk = (P + kSolveBlock - 1) / kSolveBlock;
     c->o_srhs = take(sizeof(double) * P);
@@ -365,6 +370,12 @@ qng_status plan(qng_ctx *c) {
     c->total_metric = c->metric_off[c->count];
     c->streaming = c->count == 1 && (c->path == 2 || (c->path == 0 && c->inst[0].n > kMaxQubitsSmall));
     if (c->streaming && c->inst[0].general) return QNG_ERR_UNSUPPORTED;  // generalised rotations: on-chip only
+    // mixed-precision solve where the cluster solve is there to take over
+    c->ir_C = 0;
+    if (c->max_P >= kBlockSolveMinP && solve_cluster_log2(c->max_P) >= 0) {
+        const int C = c->max_P >= 128 ? 8 : 4;
+        if (solve_ir_smem_bytes(c->max_P, C) <= kMaxSmem) c->ir_C = C;
+    }
     // the block solve takes over where the cluster solve's rows no longer fit in shared memory
     c->bsolve = false;
     if (c->count == 1 && c->inst[0].P >= kBlockSolveMinP && solve_cluster_log2(c->inst[0].P) < 0 &&
@@ -524,6 +535,7 @@ qng_status upload(qng_ctx *c) {
         const int scl = solve_cluster_log2(c->max_P);
         if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
         if (c->bsolve && (e = prepare_sblock(c->inst[0].P, c->bs_C)) != cudaSuccess) return cuda_status(e);
+        if (c->ir_C > 0 && (e = prepare_solve_ir(c->max_P, c->ir_C)) != cudaSuccess) return cuda_status(e);
         c->prepared = true;
         return QNG_OK;
     }
@@ -537,6 +549,7 @@ qng_status upload(qng_ctx *c) {
     const int scl = solve_cluster_log2(c->max_P);
     if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
     if (c->bsolve && (e = prepare_sblock(c->inst[0].P, c->bs_C)) != cudaSuccess) return cuda_status(e);
+    if (c->ir_C > 0 && (e = prepare_solve_ir(c->max_P, c->ir_C)) != cudaSuccess) return cuda_status(e);
     // batched contexts: persistent column launches fed by a device work counter per group
     for (size_t k = 0; k < c->groups.size(); ++k) {
         Group &g = c->groups[k];
@@ -660,6 +673,16 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
             return r == cudaSuccess ? launch_sback(w, a, P, c->stream) : r;
         });
         launches += nblk + 1;
+    } else if ((jobs & kJobSolve) && scl >= 0 && c->ir_C > 0) {
+        // mixed precision first; the float64 cluster solve takes any instance it hands over
+        e = timed(c, 3, [&] {
+            cudaError_t r = launch_solve_ir(w, c->count, c->max_P, c->ir_C, a, c->stream);
+            if (r != cudaSuccess) return r;
+            LaunchArgs ag = a;
+            ag.ir_gate = 1;
+            return launch_solve(w, c->count, c->max_P, scl, ag, c->stream);
+        });
+        launches += 2;
     } else if ((jobs & kJobSolve) && scl >= 0) {
         e = timed(c, 3, [&] { return launch_solve(w, c->count, c->max_P, scl, a, c->stream); });
         launches += 1;

@@ -129,6 +129,7 @@ struct Work {
     double *srhs;             // block solve: running right-hand side (P)
     double *sy;               // block solve: y (P)
     double *sdinv;            // block solve: inverses of the diagonal blocks (nblk x 16 x 16)
+    int32_t *irflag;          // per instance: 1 = the mixed-precision solve left the step to k_solve
     void *ckpt;               // checkpoint amplitudes
     void *eta;                // adjoint seeds
 };
@@ -173,6 +174,7 @@ struct LaunchArgs {
     double *energy_out;   // may be null
     double *dtheta_out;   // may be null
     const double *grad_scale;  // device, one per instance (energy backward), may be null
+    int ir_gate;               // k_solve: only the instances the mixed-precision solve handed over
     double dt, lambda;
     int jobs;
 };
@@ -196,6 +198,10 @@ size_t sblock_smem_bytes(int P, int C);
 cudaError_t prepare_sblock(int P, int C);
 cudaError_t launch_sblock(const Work &w, const LaunchArgs &a, int P, int C, int K, cudaStream_t st);
 cudaError_t launch_sback(const Work &w, const LaunchArgs &a, int P, cudaStream_t st);
+// mixed-precision solve (qng_solve_ir.cu): one cluster of C CTAs per instance
+size_t solve_ir_smem_bytes(int P, int C);
+cudaError_t prepare_solve_ir(int P, int C);
+cudaError_t launch_solve_ir(const Work &w, int count, int max_P, int C, const LaunchArgs &a, cudaStream_t st);
 cudaError_t launch_solve(const Work &w, int count, int max_P, int cl, const LaunchArgs &a, cudaStream_t st);
 size_t solve_smem_bytes(int P, int cl);
 cudaError_t prepare_solve(size_t smem);

@@ -1225,6 +1225,8 @@ __global__ void __launch_bounds__(256) k_solve(Work w, LaunchArgs a, int cl) {
     const int C = 1 << cl;
     const int b = blockIdx.x >> cl;
     const int rank = cl ? (int)cg::this_cluster().block_rank() : 0;
+    // after the mixed-precision solve: only the instances it handed over (same word in every CTA)
+    if (a.ir_gate && w.irflag[b] == 0) return;
     const DevInst in = w.inst[b];
     const int P = in.P;
     const int R = (P + C - 1) / C;

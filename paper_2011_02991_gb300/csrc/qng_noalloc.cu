@@ -212,6 +212,7 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     w.chol = w.L;  // the metric-only finish never factorises
     w.Lim = nullptr;
     w.srhs = w.sy = w.sdinv = nullptr;
+    w.irflag = nullptr;
     w.ckpt = base + o_ckpt;
     w.eta = base + o_eta;
 

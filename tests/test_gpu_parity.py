@@ -549,3 +549,40 @@ def test_controlled_diagonal_on_gpu(qng):
     g = ctx.metric(ctx.theta0())
     ctx.sync()
     assert abs(float(g[0]) - 0.125) < 1e-15
+
+
+def test_mixed_precision_solve_hands_over_not_spd(qng, oracle):
+    """P = 100, lambda = 0 and a first rotation RZ on an untouched qubit: g_00 = 0 exactly, the first
+    float32 pivot is not positive, the float64 cluster solve takes over and reports NOT_SPD; the
+    next step (lambda = 1e-3) is solved in mixed precision and matches the oracle."""
+    base = _rand_params(3, 99, 91)
+    c = W.Circuit(4, np.concatenate([np.array([[W.RZ, 3, -1, 0]], dtype=np.int32),
+                                     base.circuit.gates + np.array([0, 0, 0, 1], dtype=np.int32) * (base.circuit.gates[:, 3:4] >= 0)]))
+    p = W.Problem("singular_first", c, W.tfim_chain(4), np.concatenate([[0.4], base.theta]))
+    assert p.P == 100
+    ctx = qng.Context(p)
+    ctx.step(ctx.theta0(), 0.1, 0.0)
+    with pytest.raises(qng.QngError) as e:
+        ctx.sync()
+    assert e.value.status == qng.QNG_ERR_NOT_SPD
+    out = ctx.step(ctx.theta0(), 0.1, 1e-3)
+    ctx.sync()
+    ref = oracle.qng_step(W.Problem(p.name, c, p.hamiltonian, p.theta, 0.1, 1e-3))
+    assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[W.C128]
+
+
+@pytest.mark.parametrize("lam", [1e-6, 1e-9])
+def test_solve_ill_conditioned(qng, lam):
+    """Small lambda makes g + lambda I nearly singular (float32 refinement stalls or its pivots
+    fail, and the float64 solve takes over): the step still solves its float64 system."""
+    p = W.config_rand12()
+    ctx = qng.Context(p)
+    out = ctx.step(ctx.theta0(), p.dt, lam)
+    ctx.sync()
+    g = out["g"].cpu().numpy().reshape(p.P, p.P)
+    A = g + lam * np.eye(p.P)
+    x = out["dtheta"].cpu().numpy()
+    b = -p.dt * out["grad"].cpu().numpy()
+    r = A @ x - b
+    # backward error of a float64 Cholesky solve: |r| ~ eps |A| |x|
+    assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(A, 2) * np.linalg.norm(x) + 1e-12 * np.linalg.norm(b)

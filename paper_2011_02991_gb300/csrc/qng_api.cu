@@ -127,6 +127,7 @@ struct qng_ctx {
     int tuned_threads[kMaxQubits + 1];
     int tuned_fwd[kMaxQubits + 1];
     int64_t last_launches = 0;
+    int last_solve = QNG_SOLVE_NONE;  // which solve the last step launched
     // kernel timing (qng_profile)
     bool profiling = false;
     struct Mark { int cls; cudaEvent_t a, b; };
@@ -665,6 +666,10 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
         }
     }
     const int scl = solve_cluster_log2(c->max_P);
+    if (jobs & kJobSolve)
+        c->last_solve = c->bsolve ? QNG_SOLVE_BLOCK
+                      : scl < 0   ? QNG_SOLVE_SINGLE
+                      : c->ir_C > 0 ? QNG_SOLVE_MIXED : QNG_SOLVE_CLUSTER;
     if ((jobs & kJobSolve) && c->bsolve) {
         const int P = c->inst[0].P, nblk = (P + kSolveBlock - 1) / kSolveBlock;
         e = timed(c, 3, [&] {
@@ -1141,6 +1146,20 @@ qng_status qng_profile_read(qng_ctx *c, double *ms, int64_t *launches) {
 qng_status qng_last_launch_count(const qng_ctx *c, int64_t *launches) {
     if (!c || !launches) return QNG_ERR_ARG;
     *launches = c->last_launches;
+    return QNG_OK;
+}
+
+qng_status qng_solve_report(qng_ctx *c, int *path, int32_t *handed_over) {
+    if (!c || !path || !handed_over) return QNG_ERR_ARG;
+    *path = c->last_solve;
+    *handed_over = 0;
+    if (c->last_solve != QNG_SOLVE_MIXED) return QNG_OK;
+    std::vector<int32_t> flag((size_t)c->count);
+    cudaError_t e = cudaMemcpyAsync(flag.data(), c->ws + c->o_irflag, sizeof(int32_t) * flag.size(),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int32_t f : flag) *handed_over += f != 0;
     return QNG_OK;
 }
 

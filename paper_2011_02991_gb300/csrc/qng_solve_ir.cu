@@ -9,10 +9,10 @@
 // which converges to the float64 solution at a rate of about cond(A) times float32 rounding
 // (a few iterations for the metrics of this method, whose condition numbers are in the 10^3 range
 // with lambda = 1e-3). The step stops when the error the last correction leaves, estimated as
-// the correction times its ratio to the previous one, is below 1e-15 of x, or when it stops
-// shrinking. A float32 pivot that is not positive, or a correction still above 1e-10 of x when it
-// stops, marks the instance for the float64 cluster solve (k_solve), which is launched right after
-// and stands down for the instances this kernel finished.
+// the correction times its ratio to the previous one, is below 1e-13 of x, or when it stops
+// shrinking. A float32 pivot that is not positive, or an estimated error still above 1e-10 of x
+// when it stops, marks the instance for the float64 cluster solve (k_solve), which is launched
+// right after and stands down for the instances this kernel finished.
 //
 // One cluster of C CTAs (512 threads) per instance. CTA 0 holds the float32 matrix (full square,
 // row stride P + 1) and does the factorisation and the triangular solves; CTAs 1..C-1 hold the
@@ -36,8 +36,12 @@ constexpr int kIrMaxIter = 12; // refinement steps at most
 struct IrGeom {
     int P, C, R;     // rows of A per CTA of rank >= 1
     int ld;          // row stride of the float32 matrix
+    int Pp;          // P rounded up to 16 (row length of the transposed panel)
+    size_t o_xt, o_di, o_y, o_x;  // float offsets in CTA 0's shared memory
     size_t smem;
 };
+
+__host__ __device__ inline size_t up4(size_t x) { return (x + 3) & ~(size_t)3; }
 
 __host__ __device__ inline IrGeom ir_geom(int P, int C) {
     IrGeom g;
@@ -45,21 +49,74 @@ __host__ __device__ inline IrGeom ir_geom(int P, int C) {
     g.C = C;
     g.R = (P + C - 2) / (C - 1);
     g.ld = P + 1;
-    const size_t cta0 = sizeof(float) * ((size_t)P * g.ld + (size_t)((P + kIb - 1) / kIb) * kIb * kIb + P) +
-                        sizeof(double) * 3 * (size_t)P;
+    g.Pp = (P + kIb - 1) / kIb * kIb;
+    const int nblk = (P + kIb - 1) / kIb;
+    g.o_xt = up4((size_t)P * g.ld);                  // Lm [P][ld]
+    g.o_di = g.o_xt + (size_t)kIb * g.Pp;             // Xt [16][Pp], 16-byte aligned rows
+    g.o_y = g.o_di + (size_t)nblk * kIb * kIb;        // Di [nblk][16][16]
+    g.o_x = up4(g.o_y + (size_t)P);                   // yv [P]; then float64 x, r
+    const size_t cta0 = sizeof(float) * g.o_x + sizeof(double) * 2 * (size_t)P;
     const size_t other = sizeof(double) * ((size_t)g.R * P + P);
     g.smem = cta0 > other ? cta0 : other;
     return g;
+}
+
+// One warp: the diagonal block at (k0, k0) of the float32 matrix (row stride ld), already updated
+// by every earlier panel, with nb <= 16 real rows (the rest padded with the identity) -> its
+// Cholesky factor L_K in place and L_K^-1 in D (16 x 16, zero past nb). Lane r holds row r; a
+// column takes one rsqrt, and 1/L_cc = rsqrt(d) also serves the inverse. False if a pivot is not
+// positive.
+__device__ __noinline__ bool chol_diag16(float *Lm, int ld, int k0, int nb, float *D, int lane) {
+    float row[kIb], rdiag[kIb];
+#pragma unroll
+    for (int c = 0; c < kIb; ++c)
+        row[c] = (lane < nb) ? (c <= lane ? Lm[(size_t)(k0 + lane) * ld + k0 + c] : 0.0f) : (lane == c ? 1.0f : 0.0f);
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < kIb; ++c) {
+        const float d = __shfl_sync(0xffffffffu, row[c], c);
+        bad = bad || !(d > 0.0f);
+        const float ri = rsqrtf(d);
+        rdiag[c] = ri;
+        const float lc = (lane == c) ? d * ri : row[c] * ri;
+        if (lane >= c) row[c] = lc;
+#pragma unroll
+        for (int j = c + 1; j < kIb; ++j) {
+            const float lj = __shfl_sync(0xffffffffu, lc, j);  // L[j][c]
+            if (lane >= j) row[j] = fmaf(-lc, lj, row[j]);
+        }
+    }
+    if (lane < nb) {
+#pragma unroll
+        for (int c = 0; c < kIb; ++c)
+            if (c <= lane) Lm[(size_t)(k0 + lane) * ld + k0 + c] = row[c];
+    }
+    // lane c (mod 16) forms column c of L_K^-1 by forward substitution, rows taken from the warp
+    const int c = lane & (kIb - 1);
+    float xc[kIb];
+#pragma unroll
+    for (int r = 0; r < kIb; ++r) {
+        float sum = (r == c) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int m = 0; m < r; ++m) sum = fmaf(-__shfl_sync(0xffffffffu, row[m], r), xc[m], sum);
+        xc[r] = (r >= c) ? sum * rdiag[r] : 0.0f;
+    }
+    if (lane < kIb) {
+#pragma unroll
+        for (int r = 0; r < kIb; ++r) D[r * kIb + c] = (r < nb && c < nb) ? xc[r] : 0.0f;
+    }
+    return !bad;
 }
 
 }  // namespace
 
 size_t solve_ir_smem_bytes(int P, int C) { return ir_geom(P, C).smem + 64; }
 
-__global__ void __launch_bounds__(512) k_solve_ir(Work w, LaunchArgs a) {
+__global__ void __launch_bounds__(512, 1) k_solve_ir(Work w, LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_fail, s_done;
-    __shared__ double s_red[2][16];
+    __shared__ double s_est;
+    __shared__ float s_red[2][16];
     const int C = (int)cg::this_cluster().num_blocks();
     const int b = blockIdx.x / C;
     const int rank = (int)cg::this_cluster().block_rank();
@@ -76,9 +133,10 @@ __global__ void __launch_bounds__(512) k_solve_ir(Work w, LaunchArgs a) {
 
     // CTA 0: float32 matrix, inverse diagonal blocks, float64 x, r and the float32 work vector
     float *Lm = reinterpret_cast<float *>(smem);                       // [P][ld]
-    float *Di = Lm + (size_t)P * G.ld;                                 // [nblk][16][16]
-    float *yv = Di + (size_t)nblk * kIb * kIb;                         // [P]
-    double *xv = reinterpret_cast<double *>(yv + P + (P & 1));         // [P] (8-byte aligned)
+    float *Xt = Lm + G.o_xt;                                           // [16][Pp]: the panel, transposed
+    float *Di = Lm + G.o_di;                                           // [nblk][16][16]
+    float *yv = Lm + G.o_y;                                            // [P]
+    double *xv = reinterpret_cast<double *>(Lm + G.o_x);               // [P]
     double *rv = xv + P;                                               // [P]
     // CTAs >= 1: float64 rows [r0, r1) of A and a copy of x
     double *Arow = reinterpret_cast<double *>(smem);                   // [R][P]
@@ -106,123 +164,110 @@ __global__ void __launch_bounds__(512) k_solve_ir(Work w, LaunchArgs a) {
     }
     cl.sync();
 
-    // (B) CTA 0: float32 Cholesky in place (lower triangle), blocked by 16: a warp factors the
-    // diagonal block in registers, one thread per row solves the panel, and the trailing lower
-    // triangle takes a rank-16 update in 4 x 4 register tiles. Three barriers per block.
+    // (B) CTA 0: float32 Cholesky in place (lower triangle), blocked by 16 with look-ahead. Warp 0
+    // factors diagonal block K + 1 in registers (and inverts it) while the other warps apply the
+    // rank-16 update of panel K to the rest of the trailing triangle; the panel itself is
+    // X = A_panel D_K^-T, one independent 16-term dot product per entry. Two barriers per block.
     if (rank == 0) {
-        __shared__ float s_dinv[kIb];
-        for (int kb = 0; kb < nblk; ++kb) {
-            const int k0 = kb * kIb, nb = min(kIb, P - k0), k1 = k0 + nb;
-            if (wid == 0) {
-                // lane r < nb holds row r of the diagonal block
-                float row[kIb];
-#pragma unroll
-                for (int c = 0; c < kIb; ++c)
-                    row[c] = (lane < nb && c <= lane) ? Lm[(size_t)(k0 + lane) * G.ld + k0 + c] : 0.0f;
-                bool bad = false;
-#pragma unroll
-                for (int c = 0; c < kIb; ++c) {
-                    if (c < nb && !bad) {
-                        const float d = __shfl_sync(0xffffffffu, row[c], c);
-                        if (!(d > 0.0f)) {
-                            bad = true;
-                        } else {
-                            const float ri = rsqrtf(d);
-                            if (lane == c) row[c] = d * ri;
-                            else if (lane > c) row[c] *= ri;
-                            const float lc = row[c];
-#pragma unroll
-                            for (int j = c + 1; j < kIb; ++j) {
-                                const float lj = __shfl_sync(0xffffffffu, lc, j);  // L[j][c]
-                                if (lane >= j) row[j] = fmaf(-lc, lj, row[j]);
-                            }
-                        }
-                    }
-                }
-                if (lane < nb)
-#pragma unroll
-                    for (int c = 0; c < kIb; ++c)
-                        if (c <= lane) Lm[(size_t)(k0 + lane) * G.ld + k0 + c] = row[c];
-                if (lane < nb) s_dinv[lane] = 1.0f / row[lane];
-                if (bad && lane == 0) s_fail = 1;
-            }
-            __syncthreads();
-            if (s_fail) break;
-            // panel: rows i >= k1, X[i][c] = (A[i][c] - sum_{m<c} X[i][m] L[c][m]) / L[c][c]
-            for (int i = k1 + tid; i < P; i += nt) {
-                float *row = Lm + (size_t)i * G.ld + k0;
+        // kb = -1 only factors block 0; block kb is full whenever block kb + 1 exists
+        for (int kb = -1; !s_fail; ++kb) {
+            const int k0 = kb * kIb, nb = kIb, k1 = k0 + nb;
+            if (k1 >= P) break;  // no block kb + 1
+            // panel: X[i][c] = sum_{m <= c} A[i][m] Dinv[c][m], also into Xt (zero past P)
+            const float *D = Di + (size_t)max(kb, 0) * kIb * kIb;
+            for (int i = k1 + tid; kb >= 0 && i < G.Pp; i += nt) {
                 float x[kIb];
+                if (i < P) {
+                    float av[kIb];
+                    float *rowp = Lm + (size_t)i * G.ld + k0;
 #pragma unroll
-                for (int c = 0; c < kIb; ++c) {
-                    if (c < nb) {
-                        float v = row[c];
+                    for (int mm = 0; mm < kIb; ++mm) av[mm] = (mm < nb) ? rowp[mm] : 0.0f;
 #pragma unroll
-                        for (int m = 0; m < c; ++m) v = fmaf(-x[m], Lm[(size_t)(k0 + c) * G.ld + k0 + m], v);
-                        x[c] = v * s_dinv[c];
-                        row[c] = x[c];
+                    for (int cc = 0; cc < kIb; ++cc) {
+                        float v = 0.0f;
+#pragma unroll
+                        for (int mm = 0; mm <= cc; ++mm) v = fmaf(av[mm], D[cc * kIb + mm], v);
+                        x[cc] = v;
                     }
+#pragma unroll
+                    for (int cc = 0; cc < kIb; ++cc)
+                        if (cc < nb) rowp[cc] = x[cc];
+                } else {
+#pragma unroll
+                    for (int cc = 0; cc < kIb; ++cc) x[cc] = 0.0f;
                 }
+#pragma unroll
+                for (int cc = 0; cc < kIb; ++cc) Xt[(size_t)cc * G.Pp + i] = (cc < nb) ? x[cc] : 0.0f;
             }
             __syncthreads();
-            // trailing update: A[i][j] -= sum_c X[i][c] X[j][c] for k1 <= j <= i < P, 4 x 4 tiles of
-            // the lower triangle (tile (ti, tj), tj <= ti), decoded from a linear index
-            const int m = P - k1, mt = (m + 3) >> 2, ntile = mt * (mt + 1) / 2;
-            for (int t = tid; t < ntile; t += nt) {
-                int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-                while (ti * (ti + 1) / 2 > t) --ti;
-                while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-                const int tj = t - ti * (ti + 1) / 2;
-                const int i0 = k1 + 4 * ti, j0 = k1 + 4 * tj;
-                float acc[4][4];
+            // look-ahead: warp 0 updates and factors the next diagonal block; the other warps take
+            // the rest of the trailing triangle in 4 x 4 tiles (those of the next block skipped)
+            const int nb2 = min(kIb, P - k1);
+            const int mrem = P - k1, mt = (mrem + 3) >> 2, ntile = mt * (mt + 1) / 2;
+            const int t2 = (nb2 + 3) >> 2, skip = t2 * (t2 + 1) / 2;  // tiles inside the next block
+            if (wid == 0) {
+                // A[r][j] -= sum_c X[r][c] X[j][c] for r, j in block kb + 1, j <= r: lane (r, half)
+                // takes j in [8 half, 8 half + 8), eight independent sums (Xt is zero past P)
+                const int r = lane & (kIb - 1), jh = (lane >> 4) * 8;
+                if (kb >= 0 && r < nb2 && jh <= r) {
+                    float acc[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                    for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
-                for (int c = 0; c < nb; ++c) {
-                    float xa[4], xb[4];
+                    for (int cc = 0; cc < kIb; ++cc) {
+                        const float *xrow = Xt + (size_t)cc * G.Pp + k1;
+                        const float xr = xrow[r];
+                        const float4 u = *reinterpret_cast<const float4 *>(xrow + jh);
+                        const float4 v = *reinterpret_cast<const float4 *>(xrow + jh + 4);
+                        acc[0] = fmaf(xr, u.x, acc[0]);
+                        acc[1] = fmaf(xr, u.y, acc[1]);
+                        acc[2] = fmaf(xr, u.z, acc[2]);
+                        acc[3] = fmaf(xr, u.w, acc[3]);
+                        acc[4] = fmaf(xr, v.x, acc[4]);
+                        acc[5] = fmaf(xr, v.y, acc[5]);
+                        acc[6] = fmaf(xr, v.z, acc[6]);
+                        acc[7] = fmaf(xr, v.w, acc[7]);
+                    }
+                    float *arow = Lm + (size_t)(k1 + r) * G.ld + k1 + jh;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        xa[u] = (i0 + u < P) ? Lm[(size_t)(i0 + u) * G.ld + k0 + c] : 0.0f;
-                        xb[u] = (j0 + u < P) ? Lm[(size_t)(j0 + u) * G.ld + k0 + c] : 0.0f;
+                    for (int q = 0; q < 8; ++q)
+                        if (jh + q <= r) arow[q] -= acc[q];
+                }
+                __syncwarp();
+                const bool ok = chol_diag16(Lm, G.ld, k1, min(kIb, P - k1), Di + (size_t)(kb + 1) * kIb * kIb, lane);
+                if (!ok && lane == 0) s_fail = 1;
+            } else if (kb >= 0) {
+                for (int t = skip + tid - 32; t < ntile; t += nt - 32) {
+                    int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+                    while (ti * (ti + 1) / 2 > t) --ti;
+                    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+                    const int tj = t - ti * (ti + 1) / 2;
+                    const int i0 = k1 + 4 * ti, j0 = k1 + 4 * tj;
+                    float acc[4][4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+#pragma unroll 4
+                    for (int cc = 0; cc < kIb; ++cc) {
+                        const float4 xa = *reinterpret_cast<const float4 *>(Xt + (size_t)cc * G.Pp + i0);
+                        const float4 xb = *reinterpret_cast<const float4 *>(Xt + (size_t)cc * G.Pp + j0);
+                        const float av[4] = {xa.x, xa.y, xa.z, xa.w}, bv[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xa[u], xb[v], acc[u][v]);
+                        for (int v = 0; v < 4; ++v) {
+                            const int i = i0 + u, j = j0 + v;
+                            if (i < P && j <= i) Lm[(size_t)i * G.ld + j] -= acc[u][v];
+                        }
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int i = i0 + u, j = j0 + v;
-                        if (i < P && j <= i) Lm[(size_t)i * G.ld + j] -= acc[u][v];
-                    }
             }
             __syncthreads();
-        }
-        // inverses of the 16 x 16 diagonal blocks of L (a warp per block, lane c holds column c)
-        if (!s_fail) {
-            for (int kb = wid; kb < nblk; kb += nwarp) {
-                const int k0 = kb * kIb, nb = min(kIb, P - k0);
-                float *D = Di + (size_t)kb * kIb * kIb;  // D[r][c], lower
-                const int c = lane & (kIb - 1);
-                float xcol[kIb];
-#pragma unroll
-                for (int r = 0; r < kIb; ++r) xcol[r] = 0.0f;
-                // column c of D^-1: forward substitution of e_c (lanes >= 16 duplicate 0..15)
-#pragma unroll
-                for (int r = 0; r < kIb; ++r) {
-                    if (r < nb) {
-                        float s = (r == c) ? 1.0f : 0.0f;
-#pragma unroll
-                        for (int m = 0; m < r; ++m) s = fmaf(-Lm[(size_t)(k0 + r) * G.ld + k0 + m], xcol[m], s);
-                        xcol[r] = s / Lm[(size_t)(k0 + r) * G.ld + k0 + r];
-                    }
-                }
-                if (lane < kIb)
-#pragma unroll
-                    for (int r = 0; r < kIb; ++r) D[r * kIb + c] = (r < nb && c < nb) ? xcol[r] : 0.0f;
-            }
         }
         for (int i = tid; i < P; i += nt) { xv[i] = 0.0; rv[i] = -a.dt * gr[i]; }
         __syncthreads();
@@ -235,7 +280,7 @@ __global__ void __launch_bounds__(512) k_solve_ir(Work w, LaunchArgs a) {
 
     // (C) refinement: CTA 0 solves L L^T d = r in float32 and updates x; CTAs >= 1 take r = b - A x
     double dn_prev = 0.0;
-    double dn = 0.0, xn = 0.0;
+    double en = 0.0, xn = 0.0;
     for (int it = 0; !fallback && it < kIrMaxIter; ++it) {
         if (rank == 0) {
             for (int i = tid; i < P; i += nt) yv[i] = (float)rv[i];
@@ -244,22 +289,26 @@ __global__ void __launch_bounds__(512) k_solve_ir(Work w, LaunchArgs a) {
             // forward L y = r by blocks: y_K = D_K^-1 y_K (16 threads), then every row below at once
             for (int kb = 0; kb < nblk; ++kb) {
                 const int k0 = kb * kIb, nb = min(kIb, P - k0), k1 = k0 + nb;
-                if (tid < nb) {
+                if (tid < nb) {  // row tid of D: zero past the diagonal, so a fixed 16 terms
                     const float *D = Di + (size_t)kb * kIb * kIb + tid * kIb;
-                    float t = 0.0f;
-                    for (int m = 0; m <= tid; ++m) t = fmaf(D[m], yv[k0 + m], t);
-                    s_blk[tid] = t;
+                    float t0 = 0.0f, t1 = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < kIb; m += 2) {
+                        t0 = fmaf(D[m], (m < nb) ? yv[k0 + m] : 0.0f, t0);
+                        t1 = fmaf(D[m + 1], (m + 1 < nb) ? yv[k0 + m + 1] : 0.0f, t1);
+                    }
+                    s_blk[tid] = t0 + t1;
                 }
                 __syncthreads();
                 if (tid < nb) yv[k0 + tid] = s_blk[tid];
-                for (int i = k1 + tid; i < P; i += nt) {
+                for (int i = k1 + tid; i < P; i += nt) {  // rows below K exist only when K is full
                     const float *row = Lm + (size_t)i * G.ld + k0;
                     float s0 = yv[i], s1 = 0.0f;
-                    for (int m = 0; m + 1 < nb; m += 2) {
+#pragma unroll
+                    for (int m = 0; m < kIb; m += 2) {
                         s0 = fmaf(-row[m], s_blk[m], s0);
                         s1 = fmaf(-row[m + 1], s_blk[m + 1], s1);
                     }
-                    if (nb & 1) s0 = fmaf(-row[nb - 1], s_blk[nb - 1], s0);
                     yv[i] = s0 + s1;
                 }
                 __syncthreads();
@@ -276,45 +325,52 @@ __global__ void __launch_bounds__(512) k_solve_ir(Work w, LaunchArgs a) {
                     if (lane == 0) s_blk[wid] = yv[k0 + wid] - sacc;
                 }
                 __syncthreads();
-                if (tid < nb) {
+                if (tid < nb) {  // column tid of D: zero above the diagonal and past nb
                     const float *D = Di + (size_t)kb * kIb * kIb;
-                    float v = 0.0f;
-                    for (int m = tid; m < nb; ++m) v = fmaf(D[m * kIb + tid], s_blk[m], v);
-                    yv[k0 + tid] = v;
+                    float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < kIb; m += 2) {
+                        v0 = fmaf(D[m * kIb + tid], (m < nb) ? s_blk[m] : 0.0f, v0);
+                        v1 = fmaf(D[(m + 1) * kIb + tid], (m + 1 < nb) ? s_blk[m + 1] : 0.0f, v1);
+                    }
+                    yv[k0 + tid] = v0 + v1;
                 }
                 __syncthreads();
             }
-            // x += d; max |d| and max |x|
-            double md = 0.0, mx = 0.0;
+            // x += d; max |d| and max |x| (float32 magnitudes decide as well as float64 ones)
+            float md = 0.0f, mx = 0.0f;
             for (int i = tid; i < P; i += nt) {
-                const double d = (double)yv[i];
-                const double x = xv[i] + d;
+                const float d = yv[i];
+                const double x = xv[i] + (double)d;
                 xv[i] = x;
-                md = fmax(md, fabs(d));
-                mx = fmax(mx, fabs(x));
+                md = fmaxf(md, fabsf(d));
+                mx = fmaxf(mx, fabsf((float)x));
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
-                mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             }
             if (lane == 0) { s_red[0][wid] = md; s_red[1][wid] = mx; }
             __syncthreads();
             if (tid == 0) {
-                double a0 = 0.0, a1 = 0.0;
-                for (int q = 0; q < nwarp; ++q) { a0 = fmax(a0, s_red[0][q]); a1 = fmax(a1, s_red[1][q]); }
+                float a0 = 0.0f, a1 = 0.0f;
+                for (int q = 0; q < nwarp; ++q) { a0 = fmaxf(a0, s_red[0][q]); a1 = fmaxf(a1, s_red[1][q]); }
                 s_red[0][0] = a0;
                 s_red[1][0] = a1;
+                // error left after this correction: itself, or itself times its ratio to the last
+                const double a0d = a0;
+                s_est = it == 0 ? a0d : fmin(a0d, a0d * a0d / dn_prev);
                 // done when the correction is negligible, or when the error it leaves (about the
                 // correction times its ratio to the previous one) is, or when it stops shrinking
-                const bool small = a0 <= 1e-14 * a1 || (it >= 2 && a0 * a0 <= 1e-15 * a1 * dn_prev);
+                const bool small = (double)a0 <= 1e-14 * a1 || (it >= 2 && (double)a0 * a0 <= 1e-13 * a1 * dn_prev);
                 const bool stalled = it >= 2 && a0 > 0.5 * dn_prev;
                 s_done = (small || stalled || it + 1 == kIrMaxIter) ? 1 : 0;
             }
             __syncthreads();
-            dn = s_red[0][0];
+            dn_prev = s_red[0][0];
+            en = s_est;
             xn = s_red[1][0];
-            dn_prev = dn;
             // x and the decision to every CTA
             for (int q = 1; q < C; ++q) {
                 double *xr = cl.map_shared_rank(xc, q);
@@ -340,7 +396,7 @@ __global__ void __launch_bounds__(512) k_solve_ir(Work w, LaunchArgs a) {
     }
     // outputs, or the float64 solve's turn
     if (rank == 0) {
-        if (!fallback && !(dn <= 1e-10 * xn)) fallback = true;
+        if (!fallback && !(en <= 1e-10 * xn)) fallback = true;
         if (tid == 0) w.irflag[b] = fallback ? 1 : 0;
         if (!fallback)
             for (int i = tid; i < P; i += nt) a.dtheta_out[in.param_off + i] = xv[i];

@@ -70,6 +70,7 @@ SYMBOLS = {
     "qng_sync": [_vp],
     "qng_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "qng_last_launch_count": [_vp, _i64p],
+    "qng_solve_report": [_vp, _i32p, _i32p],
     "qng_profile": [_vp, ctypes.c_int],
     "qng_set_path": [_vp, ctypes.c_int],
     "qng_stream_traffic": [_vp, _i64p, _i64p, _i64p],
@@ -376,6 +377,14 @@ class Context:
         v = ctypes.c_int64()
         _chk(load().qng_last_launch_count(self._h, ctypes.byref(v)), "qng_last_launch_count")
         return int(v.value)
+
+    SOLVE_PATHS = {0: "none", 1: "single", 2: "cluster", 3: "mixed", 4: "block"}
+
+    def solve_report(self) -> tuple[str, int]:
+        """(solve the last step ran, instances the mixed-precision solve handed to float64)."""
+        path, handed = ctypes.c_int32(), ctypes.c_int32()
+        _chk(load().qng_solve_report(self._h, ctypes.byref(path), ctypes.byref(handed)), "qng_solve_report")
+        return self.SOLVE_PATHS[int(path.value)], int(handed.value)
 
     def close(self):
         if self._h:

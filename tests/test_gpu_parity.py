@@ -565,9 +565,38 @@ def test_mixed_precision_solve_hands_over_not_spd(qng, oracle):
     with pytest.raises(qng.QngError) as e:
         ctx.sync()
     assert e.value.status == qng.QNG_ERR_NOT_SPD
+    assert ctx.solve_report() == ("mixed", 1)
     out = ctx.step(ctx.theta0(), 0.1, 1e-3)
     ctx.sync()
+    assert ctx.solve_report() == ("mixed", 0)
     ref = oracle.qng_step(W.Problem(p.name, c, p.hamiltonian, p.theta, 0.1, 1e-3))
+    assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[W.C128]
+
+
+@pytest.mark.parametrize("n,P,path", [(5, 40, "single"), (6, 120, "mixed"), (5, 222, "mixed"), (5, 223, "cluster"),
+                                      (7, 340, "block")])
+def test_solve_selection(qng, oracle, n, P, path):
+    """Each solve the step can take matches the oracle's float64 step. The float32-factor solve
+    takes every P from 48 up to the largest factor CTA 0's shared memory holds (222) and, at
+    lambda = 1e-3 (condition numbers ~10^3), finishes without handing over to the float64 solve."""
+    p = _rand_params(n, P, 5000 + P)
+    ref = oracle.qng_step(p)
+    ctx = qng.Context(p, precision=W.C128)
+    out = ctx.step(ctx.theta0(), p.dt, p.lam)
+    ctx.sync()
+    assert ctx.solve_report() == (path, 0)
+    for key in ("g", "grad", "dtheta"):
+        assert rel(out[key].cpu(), ref[key]) <= TOL[W.C128], key
+
+
+def test_bench_workload_solves_in_mixed_precision(qng, oracle):
+    """12 qubits, P = 192 (the timed workload): the float32-factor solve finishes it alone."""
+    p = W.config_rand12()
+    ctx = qng.Context(p)
+    out = ctx.step(ctx.theta0(), p.dt, p.lam)
+    ctx.sync()
+    assert ctx.solve_report() == ("mixed", 0)
+    ref = oracle.qng_step(p)
     assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[W.C128]
 
 

@@ -75,6 +75,10 @@ qng_status validate(int n, const qng_gate *gates, int n_gates, const uint64_t *m
 
 }  // namespace
 
+constexpr int kPipeMax = 8;      // chunks of a pipelined sweep at most
+constexpr int kPipeMinP = 64;    // automatic pipelining from this many parameters
+constexpr int kPipeDefault = 3;  // chunks when automatic
+
 struct qng_ctx {
     int precision = QNG_C128;
     int count = 0;
@@ -126,8 +130,17 @@ struct qng_ctx {
     int tuned_cl[kMaxQubits + 1];
     int tuned_threads[kMaxQubits + 1];
     int tuned_fwd[kMaxQubits + 1];
+    int tuned_fcl[kMaxQubits + 1];  // cluster size (log2) of the checkpoint sweep (-1: the column kernel's)
     int64_t last_launches = 0;
     int last_solve = QNG_SOLVE_NONE;  // which solve the last step launched
+    // pipelined sweep (one on-chip instance): the checkpoint sweep in chunks on a high-priority
+    // stream; the columns each chunk makes ready run on a stream of their own meanwhile
+    int pipe_req = 0;  // qng_set_pipeline: 0 automatic, 1 off, 2..kPipeMax chunks
+    bool pipe_ready = false;
+    cudaStream_t pipe_fwd = nullptr;
+    cudaStream_t pipe_col[kPipeMax] = {};
+    cudaEvent_t pipe_ev0 = nullptr;
+    cudaEvent_t pipe_evf[kPipeMax] = {}, pipe_evc[kPipeMax] = {};
     // kernel timing (qng_profile)
     bool profiling = false;
     struct Mark { int cls; cudaEvent_t a, b; };
@@ -137,11 +150,18 @@ struct qng_ctx {
     int64_t prof_n[QNG_KERNEL_CLASSES] = {0, 0, 0, 0};
 
     qng_ctx() {
-        for (int k = 0; k <= kMaxQubits; ++k) { tuned_cl[k] = -1; tuned_threads[k] = 0; tuned_fwd[k] = 0; }
+        for (int k = 0; k <= kMaxQubits; ++k) { tuned_cl[k] = -1; tuned_threads[k] = 0; tuned_fwd[k] = 0; tuned_fcl[k] = -1; }
     }
     ~qng_ctx() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
+        if (pipe_fwd) cudaStreamDestroy(pipe_fwd);
+        for (int k = 0; k < kPipeMax; ++k) {
+            if (pipe_col[k]) cudaStreamDestroy(pipe_col[k]);
+            if (pipe_evf[k]) cudaEventDestroy(pipe_evf[k]);
+            if (pipe_evc[k]) cudaEventDestroy(pipe_evc[k]);
+        }
+        if (pipe_ev0) cudaEventDestroy(pipe_ev0);
         for (auto &m : marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
         for (auto e : spare) cudaEventDestroy(e);
     }
@@ -197,6 +217,24 @@ int default_cl(int n, int precision) {
 // amplitudes per thread (64..512 threads) hide more float64 latency than the column kernel's shape.
 int default_fwd_threads(int nl) {
     return std::max(64, std::min(512, (1 << nl) / 2));
+}
+
+// Cluster size (log2) of the checkpoint sweep for n qubits. The sweep is one sequential chain per
+// instance, so a single instance takes twice the column kernel's CTAs (up to 16) while each keeps
+// at least 256 amplitudes (measured at 12 qubits, c128: sweep 0.257 -> 0.206 ms); batches keep
+// the column kernel's size (their sweeps already run side by side).
+int fwd_cluster(const qng_ctx *c, int n, int cl) {
+    int f = cl;
+    if (c->tuned_fcl[n] >= 0) f = c->tuned_fcl[n];
+    else if (c->count == 1 && cl + 1 <= kMaxFwdClusterLog2 && n - (cl + 1) >= 8) f = cl + 1;
+    return std::max(0, std::min(f, std::min(kMaxFwdClusterLog2, n - 1)));
+}
+
+// CTA size of the checkpoint sweep: as set, else half the column kernel's amplitudes per CTA but
+// no more threads than the sweep's own amplitudes per CTA (at least 64).
+int fwd_threads_for(const qng_ctx *c, int n, int cl, int fcl) {
+    if (c->tuned_fwd[n] > 0) return c->tuned_fwd[n];
+    return std::min(default_fwd_threads(n - cl), std::max(64, 1 << std::min(n - fcl, 20)));
 }
 
 int default_threads(int nl) {
@@ -386,8 +424,8 @@ qng_status plan(qng_ctx *c) {
     }
     if (c->streaming) return plan_streaming(c, scale_n);
 
-    // groups: instances sharing (cluster size, column CTA size, forward CTA size)
-    std::vector<std::array<int, 3>> shape(c->count);
+    // groups: instances sharing (cluster size, column CTA size, sweep cluster size, sweep CTA size)
+    std::vector<std::array<int, 4>> shape(c->count);
     for (int b = 0; b < c->count; ++b) {
         const int n = c->inst[b].n;
         int cl = default_cl(n, c->precision);
@@ -397,19 +435,20 @@ qng_status plan(qng_ctx *c) {
         int th = default_threads(n - cl);
         if (c->tuned_threads[n] > 0) th = c->tuned_threads[n];
         if (c->tune_threads > 0 && n >= c->tune_min_qubits) th = c->tune_threads;
-        int fth = default_fwd_threads(n - cl);
-        if (c->tuned_fwd[n] > 0) fth = c->tuned_fwd[n];
-        shape[b] = {cl, th, fth};
+        const int fcl = fwd_cluster(c, n, cl);
+        const int fth = fwd_threads_for(c, n, cl, fcl);
+        shape[b] = {cl, th, fcl, fth};
         c->t_inst[b].cl = cl;
     }
-    std::vector<std::array<int, 3>> keys(shape);
+    std::vector<std::array<int, 4>> keys(shape);
     std::sort(keys.begin(), keys.end());
     keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
     for (const auto &key : keys) {
         Group g;
         g.cl = key[0];
         g.threads = key[1];
-        g.fwd_threads = key[2];
+        g.fwd_cl = key[2];
+        g.fwd_threads = key[3];
         g.first_inst = (int)c->t_group_inst.size();
         std::vector<DevWork> items;
         for (int b = 0; b < c->count; ++b) {
@@ -437,7 +476,7 @@ qng_status plan(qng_ctx *c) {
         const size_t Nl = size_t(1) << (g.max_n - g.cl);
         const int nw = g.threads / 32;
         const size_t state = Nl * ab * (g.cl ? 3 : 1);
-        g.smem_fwd = state + 64 * sizeof(double);
+        g.smem_fwd = (size_t(1) << (g.max_n - g.fwd_cl)) * ab * (g.fwd_cl ? 3 : 1) + 64 * sizeof(double);
         g.smem_col = state + (size_t)(g.max_P + 1) * nw * sizeof(double) + (size_t)(g.max_P + 1) * sizeof(double);
         g.smem_col_im = g.smem_col + (size_t)(g.max_P + 1) * nw * sizeof(double);
         if (g.smem_col > kMaxSmem || g.smem_fwd > kMaxSmem) return QNG_ERR_UNSUPPORTED;
@@ -551,6 +590,21 @@ qng_status upload(qng_ctx *c) {
     if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
     if (c->bsolve && (e = prepare_sblock(c->inst[0].P, c->bs_C)) != cudaSuccess) return cuda_status(e);
     if (c->ir_C > 0 && (e = prepare_solve_ir(c->max_P, c->ir_C)) != cudaSuccess) return cuda_status(e);
+    // single instance: streams and events of the pipelined sweep, made here so that no stream is
+    // created inside a graph capture
+    if (c->count == 1 && !c->pipe_ready) {
+        int lo = 0, hi = 0;
+        if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaStreamCreateWithPriority(&c->pipe_fwd, cudaStreamNonBlocking, hi)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaEventCreateWithFlags(&c->pipe_ev0, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+        for (int k = 0; k < kPipeMax; ++k) {
+            if ((e = cudaStreamCreateWithPriority(&c->pipe_col[k], cudaStreamNonBlocking, lo)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&c->pipe_evf[k], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&c->pipe_evc[k], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_status(e);
+        }
+        c->pipe_ready = true;
+    }
     // batched contexts: persistent column launches fed by a device work counter per group
     for (size_t k = 0; k < c->groups.size(); ++k) {
         Group &g = c->groups[k];
@@ -565,17 +619,57 @@ qng_status upload(qng_ctx *c) {
     return QNG_OK;
 }
 
-// Record events around a launch when profiling (class cls), then launch.
-template <class F> cudaError_t timed(qng_ctx *c, int cls, F &&launch) {
+// Record events around a launch when profiling (class cls), on the stream it is launched on.
+template <class F> cudaError_t timed_on(qng_ctx *c, int cls, cudaStream_t st, F &&launch) {
     if (!c->profiling) return launch();
     cudaEvent_t a = c->take_event(), b = c->take_event();
     if (!a || !b) return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaEventRecord(a, c->stream);
+    cudaError_t e = cudaEventRecord(a, st);
     if (e == cudaSuccess) e = launch();
-    if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
     if (e != cudaSuccess) { c->spare.push_back(a); c->spare.push_back(b); return e; }
     c->marks.push_back({cls, a, b});
     return cudaSuccess;
+}
+template <class F> cudaError_t timed(qng_ctx *c, int cls, F &&launch) { return timed_on(c, cls, c->stream, launch); }
+
+// Chunks of the pipelined sweep for this call (0: one sweep, then one column launch).
+int pipe_chunks(const qng_ctx *c) {
+    if (!c->pipe_ready || c->streaming || c->count != 1 || c->groups.size() != 1) return 0;
+    const int P = c->inst[0].P;
+    // automatic: only for circuits with generalised rotations (measured faster there; with plain
+    // rotations the column phase ends on the latency of its longest items, which cannot start
+    // before the sweep has ended, and chunking only adds launches)
+    const bool auto_on = P >= kPipeMinP && c->groups[0].general;
+    int S = c->pipe_req == 0 ? (auto_on ? kPipeDefault : 0) : (c->pipe_req == 1 ? 0 : c->pipe_req);
+    S = std::min(S, P / 2);
+    return S >= 2 ? S : 0;
+}
+
+// Work-list ranges of the columns each chunk of the sweep makes ready. Chunk s covers parameters
+// [K_s, K_s+1) and writes checkpoints up to K_s+1; column j reads checkpoints 0..j, so chunk 0
+// readies columns 0..K_1 and chunk s columns K_s + 1..K_s+1 (the last chunk also the gradient
+// column, P, which needs eta). False if a chunk's items are not contiguous in the list.
+bool pipe_ranges(const qng_ctx *c, const Group &g, int wm, int wg, int S, const std::vector<int> &K,
+                 std::vector<std::array<int, 2>> &rng) {
+    const int first = wm && wg ? g.first_work : (wm ? g.first_met : g.first_grad);
+    const int num = wm && wg ? g.num_work : (wm ? g.num_met : g.num_grad);
+    rng.assign(S, {INT32_MAX, -1});
+    std::vector<int> cnt(S, 0);
+    for (int t = first; t < first + num; ++t) {
+        const int j = c->t_work[t].col;
+        int s = 0;
+        while (s + 1 < S && j > K[s + 1]) ++s;
+        rng[s][0] = std::min(rng[s][0], t);
+        rng[s][1] = std::max(rng[s][1], t);
+        ++cnt[s];
+    }
+    for (int s = 0; s < S; ++s) {
+        if (cnt[s] == 0) { rng[s] = {first, 0}; continue; }
+        if (rng[s][1] - rng[s][0] + 1 != cnt[s]) return false;
+        rng[s][1] = cnt[s];  // (first item, count)
+    }
+    return true;
 }
 
 // The streaming schedule's launches for the requested jobs.
@@ -646,20 +740,55 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
         qng_status st = run_streaming(c, jobs, launches);
         if (st != QNG_OK) return st;
     }
-    for (const Group &g : c->groups) {
-        if (g.num_inst == 0) continue;
-        e = timed(c, 1, [&] { return launch_forward(w, g, c->precision, want_eta, c->stream); });
-        if (e != cudaSuccess) return cuda_status(e);
-        launches += 1;
+    const int wm = (jobs & (kJobMetric | kJobSolve)) ? 1 : 0;
+    const int wg = (jobs & (kJobGradient | kJobSolve)) ? 1 : 0;
+    const int wim = (jobs & kJobMetricIm) ? 1 : 0;
+    int S = wm ? pipe_chunks(c) : 0;
+    std::vector<int> K;
+    std::vector<std::array<int, 2>> rng;
+    if (S) {
+        const int P = c->inst[0].P;
+        for (int s = 0; s <= S; ++s) K.push_back((int)((int64_t)s * P / S));
+        if (!pipe_ranges(c, c->groups[0], wm, wg, S, K, rng)) S = 0;
+    }
+    if (S) {
+        // fork: the sweep's stream follows the coefficients; chunk s's columns follow chunk s;
+        // join: the main stream waits for every column chunk (the last follows the whole sweep)
+        const Group &g = c->groups[0];
+        if ((e = cudaEventRecord(c->pipe_ev0, c->stream)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaStreamWaitEvent(c->pipe_fwd, c->pipe_ev0, 0)) != cudaSuccess) return cuda_status(e);
+        for (int s = 0; s < S; ++s) {
+            e = timed_on(c, 1, c->pipe_fwd, [&] {
+                return launch_forward(w, g, c->precision, want_eta, c->pipe_fwd, K[s], K[s + 1], s == S - 1);
+            });
+            if (e != cudaSuccess) return cuda_status(e);
+            if ((e = cudaEventRecord(c->pipe_evf[s], c->pipe_fwd)) != cudaSuccess) return cuda_status(e);
+            cudaStream_t cs = c->pipe_col[s];
+            if ((e = cudaStreamWaitEvent(cs, c->pipe_evf[s], 0)) != cudaSuccess) return cuda_status(e);
+            if (rng[s][1] > 0) {
+                e = timed_on(c, 2, cs, [&] {
+                    return launch_columns_range(w, g, c->precision, wim, rng[s][0], rng[s][1], false, cs);
+                });
+                if (e != cudaSuccess) return cuda_status(e);
+                launches += 1;
+            }
+            if ((e = cudaEventRecord(c->pipe_evc[s], cs)) != cudaSuccess) return cuda_status(e);
+            if ((e = cudaStreamWaitEvent(c->stream, c->pipe_evc[s], 0)) != cudaSuccess) return cuda_status(e);
+            launches += 1;
+        }
+    } else {
+        for (const Group &g : c->groups) {
+            if (g.num_inst == 0) continue;
+            e = timed(c, 1, [&] { return launch_forward(w, g, c->precision, want_eta, c->stream); });
+            if (e != cudaSuccess) return cuda_status(e);
+            launches += 1;
+        }
     }
     LaunchArgs a = args;
     a.jobs = jobs;
-    if (need_cols) {
-        const int wm = (jobs & (kJobMetric | kJobSolve)) ? 1 : 0;
-        const int wg = (jobs & (kJobGradient | kJobSolve)) ? 1 : 0;
+    if (need_cols && !S) {
         for (const Group &g : c->groups) {
             if ((wm && wg ? g.num_work : (wm ? g.num_met : g.num_grad)) == 0) continue;
-            const int wim = (jobs & kJobMetricIm) ? 1 : 0;
             e = timed(c, 2, [&] { return launch_columns(w, g, c->precision, wm, wg, wim, c->stream); });
             if (e != cudaSuccess) return cuda_status(e);
             launches += 1;
@@ -1034,21 +1163,39 @@ qng_status qng_autotune(qng_ctx *c, const double *theta, int reps, int64_t *repo
         c->tuned_cl[n] = best_cl;
         c->tuned_threads[n] = best_th;
         if (st != QNG_OK) break;
-        // the checkpoint sweep's CTA size, at the chosen cluster and column shape
+        // the checkpoint sweep's cluster and CTA size, at the chosen column shape
         if (best_cl < 0) continue;
-        int best_fth = c->tuned_fwd[n];
-        for (int fth : {64, 128, 256, 512}) {
-            if ((1 << (n - best_cl)) < fth) continue;
-            c->tuned_fwd[n] = fth;
-            if (plan(c) != QNG_OK || c->ws_bytes > bytes) continue;
-            if ((st = upload(c)) != QNG_OK) break;
+        int best_fth = c->tuned_fwd[n], best_fcl = c->tuned_fcl[n];
+        for (int fcl = best_cl; fcl <= std::min(kMaxFwdClusterLog2, std::min(best_cl + 1, n - 1)); ++fcl) {
+            for (int fth : {64, 128, 256, 512}) {
+                if ((1 << (n - fcl)) < fth) continue;
+                c->tuned_fcl[n] = fcl;
+                c->tuned_fwd[n] = fth;
+                if (plan(c) != QNG_OK || c->ws_bytes > bytes) continue;
+                if ((st = upload(c)) != QNG_OK) break;
+                float ms = 0.f;
+                if ((st = time_step(ms)) != QNG_OK) break;
+                ++tried;
+                if (ms < best) { best = ms; best_fth = fth; best_fcl = fcl; }
+            }
+            if (st != QNG_OK) break;
+        }
+        c->tuned_fcl[n] = best_fcl;
+        c->tuned_fwd[n] = best_fth;
+        if (st != QNG_OK) break;
+    }
+    // a single instance: the pipelined sweep's chunk count, at the chosen shapes
+    if (st == QNG_OK && c->count == 1 && (st = plan(c)) == QNG_OK && (st = upload(c)) == QNG_OK) {
+        float best = 3.4e38f;
+        int best_req = c->pipe_req;
+        for (int req : {1, 2, 3, 4}) {
+            c->pipe_req = req;
             float ms = 0.f;
             if ((st = time_step(ms)) != QNG_OK) break;
             ++tried;
-            if (ms < best) { best = ms; best_fth = fth; }
+            if (ms < best) { best = ms; best_req = req; }
         }
-        c->tuned_fwd[n] = best_fth;
-        if (st != QNG_OK) break;
+        c->pipe_req = best_req;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1065,8 +1212,7 @@ qng_status qng_get_tuning(const qng_ctx *c, int n_qubits, int *cluster_log2, int
     cl = std::max(0, std::min(cl, std::min(kMaxClusterLog2, n_qubits - 1)));
     int th = default_threads(n_qubits - cl);
     if (c->tuned_threads[n_qubits] > 0) th = c->tuned_threads[n_qubits];
-    int fth = default_fwd_threads(n_qubits - cl);
-    if (c->tuned_fwd[n_qubits] > 0) fth = c->tuned_fwd[n_qubits];
+    const int fth = fwd_threads_for(c, n_qubits, cl, fwd_cluster(c, n_qubits, cl));
     if (cluster_log2) *cluster_log2 = cl;
     if (threads) *threads = th;
     if (forward_threads) *forward_threads = fth;
@@ -1093,6 +1239,31 @@ qng_status qng_set_shape(qng_ctx *c, int n_qubits, int cluster_log2, int threads
         return s != QNG_OK ? s : QNG_ERR_WORKSPACE;
     }
     if (c->ws) return upload(c);
+    return QNG_OK;
+}
+
+qng_status qng_set_forward_cluster(qng_ctx *c, int n_qubits, int cluster_log2) {
+    if (!c || n_qubits < 1 || n_qubits > kMaxQubits) return QNG_ERR_ARG;
+    if (cluster_log2 < -1 || cluster_log2 > kMaxFwdClusterLog2) return QNG_ERR_ARG;
+    const int old = c->tuned_fcl[n_qubits];
+    c->tuned_fcl[n_qubits] = cluster_log2;
+    qng_status s = plan(c);
+    if (s != QNG_OK || (c->ws && c->ws_bytes > c->ws_cap)) {
+        c->tuned_fcl[n_qubits] = old;
+        plan(c);
+        if (c->ws) upload(c);
+        return s != QNG_OK ? s : QNG_ERR_WORKSPACE;
+    }
+    if (c->ws) return upload(c);
+    return QNG_OK;
+}
+
+qng_status qng_get_forward_cluster(const qng_ctx *c, int n_qubits, int *cluster_log2) {
+    if (!c || !cluster_log2 || n_qubits < 1 || n_qubits > kMaxQubits) return QNG_ERR_ARG;
+    int cl = default_cl(n_qubits, c->precision);
+    if (c->tuned_cl[n_qubits] >= 0) cl = c->tuned_cl[n_qubits];
+    cl = std::max(0, std::min(cl, std::min(kMaxClusterLog2, n_qubits - 1)));
+    *cluster_log2 = fwd_cluster(c, n_qubits, cl);
     return QNG_OK;
 }
 
@@ -1146,6 +1317,18 @@ qng_status qng_profile_read(qng_ctx *c, double *ms, int64_t *launches) {
 qng_status qng_last_launch_count(const qng_ctx *c, int64_t *launches) {
     if (!c || !launches) return QNG_ERR_ARG;
     *launches = c->last_launches;
+    return QNG_OK;
+}
+
+qng_status qng_set_pipeline(qng_ctx *c, int chunks) {
+    if (!c || chunks < 0 || chunks > kPipeMax) return QNG_ERR_ARG;
+    c->pipe_req = chunks;
+    return QNG_OK;
+}
+
+qng_status qng_get_pipeline(const qng_ctx *c, int *chunks) {
+    if (!c || !chunks) return QNG_ERR_ARG;
+    *chunks = pipe_chunks(c);
     return QNG_OK;
 }
 

@@ -15,6 +15,7 @@ namespace qng {
 constexpr int kMaxQubits = 30;         // any single instance
 constexpr int kMaxQubitsSmall = 16;    // instances run by the on-chip (cluster-resident) path
 constexpr int kMaxClusterLog2 = 3;     // 8 CTAs per cluster (the portable maximum)
+constexpr int kMaxFwdClusterLog2 = 4;  // the checkpoint sweep: up to 16 CTAs (non-portable size)
 constexpr int kAxisX = 0, kAxisY = 1, kAxisZ = 2;
 constexpr int kAxisGen = 3;  // generalised rotation: generator K = C (x) S, see DevParam::gx
 
@@ -138,6 +139,7 @@ struct Work {
 struct Group {
     int cl = 0;
     int threads = 128;      // CTA size of the column kernel
+    int fwd_cl = 0;         // cluster size (log2) of the checkpoint sweep
     int fwd_threads = 256;  // CTA size of the checkpoint sweep (k_forward)
     bool general = false;   // some instance has generalised rotations (GEN kernel instantiations)
     int max_n = 0;
@@ -182,9 +184,16 @@ struct LaunchArgs {
 // Kernel-side launchers (qng_kernels.cu). Return cudaSuccess or the launch error.
 cudaError_t launch_coef(const Work &w, const double *theta, int64_t total_params, cudaStream_t st);
 cudaError_t launch_theta_update(const Work &w, double *theta, const double *dtheta, int64_t total, cudaStream_t st);
-cudaError_t launch_forward(const Work &w, const Group &g, int precision, int want_eta, cudaStream_t st);
+// The checkpoint sweep over parameters [k_begin, k_end) (clipped to P); last = 1 adds the
+// trailing gates, <E> and eta. k_begin > 0 restarts from checkpoint k_begin.
+cudaError_t launch_forward(const Work &w, const Group &g, int precision, int want_eta, cudaStream_t st, int k_begin = 0,
+                           int k_end = 1 << 30, int last = 1);
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
                            int metric_im, cudaStream_t st);
+// Work items [first, first + num) of the group's list; persistent = false gives one cluster per
+// item (no work queue), so finished clusters leave their SMs to other kernels.
+cudaError_t launch_columns_range(const Work &w, const Group &g, int precision, int metric_im, int first, int num,
+                                 bool persistent, cudaStream_t st);
 cudaError_t launch_finish(const Work &w, int count, int max_P, const LaunchArgs &a, cudaStream_t st);
 // block solve (qng_solve.cu). Largest own-row count of a CTA over all block columns: CTA 0
 // holds the 16 diagonal-block rows (all P rows when it is alone); a CTA of rank >= 1 holds at most

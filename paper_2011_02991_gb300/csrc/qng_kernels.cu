@@ -729,7 +729,8 @@ __device__ __forceinline__ bool fwd_zrun(Eng<R> &e, typename CX<R>::T *ckpt, uin
 // GEN = 1: the group has generalised rotations (a separate instantiation keeps the registers of
 // the ordinary one unchanged).
 template <typename R, int GEN>
-__global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl, int want_eta) {
+__global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl, int want_eta, int k_begin, int k_end,
+                                                 int last) {
     using cx = typename CX<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const DevInst in = w.inst[w.group_inst[group_first + (blockIdx.x >> cl)]];
@@ -739,36 +740,48 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
     cx *ckpt = reinterpret_cast<cx *>(w.ckpt) + in.ckpt_off;
     double *scales = w.scale + in.scale_off;
 
-    for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
-        cx z = {0, 0};
-        if ((e.base | l) == 0) z.x = 1;
-        e.buf[l] = z;
-        ckpt[e.base | l] = z;
-    }
+    // parameters [k_begin, k_end) of the sweep: from |0> at k_begin = 0, else from checkpoint
+    // k_begin as an earlier launch wrote it (the carried state is that checkpoint, renormalised
+    // exactly as the uninterrupted sweep would have renormalised it)
+    const int kb = min(k_begin, in.P), ke = min(k_end, in.P);
     double scale = 1.0;
-    if (e.rank == 0 && threadIdx.x == 0) scales[0] = 1.0;
+    if (kb == 0) {
+        for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
+            cx z = {0, 0};
+            if ((e.base | l) == 0) z.x = 1;
+            e.buf[l] = z;
+            ckpt[e.base | l] = z;
+        }
+        if (e.rank == 0 && threadIdx.x == 0) scales[0] = 1.0;
+    } else {
+        const cx *src = ckpt + (uint64_t)kb * N;
+        for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) e.buf[l] = src[e.base | l];
+        scale = scales[kb];
+    }
     __syncthreads();
+    if (kb > 0) e.maybe_renorm(scale);
 
     DevParam pk_n;
     DevCoef co_n;
-    if (in.P > 0) { pk_n = w.param[in.param_tab]; co_n = w.coef[in.param_off]; }
-    for (int k = 0; k < in.P; ++k) {
+    if (kb < ke) { pk_n = w.param[in.param_tab + kb]; co_n = w.coef[in.param_off + kb]; }
+    for (int k = kb; k < ke; ++k) {
         // a run of Z rotations with diagonal fixed blocks: one pass, no barriers in between
-        if (pk_n.zrun > 1) {
-            const int m = pk_n.zrun;
+        // (clipped at the end of the range)
+        if (pk_n.zrun > 1 && ke - k > 1) {
+            const int m = min((int)pk_n.zrun, ke - k);
             // the whole run stays above the renormalisation threshold: each factor is >= 1/sqrt2
             const int ex = (int)((__double_as_longlong(scale) >> 52) & 0x7ff);
             if ((!std::is_same<R, double>::value || ex - (m + 1) / 2 - 1 >= 1023 - 200) &&
                 fwd_zrun<R>(e, ckpt, N, w.param + in.param_tab, w.coef + in.param_off, k, m, w.diag, scale, scales,
                             e.rank == 0 && threadIdx.x == 0)) {
                 k += m - 1;
-                if (k + 1 < in.P) { pk_n = w.param[in.param_tab + k + 1]; co_n = w.coef[in.param_off + k + 1]; }
+                if (k + 1 < ke) { pk_n = w.param[in.param_tab + k + 1]; co_n = w.coef[in.param_off + k + 1]; }
                 continue;
             }
         }
         const DevParam pk = pk_n;
         const DevCoef co = co_n;
-        if (k + 1 < in.P) { pk_n = w.param[in.param_tab + k + 1]; co_n = w.coef[in.param_off + k + 1]; }
+        if (k + 1 < ke) { pk_n = w.param[in.param_tab + k + 1]; co_n = w.coef[in.param_off + k + 1]; }
         if constexpr (GEN) {
             if (pk.axis == kAxisGen) {  // generalised rotation: F_k gate by gate, then the plain (cos, sin) form
                 for (int f = 0; f < pk.fix_count; ++f) e.fixed_gate(w.fixed[pk.fix_begin + f], scale);
@@ -790,6 +803,7 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
         e.maybe_renorm(scale);                                         // then the state carried on to k+2
     }
 
+    if (!last) return;
     // trailing fixed gates W, then H W psi, <E> and eta = W^dag H W psi
     for (int f = 0; f < in.w_count; ++f) e.fixed_gate(w.fixed[in.w_begin + f], scale);
     cx *eta = reinterpret_cast<cx *>(w.eta) + in.eta_off;
@@ -1481,14 +1495,15 @@ cudaError_t launch_coef(const Work &w, const double *theta, int64_t total, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_forward(const Work &w, const Group &g, int precision, int want_eta, cudaStream_t st) {
+cudaError_t launch_forward(const Work &w, const Group &g, int precision, int want_eta, cudaStream_t st, int k_begin,
+                           int k_end, int last) {
     if (g.num_inst == 0) return cudaSuccess;
-    const int grid = g.num_inst << g.cl;
-    if (precision == QNG_C128)
-        return g.general ? launch_cluster(k_forward<double, 1>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta)
-                         : launch_cluster(k_forward<double, 0>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
-    return g.general ? launch_cluster(k_forward<float, 1>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta)
-                     : launch_cluster(k_forward<float, 0>, grid, g.fwd_threads, g.smem_fwd, g.cl, st, w, g.first_inst, g.cl, want_eta);
+    const int grid = g.num_inst << g.fwd_cl;
+#define QNG_FWD(RT, G) launch_cluster(k_forward<RT, G>, grid, g.fwd_threads, g.smem_fwd, g.fwd_cl, st, w, g.first_inst, g.fwd_cl, \
+                                      want_eta, k_begin, k_end, last)
+    if (precision == QNG_C128) return g.general ? QNG_FWD(double, 1) : QNG_FWD(double, 0);
+    return g.general ? QNG_FWD(float, 1) : QNG_FWD(float, 0);
+#undef QNG_FWD
 }
 
 cudaError_t launch_columns(const Work &w, const Group &g, int precision, int with_metric, int with_grad,
@@ -1497,10 +1512,15 @@ cudaError_t launch_columns(const Work &w, const Group &g, int precision, int wit
     if (with_metric && with_grad) { first = g.first_work; num = g.num_work; }
     else if (with_metric)         { first = g.first_met; num = g.num_met; }
     else                          { first = g.first_grad; num = g.num_grad; }
+    return launch_columns_range(w, g, precision, metric_im, first, num, true, st);
+}
+
+cudaError_t launch_columns_range(const Work &w, const Group &g, int precision, int metric_im, int first, int num,
+                                 bool persistent, cudaStream_t st) {
     if (num == 0) return cudaSuccess;
     int *queue = nullptr;
     int clusters = num;
-    if (g.queue && g.resident_clusters > 0 && g.resident_clusters < num) {
+    if (persistent && g.queue && g.resident_clusters > 0 && g.resident_clusters < num) {
         queue = g.queue;
         clusters = g.resident_clusters;
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);

@@ -127,6 +127,7 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     const uint32_t Nl = 1u << (n - grp.cl);
     grp.threads = Nl <= 256 ? 64 : (Nl <= 1024 ? 128 : 256);
     grp.fwd_threads = Nl / 2 < 64 ? 64 : (Nl / 2 > 512 ? 512 : (int)(Nl / 2));
+    grp.fwd_cl = grp.cl;
     grp.max_n = n;
     grp.max_P = P;
     grp.first_inst = 0;

@@ -71,6 +71,10 @@ SYMBOLS = {
     "qng_set_tuning": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "qng_last_launch_count": [_vp, _i64p],
     "qng_solve_report": [_vp, _i32p, _i32p],
+    "qng_set_pipeline": [_vp, ctypes.c_int],
+    "qng_set_forward_cluster": [_vp, ctypes.c_int, ctypes.c_int],
+    "qng_get_forward_cluster": [_vp, ctypes.c_int, _i32p],
+    "qng_get_pipeline": [_vp, _i32p],
     "qng_profile": [_vp, ctypes.c_int],
     "qng_set_path": [_vp, ctypes.c_int],
     "qng_stream_traffic": [_vp, _i64p, _i64p, _i64p],
@@ -376,6 +380,25 @@ class Context:
     def last_launch_count(self) -> int:
         v = ctypes.c_int64()
         _chk(load().qng_last_launch_count(self._h, ctypes.byref(v)), "qng_last_launch_count")
+        return int(v.value)
+
+    def set_forward_cluster(self, n_qubits: int, cluster_log2: int):
+        """Cluster size (log2, up to 4) of the checkpoint sweep for n_qubits; -1 = the column kernel's."""
+        _chk(load().qng_set_forward_cluster(self._h, int(n_qubits), int(cluster_log2)), "qng_set_forward_cluster")
+
+    def forward_cluster(self, n_qubits: int) -> int:
+        v = ctypes.c_int32()
+        _chk(load().qng_get_forward_cluster(self._h, int(n_qubits), ctypes.byref(v)), "qng_get_forward_cluster")
+        return int(v.value)
+
+    def set_pipeline(self, chunks: int):
+        """Chunks of the pipelined checkpoint sweep: 0 automatic, 1 off, 2..8 that many."""
+        _chk(load().qng_set_pipeline(self._h, int(chunks)), "qng_set_pipeline")
+
+    def pipeline(self) -> int:
+        """Chunk count the next call uses (0: no pipelining)."""
+        v = ctypes.c_int32()
+        _chk(load().qng_get_pipeline(self._h, ctypes.byref(v)), "qng_get_pipeline")
         return int(v.value)
 
     SOLVE_PATHS = {0: "none", 1: "single", 2: "cluster", 3: "mixed", 4: "block"}

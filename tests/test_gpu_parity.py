@@ -86,8 +86,9 @@ def test_z_runs_forward_shapes(qng, oracle, precision, fwd_threads):
     amplitudes per thread: one rotation at a time)."""
     p = W.z_run_problem(10, 160, 5, precision)
     ctx = qng.Context(p, precision=precision)
+    ctx.set_forward_cluster(10, 1)
     ctx.set_shape(10, 1, 128, fwd_threads)
-    assert ctx.get_tuning(10) == (1, 128, fwd_threads)
+    assert ctx.get_tuning(10) == (1, 128, fwd_threads) and ctx.forward_cluster(10) == 1
     out = ctx.step(ctx.theta0(), p.dt, p.lam)
     ctx.sync()
     ref = oracle.qng_step(p)

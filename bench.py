@@ -389,6 +389,9 @@ def run_ours(args, name, problems, kind, rank, world, local_rank):
                                "derived: float32 128 FMA/clk/SM x 152 SMs x 2.07 GHz",
                 "kernel_avg_ms": col_avg_s * 1e3, "flops_per_launch": flops,
                 "launches_per_step": launches_per_step}
+        if ctx.pipeline():
+            roof["note"] = ("pipelined sweep: the column launches overlap one another and the sweep; achieved divides "
+                            "the step's column flops by the sum of their durations, a lower bound")
     kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4) for k, v in prof.items()}
     cpu_value, cpu_sample = (None, "skipped") if args.cpu_budget <= 0 else oracle_baseline(kind, problems, args.cpu_budget)
     P_tot, M_tot, cnt = ctx.total_params, ctx.total_metric, ctx.count
@@ -401,6 +404,7 @@ def run_ours(args, name, problems, kind, rank, world, local_rank):
                    "n_qubits": sorted({p.n for p in problems}), "P_total": P_tot,
                    "precision": "c128" if prec64 else "c64",
                    "path": "streaming" if kind == "stream" else "on-chip",
+                   "sweep_chunks": ctx.pipeline() if kind != "stream" else 0,
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": ("batch instances sharded over GPUs (LPT by work), no collective on the data path"
                                    if args.sharded else "independent replica per GPU" if world > 1 else "single GPU")},

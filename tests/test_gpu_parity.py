@@ -306,6 +306,19 @@ def test_autotune_keeps_results(qng, oracle):
         assert 0 <= cl <= 3 and th in (64, 128, 256) and fth in (64, 128, 256, 512)
 
 
+def test_z_runs_complex_metric_and_gradient_c64(qng, oracle):
+    """complex64 column walks through long runs of Z rotations (9 qubits, 2 CTAs, 4 amplitudes per
+    thread): Re and Im of G, and the gradient column, against the oracle."""
+    p = W.z_run_problem(9, 240, 3, W.C64)
+    check_complex(qng, oracle, p, W.C64, shape=(9, 1, 64, 0))
+    ctx = qng.Context(p, precision=W.C64)
+    ctx.set_shape(9, 1, 64, 0)
+    gr, en = ctx.gradient(ctx.theta0())
+    ctx.sync()
+    ref = oracle.qng_step(p)
+    assert rel(gr.cpu(), ref["grad"]) <= TOL[W.C64]
+
+
 def check_complex(qng, oracle, probs, precision, shape=None):
     """qng_metric_complex against the oracle's G (Eq. 4), Re and Im, every instance."""
     probs = probs if isinstance(probs, list) else [probs]

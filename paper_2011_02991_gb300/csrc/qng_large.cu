@@ -54,6 +54,15 @@ struct TileCtx {
     uint64_t base;         // global index of the tile's local index 0
 };
 
+constexpr int kOpsCached = 96;  // pass ops kept in shared memory (the rest are read from global memory)
+
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only). Both addresses must be
+// 16-byte aligned: tiles start on 16-byte boundaries and rows of the state are at least 128 bytes.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
 // global index of local index l in the current tile
 __device__ __forceinline__ uint64_t gidx(const TileCtx &tc, const uint64_t *rowoff, uint32_t l) {
     return tc.base | rowoff[l >> tc.low] | (l & ((1u << tc.low) - 1u));
@@ -119,8 +128,12 @@ __device__ __forceinline__ Acc2<R> step_diag(const TileCtx &tc, typename CX2<R>:
     using cx = typename CX2<R>::T;
     constexpr bool kScaled = std::is_same<R, double>::value;
     Acc2<R> acc = {0, 0};
-    for (uint32_t l = threadIdx.x; l < tc.T; l += blockDim.x) {
-        const int beta = gbit(tc, l, q);
+    // the tile's fields in registers (the loop's shared-memory stores would force re-reads)
+    const uint32_t T = tc.T;
+    const int lb = tc.lbit[q];
+    const int bfix = lb < 0 ? (int)((tc.base >> q) & 1ull) : 0;
+    for (uint32_t l = threadIdx.x; l < T; l += blockDim.x) {
+        const int beta = lb >= 0 ? (int)((l >> lb) & 1u) : bfix;
         const cx a = A[l], b = B[l];
         const cx af = lflip2(a, beta);  // (Z b)_beta = (-1)^beta b, folded into a
         if constexpr (IM != 0) acc.im = fma(af.x, b.y, fma(-af.y, b.x, acc.im));
@@ -173,9 +186,11 @@ template <typename R, int MIM>
 __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
     using cx = typename CX2<R>::T;
     constexpr bool kScaled = std::is_same<R, double>::value;
+    constexpr uint32_t kAmpsPer16 = 16 / sizeof(cx);
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t rowoff[1 << kMaxWin];
     __shared__ TileCtx tc;
+    __shared__ PassOp ops_sh[kOpsCached];  // the pass's program, the same for every tile
     __shared__ double red[32];
     const PassDesc pd = *pa.desc;
     const int nt = blockDim.x, nw = nt >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -196,6 +211,7 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
         for (int q = 0; q < pd.low; ++q) tc.lbit[q] = q;
         for (int k = 0; k < pd.win; ++k) tc.lbit[pd.wq[k]] = pd.low + k;
     }
+    for (int o = threadIdx.x; o < pd.nops && o < kOpsCached; o += nt) ops_sh[o] = pa.ops[pd.op_begin + o];
     for (uint32_t r = threadIdx.x; r < (1u << pd.win); r += nt) {
         uint64_t o = 0;
         for (int k = 0; k < pd.win; ++k) o |= (uint64_t)((r >> k) & 1u) << pd.wq[k];
@@ -220,17 +236,23 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
             tc.base = b;
         }
         __syncthreads();
-        // load
+        // load: asynchronous 16-byte copies global -> shared (one complex128 amplitude, or two
+        // adjacent complex64 ones of the same row), every copy of every register in flight before
+        // one wait, so the pass has the memory parallelism to stream at HBM rate
         for (int r = 0; r < kRegs; ++r) {
             if (!(pd.regmask & (1 << r)) || !(pd.loadmask & (1 << r))) continue;
             const cx *src = reinterpret_cast<const cx *>(pa.reg[r]);
-            for (uint32_t l = threadIdx.x; l < tc.T; l += nt) tile[r][l] = src[gidx(tc, rowoff, l)];
+            for (uint32_t c = threadIdx.x; c < tc.T / kAmpsPer16; c += nt) {
+                const uint32_t l = c * kAmpsPer16;
+                cp_async16(tile[r] + l, src + gidx(tc, rowoff, l));
+            }
         }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
         double sc[kRegs];
         for (int r = 0; r < kRegs; ++r) sc[r] = scale[r];
         for (int o = 0; o < pd.nops; ++o) {
-            const PassOp op = pa.ops[pd.op_begin + o];
+            const PassOp op = o < kOpsCached ? ops_sh[o] : pa.ops[pd.op_begin + o];
             switch (op.kind) {
             case kOpCopy: {
                 for (uint32_t l = threadIdx.x; l < tc.T; l += nt) tile[op.r1][l] = tile[op.r0][l];
@@ -257,8 +279,11 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
                     if (!(op.regs & (1 << r))) continue;
                     cx *X = tile[r];
                     if (ax == kAxisZ) {
-                        for (uint32_t l = threadIdx.x; l < tc.T; l += nt) {
-                            const int beta = gbit(tc, l, q);
+                        const uint32_t T = tc.T;
+                        const int lbz = tc.lbit[q];
+                        const int bfix = lbz < 0 ? (int)((tc.base >> q) & 1ull) : 0;
+                        for (uint32_t l = threadIdx.x; l < T; l += nt) {
+                            const int beta = lbz >= 0 ? (int)((l >> lbz) & 1u) : bfix;
                             const cx x = X[l];
                             const cx v = {lflip(x.y, beta ^ 1), lflip(x.x, beta)};  // (i Z x)
                             cx y;
@@ -360,8 +385,12 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
                 const int q = op.q0, ax = op.axis, im = op.adjoint;
                 R acc = 0;
                 if (ax < 0 || ax == kAxisZ) {
-                    for (uint32_t l = threadIdx.x; l < tc.T; l += nt) {
-                        const cx a = (ax == kAxisZ) ? lflip2(A[l], gbit(tc, l, q)) : A[l];
+                    const uint32_t T = tc.T;
+                    const int lbz = ax == kAxisZ ? tc.lbit[q] : -1;
+                    const int bfix = (ax == kAxisZ && lbz < 0) ? (int)((tc.base >> q) & 1ull) : 0;
+                    for (uint32_t l = threadIdx.x; l < T; l += nt) {
+                        const int beta = lbz >= 0 ? (int)((l >> lbz) & 1u) : bfix;
+                        const cx a = (ax == kAxisZ) ? lflip2(A[l], beta) : A[l];
                         const cx b = B[l];
                         acc = im ? fma(a.x, b.y, fma(-a.y, b.x, acc)) : fma(a.x, b.x, fma(a.y, b.y, acc));
                     }
@@ -437,11 +466,14 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
                 }
             }
         }
-        // store
+        // store: 16-byte vector stores (a row of 2^low amplitudes is contiguous)
         for (int r = 0; r < kRegs; ++r) {
             if (!(pd.regmask & (1 << r)) || !(pd.storemask & (1 << r))) continue;
             cx *dst = reinterpret_cast<cx *>(pa.reg[r]);
-            for (uint32_t l = threadIdx.x; l < tc.T; l += nt) dst[gidx(tc, rowoff, l)] = tile[r][l];
+            for (uint32_t c = threadIdx.x; c < tc.T / kAmpsPer16; c += nt) {
+                const uint32_t l = c * kAmpsPer16;
+                *reinterpret_cast<float4 *>(dst + gidx(tc, rowoff, l)) = *reinterpret_cast<const float4 *>(tile[r] + l);
+            }
         }
         if (tile_id + gridDim.x >= ntiles && blockIdx.x == 0 && threadIdx.x == 0 && kScaled)
             for (int r = 0; r < kRegs; ++r) pa.regscale[((pd.parity + 1) & 1) * kRegs + r] = sc[r];

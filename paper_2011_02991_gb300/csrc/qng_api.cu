@@ -395,6 +395,8 @@ qng_status plan(qng_ctx *c) {
         d.w_begin = (int32_t)c->t_fixed.size();
         d.w_count = (int32_t)pending.size();
         for (const qng_gate *g : pending) c->t_fixed.push_back(DevFixed{g->kind, g->q0, g->q1, 0});
+        // terms grouped by X mask (stable): H psi gathers psi[m ^ x] once per distinct mask
+        const size_t tfirst = c->t_term.size();
         for (const qng_pauli &t : h.terms) {
             DevTerm dt = {};
             dt.coeff = t.coeff;
@@ -403,6 +405,8 @@ qng_status plan(qng_ctx *c) {
             dt.ny = __builtin_popcountll(t.xmask & t.zmask) & 3;
             c->t_term.push_back(dt);
         }
+        std::stable_sort(c->t_term.begin() + tfirst, c->t_term.end(),
+                         [](const DevTerm &a, const DevTerm &b) { return a.x < b.x; });
         c->t_inst.push_back(d);
     }
     c->total_params = c->param_off[c->count];

@@ -504,21 +504,31 @@ __global__ void __launch_bounds__(256) k_hpsi(const void *in_, void *out_, const
     const uint64_t N = 1ull << n;
     double e = 0.0;
     for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < N; m += (uint64_t)gridDim.x * blockDim.x) {
-        double hr = 0.0, hi = 0.0;
+        // each element in the amplitudes' own precision (complex64: float32, the precision it is
+        // stored in); the inner product <in|out> below in float64. Terms come grouped by X mask,
+        // so psi[m ^ x] is gathered once per distinct mask.
+        R hr = 0, hi = 0;
+        uint64_t xl = ~0ull;
+        R vr = 0, vi = 0;
         for (int t = 0; t < nterms; ++t) {
             const DevTerm tm = terms[t];
             const uint64_t src = m ^ tm.x;
-            const cx v = in[src];
+            if (tm.x != xl) {
+                const cx v = in[src];
+                vr = v.x;
+                vi = v.y;
+                xl = tm.x;
+            }
             const int ph = (tm.ny + 2 * (__popcll(src & tm.z) & 1)) & 3;
-            const double vr = (double)v.x, vi = (double)v.y;
-            if (ph == 0)      { hr = fma(tm.coeff, vr, hr);  hi = fma(tm.coeff, vi, hi); }
-            else if (ph == 1) { hr = fma(-tm.coeff, vi, hr); hi = fma(tm.coeff, vr, hi); }
-            else if (ph == 2) { hr = fma(-tm.coeff, vr, hr); hi = fma(-tm.coeff, vi, hi); }
-            else              { hr = fma(tm.coeff, vi, hr);  hi = fma(-tm.coeff, vr, hi); }
+            const R cf = (R)tm.coeff;
+            if (ph == 0)      { hr = fma(cf, vr, hr);  hi = fma(cf, vi, hi); }
+            else if (ph == 1) { hr = fma(-cf, vi, hr); hi = fma(cf, vr, hi); }
+            else if (ph == 2) { hr = fma(-cf, vr, hr); hi = fma(-cf, vi, hi); }
+            else              { hr = fma(cf, vi, hr);  hi = fma(-cf, vr, hi); }
         }
         const cx x = in[m];
-        e += (double)x.x * hr + (double)x.y * hi;
-        out[m] = cx{(R)hr, (R)hi};
+        e += (double)x.x * (double)hr + (double)x.y * (double)hi;
+        out[m] = cx{hr, hi};
     }
     e = lwarp_sum(e);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;

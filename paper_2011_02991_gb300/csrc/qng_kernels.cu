@@ -238,6 +238,42 @@ template <typename R> struct Eng {
         if (kind == QNG_GATE_H && kScaled) scale *= 0.70710678118654752440;
     }
 
+    // fixed gates gs[0..count) in circuit order (reverse = true: their adjoint, last gate first);
+    // consecutive diagonal ones (CZ, Z) commute and go through one sign pass with one barrier
+    __device__ void fixed_gates(const DevFixed *gs, int count, double &scale, bool reverse) {
+        for (int f = 0; f < count;) {
+            const DevFixed g = gs[reverse ? count - 1 - f : f];
+            if (g.kind != QNG_GATE_CZ && g.kind != QNG_GATE_Z) {
+                fixed_gate(g, scale);
+                ++f;
+                continue;
+            }
+            int r = f + 1;
+            while (r < count) {
+                const int kd = gs[reverse ? count - 1 - r : r].kind;
+                if (kd != QNG_GATE_CZ && kd != QNG_GATE_Z) break;
+                ++r;
+            }
+            if (r - f == 1) {
+                fixed_gate(g, scale);
+                ++f;
+                continue;
+            }
+            for (uint32_t l = threadIdx.x; l < Nl; l += blockDim.x) {
+                const uint64_t k = base | l;
+                int par = 0;
+                for (int u = f; u < r; ++u) {
+                    const DevFixed d = gs[reverse ? count - 1 - u : u];
+                    const uint64_t m = (d.kind == QNG_GATE_CZ) ? ((1ull << d.q0) | (1ull << d.q1)) : (1ull << d.q0);
+                    par += (k & m) == m;
+                }
+                if (par & 1) { cx x = buf[l]; x.x = -x.x; x.y = -x.y; buf[l] = x; }
+            }
+            __syncthreads();
+            f = r;
+        }
+    }
+
     // keep the float64 scale factor far from underflow: fold 2^-200 into the vector (exact)
     __device__ void maybe_renorm(double &scale) {
         if constexpr (std::is_same<R, double>::value) {
@@ -652,7 +688,8 @@ __global__ void k_coef(const double *theta, DevCoef *coef, double *pctrl, int64_
 template <typename R, int AMPS>
 __device__ __forceinline__ void fwd_zrun_t(Eng<R> &e, typename CX<R>::T *__restrict__ ckpt, uint64_t N,
                                            const DevParam *__restrict__ params, const DevCoef *__restrict__ coefs,
-                                           int k0, int m, const DevDiag *__restrict__ dt) {
+                                           int k0, int m, const DevDiag *__restrict__ dt, double sc, double *sbcast,
+                                           double *scales, bool write_scales) {
     using cx = typename CX<R>::T;
     constexpr bool kScaled = std::is_same<R, double>::value;
     cx x[AMPS];
@@ -693,11 +730,16 @@ __device__ __forceinline__ void fwd_zrun_t(Eng<R> &e, typename CX<R>::T *__restr
             }
             out[kk[a]] = x[a];
         }
+        if (threadIdx.x == 0) {  // thread 0 carries the run's scale sequence (one float64 multiply a step)
+            if constexpr (kScaled) sc *= co.caseB ? -co.f : co.f;
+            if (write_scales) scales[k0 + u + 1] = sc;
+        }
         pk = pn;
         co = cn;
     }
 #pragma unroll
     for (int a = 0; a < AMPS; ++a) e.buf[threadIdx.x + a * blockDim.x] = x[a];
+    if (threadIdx.x == 0) *sbcast = sc;
 }
 
 // returns false (and does nothing) when the CTA shape has no compiled amplitude count
@@ -707,20 +749,16 @@ __device__ __forceinline__ bool fwd_zrun(Eng<R> &e, typename CX<R>::T *ckpt, uin
                                          double *scales, bool write_scales) {
     if (e.Nl % blockDim.x) return false;
     const uint32_t amps = e.Nl / blockDim.x;
+    __shared__ double sbcast;  // the scale after the run, from thread 0 to the CTA
     switch (amps) {
-    case 1: fwd_zrun_t<R, 1>(e, ckpt, N, params, coefs, k0, m, dt); break;
-    case 2: fwd_zrun_t<R, 2>(e, ckpt, N, params, coefs, k0, m, dt); break;
-    case 4: fwd_zrun_t<R, 4>(e, ckpt, N, params, coefs, k0, m, dt); break;
-    case 8: fwd_zrun_t<R, 8>(e, ckpt, N, params, coefs, k0, m, dt); break;
+    case 1: fwd_zrun_t<R, 1>(e, ckpt, N, params, coefs, k0, m, dt, scale, &sbcast, scales, write_scales); break;
+    case 2: fwd_zrun_t<R, 2>(e, ckpt, N, params, coefs, k0, m, dt, scale, &sbcast, scales, write_scales); break;
+    case 4: fwd_zrun_t<R, 4>(e, ckpt, N, params, coefs, k0, m, dt, scale, &sbcast, scales, write_scales); break;
+    case 8: fwd_zrun_t<R, 8>(e, ckpt, N, params, coefs, k0, m, dt, scale, &sbcast, scales, write_scales); break;
     default: return false;
     }
-    // the scale sequence of the run (identical in every thread)
-    for (int u = 0; u < m; ++u) {
-        const DevCoef co = coefs[k0 + u];
-        if (std::is_same<R, double>::value) scale *= co.caseB ? -co.f : co.f;
-        if (write_scales) scales[k0 + u + 1] = scale;
-    }
     __syncthreads();
+    scale = sbcast;
     return true;
 }
 
@@ -791,8 +829,7 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
                 continue;
             }
         }
-        if (pk.diag_count < 0)
-            for (int f = 0; f < pk.fix_count; ++f) e.fixed_gate(w.fixed[pk.fix_begin + f], scale);
+        if (pk.diag_count < 0) e.fixed_gates(w.fixed + pk.fix_begin, pk.fix_count, scale, false);
         const bool pre = pk.diag_count > 0 || pk.zmask != 0;
         double fs;
         const Rot<R> rot = make_rot<R>(co, false, fs);
@@ -805,7 +842,7 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
 
     if (!last) return;
     // trailing fixed gates W, then H W psi, <E> and eta = W^dag H W psi
-    for (int f = 0; f < in.w_count; ++f) e.fixed_gate(w.fixed[in.w_begin + f], scale);
+    e.fixed_gates(w.fixed + in.w_begin, in.w_count, scale, false);
     cx *eta = reinterpret_cast<cx *>(w.eta) + in.eta_off;
     for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) eta[e.base | l] = e.buf[l];
     __syncthreads();
@@ -814,6 +851,7 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
     for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) {
         const uint64_t kk = e.base | l;
         double hr = 0.0, hi = 0.0;
+#pragma unroll 4  // independent gathers of W psi in flight together (each is an L2 round trip)
         for (int t = 0; t < in.nterms; ++t) {
             const DevTerm tm = w.term[in.term_off + t];
             const uint64_t src = kk ^ tm.x;
@@ -834,7 +872,7 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
     const double esum = cluster_sum(epart, red, cl);  // also orders the reads of eta before the writes below
     if (e.rank == 0 && threadIdx.x == 0) w.energy[w.group_inst[group_first + (blockIdx.x >> cl)]] = esum * scale * scale;
     if (want_eta) {
-        for (int f = in.w_count - 1; f >= 0; --f) e.fixed_gate(w.fixed[in.w_begin + f], scale);
+        e.fixed_gates(w.fixed + in.w_begin, in.w_count, scale, true);
         for (uint32_t l = threadIdx.x; l < e.Nl; l += blockDim.x) eta[e.base | l] = e.buf[l];
         if (e.rank == 0 && threadIdx.x == 0) scales[in.P + 1] = scale;
     }

@@ -167,3 +167,53 @@ def test_streaming_workspace(lib):
 def test_status_strings(lib):
     for s in range(8):
         assert lib.qng_status_string(s)
+
+
+def test_pipeline_forward_cluster_and_solve_report_on_the_host(lib):
+    """Host-side settings: the chunk count of the pipelined sweep and the sweep's cluster size are
+    validated and planned without a device; the solve report is empty before any step."""
+    c = W.layered_ansatz(12, 8)
+    st, h = _create(lib, 12, [tuple(int(v) for v in r) for r in c.gates], [(1.0, 1, 0)], W.C128)
+    assert st == 0
+    chunks = ctypes.c_int32()
+    for bad in (-1, 9):
+        assert lib.qng_set_pipeline(h, bad) == 1
+    for ok in (0, 1, 2, 8):
+        assert lib.qng_set_pipeline(h, ok) == 0
+    assert lib.qng_get_pipeline(h, ctypes.byref(chunks)) == 0
+    assert chunks.value == 0  # no workspace yet: nothing pipelines
+    fcl = ctypes.c_int32()
+    assert lib.qng_get_forward_cluster(h, 12, ctypes.byref(fcl)) == 0
+    assert fcl.value == 4  # one instance: twice the column kernel's 8 CTAs
+    for bad in (-2, 5):
+        assert lib.qng_set_forward_cluster(h, 12, bad) == 1
+    assert lib.qng_set_forward_cluster(h, 0, 2) == 1  # qubit count out of range
+    assert lib.qng_set_forward_cluster(h, 12, 2) == 0
+    assert lib.qng_get_forward_cluster(h, 12, ctypes.byref(fcl)) == 0 and fcl.value == 2
+    assert lib.qng_set_forward_cluster(h, 12, -1) == 0
+    assert lib.qng_get_forward_cluster(h, 12, ctypes.byref(fcl)) == 0 and fcl.value == 4
+    path, handed = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.qng_solve_report(h, ctypes.byref(path), ctypes.byref(handed)) == 0
+    assert path.value == 0 and handed.value == 0
+    lib.qng_destroy(h)
+    # a batch keeps one cluster size for both kernels
+    from paper_2011_02991_gb300 import qng
+    probs = W.config_batch(count=3)
+    rows = [np.ascontiguousarray(p.circuit.gates, dtype=np.int32) for p in probs]
+    allg = np.concatenate(rows)
+    ga = (qng.qng_gate * len(allg))()
+    ctypes.memmove(ga, allg.ctypes.data, allg.nbytes)
+    ta = (qng.qng_pauli * 3)(*[qng.qng_pauli(1.0, 1, 0)] * 3)
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    nq = np.array([p.n for p in probs], dtype=np.int32)
+    ng = np.array([len(r) for r in rows], dtype=np.int32)
+    nt = np.ones(3, dtype=np.int32)
+    hb = ctypes.c_void_p()
+    assert lib.qng_create_batch(3, nq.ctypes.data_as(i32), ga, ng.ctypes.data_as(i32), ta, nt.ctypes.data_as(i32),
+                                W.C64, ctypes.byref(hb)) == 0
+    cl, th, fth = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    for n in {p.n for p in probs}:
+        assert lib.qng_get_tuning(hb, n, ctypes.byref(cl), ctypes.byref(th), ctypes.byref(fth)) == 0
+        assert lib.qng_get_forward_cluster(hb, n, ctypes.byref(fcl)) == 0
+        assert fcl.value == cl.value
+    lib.qng_destroy(hb)

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -12,6 +13,20 @@
 #include "qng_large.h"
 
 using namespace qng;
+
+namespace qng {
+
+cudaError_t raise_smem_limit(const void *fn, size_t bytes) {
+    static std::mutex mu;  // read, compare and set as one step across host threads
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace qng
 
 namespace {
 

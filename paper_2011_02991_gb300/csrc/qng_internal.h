@@ -217,4 +217,10 @@ cudaError_t prepare_solve(size_t smem);
 int resident_clusters(const Group &g, int precision);
 cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col, size_t smem_col_im);
 
+// Raise fn's dynamic shared memory limit (cudaFuncAttributeMaxDynamicSharedMemorySize) on the
+// current device to at least bytes; never lowers it. The attribute belongs to the kernel, not to a
+// context, so every context and the allocation-free entry point share it: lowering it for a small
+// problem would make the next launch of a larger live context fail.
+cudaError_t raise_smem_limit(const void *fn, size_t bytes);
+
 }  // namespace qng

@@ -1487,7 +1487,7 @@ static cudaError_t launch_cluster(K kern, int grid, int threads, size_t smem, in
 }
 
 template <typename K> static cudaError_t set_attrs(K kern, size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void *>(kern), smem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
@@ -1602,7 +1602,7 @@ int resident_clusters(const Group &g, int precision) {
 }
 
 cudaError_t prepare_solve(size_t smem) {
-    return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return raise_smem_limit(reinterpret_cast<const void *>(k_solve), smem);
 }
 
 cudaError_t launch_solve(const Work &w, int count, int max_P, int cl, const LaunchArgs &a, cudaStream_t st) {

@@ -555,14 +555,13 @@ __global__ void k_reduce(const double *partial, const double *slotfac, int nctas
 
 // ------------------------------------------------------------------------------------------
 cudaError_t prepare_pass(int precision, size_t smem) {
-    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e;
     if (precision == QNG_C128) {
-        if ((e = cudaFuncSetAttribute(k_pass<double, 0>, attr, (int)smem)) != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_pass<double, 1>, attr, (int)smem);
+        if ((e = raise_smem_limit(reinterpret_cast<const void *>(k_pass<double, 0>), smem)) != cudaSuccess) return e;
+        return raise_smem_limit(reinterpret_cast<const void *>(k_pass<double, 1>), smem);
     }
-    if ((e = cudaFuncSetAttribute(k_pass<float, 0>, attr, (int)smem)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pass<float, 1>, attr, (int)smem);
+    if ((e = raise_smem_limit(reinterpret_cast<const void *>(k_pass<float, 0>), smem)) != cudaSuccess) return e;
+    return raise_smem_limit(reinterpret_cast<const void *>(k_pass<float, 1>), smem);
 }
 
 cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, int metric_im,

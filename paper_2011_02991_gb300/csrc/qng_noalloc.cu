@@ -10,11 +10,15 @@
 // process exits. All calls on one device share it and it keeps what the last call left there:
 // two calls whose work overlaps on the GPU (different streams, or different host threads) race on
 // it and give wrong results, so callers must order them. The device status word at its start is
-// cleared by every call. On each device the first call looks up the array's device address
-// (cudaGetSymbolAddress, with that device current); make that first call before capturing any
-// stream. No cudaMalloc, cudaFree or other allocating routine is called, on the device or on the
-// host: the circuit tables are built in fixed-size arrays on the caller's stack.
-#include <atomic>
+// cleared by every call. Every call looks up the array's device address on the current device
+// (cudaGetSymbolAddress, which allocates nothing), so the address stays right if the device's
+// context is ever re-created; the first call on a device may load the library's kernels, so make
+// it before capturing any stream. No cudaMalloc, cudaFree or other allocating routine is called,
+// on the device or on the host: the circuit tables are built in fixed-size arrays on the caller's
+// stack and copied into the array with cudaMemcpyAsync from that (pageable) memory, which the
+// CUDA runtime stages before the call returns; the host may wait for that staging. A stream that
+// is being captured would record copies from stack memory that is gone by the time the graph
+// runs, so the call refuses such a stream before it touches the device.
 #include <cmath>
 #include <cstring>
 
@@ -24,26 +28,20 @@ namespace {
 
 using namespace qng;
 
-constexpr int kMaxDevices = 64;
 constexpr int kNaMaxGates = 1024;
 constexpr int kNaMaxParams = 320;
 constexpr int kNaMaxDiag = 1024;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[QNG_NOALLOC_SCRATCH_BYTES];
 
-std::atomic<void *> g_scratch_addr[kMaxDevices];
-
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array in the current device's context. The name
+// g_noalloc_scratch in host code is only a host-side handle of the symbol, never an address a
+// kernel may be given.
 qng_status scratch_address(unsigned char **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QNG_ERR_CUDA;
-    void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return QNG_ERR_CUDA;
-        g_scratch_addr[dev].store(p, std::memory_order_release);
-    }
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return QNG_ERR_CUDA;
     *out = static_cast<unsigned char *>(p);
     return QNG_OK;
 }
@@ -176,10 +174,13 @@ extern "C" qng_status qng_metric_noalloc(int n_qubits, const qng_gate *gates, in
     in.eta_off = 0;
     in.scale_off = 0;
 
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return QNG_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return QNG_ERR_UNSUPPORTED;
     unsigned char *base = nullptr;
     qng_status s = scratch_address(&base);
     if (s != QNG_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(base + o_status, 0, 256, st);
     auto put = [&](size_t o, const void *src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, st);

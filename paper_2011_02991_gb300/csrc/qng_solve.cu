@@ -312,10 +312,9 @@ __global__ void __launch_bounds__(256) k_sback(Work w, LaunchArgs a) {
 }
 
 cudaError_t prepare_sblock(int P, int C) {
-    cudaError_t e = cudaFuncSetAttribute(k_sblock, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sblock_smem_bytes(P, C));
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void *>(k_sblock), sblock_smem_bytes(P, C));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sback, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * P));
+    return raise_smem_limit(reinterpret_cast<const void *>(k_sback), sizeof(double) * P);
 }
 
 cudaError_t launch_sblock(const Work &w, const LaunchArgs &a, int P, int C, int K, cudaStream_t st) {

@@ -10,9 +10,12 @@
 // (a few iterations for the metrics of this method, whose condition numbers are in the 10^3 range
 // with lambda = 1e-3). The step stops when the error the last correction leaves, estimated as
 // the correction times its ratio to the previous one, is below 1e-13 of x, or when it stops
-// shrinking. A float32 pivot that is not positive, or an estimated error still above 1e-10 of x
-// when it stops, marks the instance for the float64 cluster solve (k_solve), which is launched
-// right after and stands down for the instances this kernel finished.
+// shrinking. The result is accepted on two tests: the estimated error is at most 1e-12 of |x|, and
+// a final residual r = b - A x computed in float64 gives a normwise backward error
+// |r|_inf / (|A|_inf |x|_inf + |b|_inf) of at most 2 P eps (eps = 2^-53, the bound of a
+// backward-stable float64 solve up to the rounding of r itself). A float32 pivot that is not
+// positive, or a result that fails either test, marks the instance for the float64 cluster solve
+// (k_solve), which is launched right after and stands down for the instances this kernel finished.
 //
 // One cluster of C CTAs (512 threads) per instance. CTA 0 holds the float32 matrix (full square,
 // row stride P + 1) and does the factorisation and the triangular solves; CTAs 1..C-1 hold the
@@ -394,9 +397,51 @@ __global__ void __launch_bounds__(512, 1) k_solve_ir(Work w, LaunchArgs a) {
         }
         cl.sync();
     }
+    // (D) computed backward error of the final x: CTAs >= 1 take r = b - A x over their own rows
+    // with the row sums of |A| (x is the copy CTA 0 pushed before the last barrier) and hand their
+    // maxima of |r_i|, sum_j |A_ij| and |b_i| to CTA 0
+    __shared__ double s_wmax[3][32];
+    __shared__ double s_rmax[3][8];
+    if (!fallback && rank > 0) {
+        double mr = 0.0, ma = 0.0, mb = 0.0;
+        for (int il = wid; il < r1 - r0; il += nwarp) {
+            const double *row = Arow + (size_t)il * P;
+            double s = 0.0, sa = 0.0;
+            for (int j = lane; j < P; j += 32) {
+                s = fma(row[j], xc[j], s);
+                sa += fabs(row[j]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            }
+            const double bi = -a.dt * gr[r0 + il];
+            mr = fmax(mr, fabs(bi - s));
+            ma = fmax(ma, sa);
+            mb = fmax(mb, fabs(bi));
+        }
+        if (lane == 0) { s_wmax[0][wid] = mr; s_wmax[1][wid] = ma; s_wmax[2][wid] = mb; }
+        __syncthreads();
+        if (tid < 3) {
+            double m = 0.0;
+            for (int q = 0; q < nwarp; ++q) m = fmax(m, s_wmax[tid][q]);
+            *cl.map_shared_rank(&s_rmax[tid][rank], 0) = m;
+        }
+    }
+    cl.sync();
     // outputs, or the float64 solve's turn
     if (rank == 0) {
-        if (!fallback && !(en <= 1e-10 * xn)) fallback = true;
+        if (!fallback) {
+            double mr = 0.0, ma = 0.0, mb = 0.0;
+            for (int q = 1; q < C; ++q) {
+                mr = fmax(mr, s_rmax[0][q]);
+                ma = fmax(ma, s_rmax[1][q]);
+                mb = fmax(mb, s_rmax[2][q]);
+            }
+            const bool backward_ok = mr <= 2.0 * P * 0x1p-53 * (ma * xn + mb);
+            if (!(en <= 1e-12 * xn) || !backward_ok) fallback = true;
+        }
         if (tid == 0) w.irflag[b] = fallback ? 1 : 0;
         if (!fallback)
             for (int i = tid; i < P; i += nt) a.dtheta_out[in.param_off + i] = xv[i];
@@ -410,7 +455,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_ir(Work w, LaunchArgs a) {
 }
 
 cudaError_t prepare_solve_ir(int P, int C) {
-    return cudaFuncSetAttribute(k_solve_ir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_ir_smem_bytes(P, C));
+    return raise_smem_limit(reinterpret_cast<const void *>(k_solve_ir), solve_ir_smem_bytes(P, C));
 }
 
 cudaError_t launch_solve_ir(const Work &w, int count, int max_P, int C, const LaunchArgs &a, cudaStream_t st) {

@@ -217,3 +217,28 @@ def test_pipeline_forward_cluster_and_solve_report_on_the_host(lib):
         assert lib.qng_get_forward_cluster(hb, n, ctypes.byref(fcl)) == 0
         assert fcl.value == cl.value
     lib.qng_destroy(hb)
+
+
+def _noalloc_status(lib, n, circuit, precision):
+    """Call qng_metric_noalloc with placeholder device pointers on inputs it must reject on the
+    host, before it touches the device (the pointers are never dereferenced)."""
+    from paper_2011_02991_gb300 import qng
+    f = lib.qng_metric_noalloc
+    f.argtypes = [ctypes.c_int, ctypes.POINTER(qng.qng_gate), ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    ga, ng = qng._gates_array(circuit)
+    fake = ctypes.c_void_p(1 << 40)
+    return f(n, ga, ng, precision, fake, fake, None)
+
+
+@pytest.mark.parametrize("n,layers,precision,expect", [
+    (16, 1, W.C128, 7),   # 16 qubits at complex128: the cluster's state buffers exceed shared memory
+    (16, 1, W.C64, 6),    # 16 qubits complex64, P = 32: the checkpoints exceed the 16 MiB array
+    (15, 1, W.C128, 6),   # 15 qubits complex128, P = 30
+    (12, 16, W.C128, 6),  # 12 qubits complex128, P = 384 > 320 parameters
+    (17, 1, W.C64, 1),    # beyond the on-chip path
+])
+def test_noalloc_limits_rejected_on_host(lib, n, layers, precision, expect):
+    c = W.layered_ansatz(n, layers)
+    assert _noalloc_status(lib, n, c, precision) == expect

@@ -615,10 +615,12 @@ def test_bench_workload_solves_in_mixed_precision(qng, oracle):
 
 
 @pytest.mark.parametrize("lam", [1e-6, 1e-9])
-def test_solve_ill_conditioned(qng, lam):
+@pytest.mark.parametrize("which", ["rand12", "rand6_p200"])
+def test_solve_ill_conditioned(qng, lam, which):
     """Small lambda makes g + lambda I nearly singular (float32 refinement stalls or its pivots
-    fail, and the float64 solve takes over): the step still solves its float64 system."""
-    p = W.config_rand12()
+    fail, and the float64 solve takes over): the step still solves its float64 system, to the
+    backward error of a float64 Cholesky solve and within cond(A) eps of LAPACK's solution."""
+    p = W.config_rand12() if which == "rand12" else _rand_params(6, 200, 7200)
     ctx = qng.Context(p)
     out = ctx.step(ctx.theta0(), p.dt, lam)
     ctx.sync()
@@ -629,3 +631,28 @@ def test_solve_ill_conditioned(qng, lam):
     r = A @ x - b
     # backward error of a float64 Cholesky solve: |r| ~ eps |A| |x|
     assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(A, 2) * np.linalg.norm(x) + 1e-12 * np.linalg.norm(b)
+    # forward error against LAPACK on the same float64 system: at most about cond(A) eps
+    x_ref = np.linalg.solve(A, b)
+    cond = np.linalg.cond(A)
+    assert np.abs(x - x_ref).max() <= 64 * cond * 2.0 ** -53 * np.abs(x_ref).max()
+
+
+def test_live_contexts_of_different_sizes(qng, oracle):
+    """Kernel attributes (the dynamic shared memory limit) are shared by every context of the
+    process: creating a small context after a large one must leave the large one working."""
+    big = W.config_rand12()
+    ctx_big = qng.Context(big)
+    small = W.config_tfim4()
+    ctx_small = qng.Context(small)
+    stream_big = W.random_problem(17, 30, 6, 4242)  # streaming path: its own pass kernels
+    ctx_stream = qng.Context(stream_big)
+    ref_big = oracle.qng_step(big)
+    ref_small = oracle.qng_step(small)
+    for _ in range(2):
+        for ctx, p, ref in ((ctx_big, big, ref_big), (ctx_small, small, ref_small)):
+            out = ctx.step(ctx.theta0(), p.dt, p.lam)
+            ctx.sync()
+            assert rel(out["g"].cpu(), ref["g"]) <= TOL[W.C128], p.name
+            assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[W.C128], p.name
+        ctx_stream.metric(ctx_stream.theta0())
+        ctx_stream.sync()

@@ -65,3 +65,56 @@ def test_noalloc_rejects_too_large(qng):
     theta = torch.zeros(p.P, dtype=torch.float64, device="cuda")
     g = torch.zeros(p.P * p.P, dtype=torch.float64, device="cuda")
     assert _noalloc(qng, p, theta, g, torch.cuda.current_stream()) == qng.QNG_ERR_WORKSPACE
+
+
+def test_noalloc_against_oracle(qng, oracle):
+    """The allocation-free call against the CPU oracle directly (not only against qng_metric)."""
+    stream = torch.cuda.current_stream()
+    for p, tol in ((W.random_problem(6, 60, 4, 909), 1e-10), (W.config_rand12(), 1e-10)):
+        ref = oracle.qng_step(p)["g"]
+        theta = torch.tensor(p.theta, dtype=torch.float64, device="cuda")
+        for call in range(2):
+            g = torch.full((p.P * p.P,), float("nan"), dtype=torch.float64, device="cuda")
+            assert _noalloc(qng, p, theta, g, stream) == 0
+            torch.cuda.synchronize()
+            assert _rel(g.cpu(), ref) <= tol, (p.name, call)
+
+
+def test_noalloc_leaves_live_context_working(qng, oracle):
+    """A small allocation-free call between two calls of a larger live context: the kernels' shared
+    memory limits are process-wide, so the small call must not lower what the context needs."""
+    big = W.config_rand12()
+    ctx = qng.Context(big)
+    ref = oracle.qng_step(big)
+    small = W.config_tfim4()
+    theta_s = torch.tensor(small.theta, dtype=torch.float64, device="cuda")
+    g_s = torch.zeros(small.P * small.P, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        out = ctx.step(ctx.theta0(), big.dt, big.lam)
+        ctx.sync()
+        assert _rel(out["g"].cpu(), ref["g"]) <= 1e-10
+        assert _rel(out["dtheta"].cpu(), ref["dtheta"]) <= 1e-10
+        assert _noalloc(qng, small, theta_s, g_s, stream) == 0
+        torch.cuda.synchronize()
+
+
+def test_noalloc_refuses_capturing_stream(qng):
+    """Under stream capture the call would record copies from stack memory that is gone when the
+    graph runs: it must return QNG_ERR_UNSUPPORTED and issue nothing."""
+    p = W.config_tfim4()
+    theta = torch.tensor(p.theta, dtype=torch.float64, device="cuda")
+    g = torch.zeros(p.P * p.P, dtype=torch.float64, device="cuda")
+    x = torch.zeros(16, device="cuda")
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        x.add_(1.0)
+        status = _noalloc(qng, p, theta, g, torch.cuda.current_stream())
+    assert status == qng.QNG_ERR_UNSUPPORTED
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0
+    assert _noalloc(qng, p, theta, g, torch.cuda.current_stream()) == 0  # outside capture it runs
+    torch.cuda.synchronize()

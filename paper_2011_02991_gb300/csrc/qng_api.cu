@@ -129,7 +129,7 @@ struct qng_ctx {
     large::Schedule sched;
     int l_grid = 0;
     size_t o_reg[large::kRegs] = {0, 0, 0};
-    size_t o_regscale = 0, o_partial = 0, o_slotfac = 0, o_pdesc = 0, o_pops = 0, o_red = 0;
+    size_t o_regscale = 0, o_partial = 0, o_slotfac = 0, o_pdesc = 0, o_pops = 0, o_red = 0, o_phases = 0;
     size_t o_queue = 0;
     // mixed-precision solve: cluster size (0 = not used: P < 48 or its float32 matrix does not fit)
     int ir_C = 0;
@@ -276,7 +276,8 @@ qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
     c->sched = large::Schedule();
     large::build_schedule(h.gates, h.n, h.P, c->precision, c->sched);
     const int64_t ntiles = 1ll << (h.n - c->sched.t);
-    c->l_grid = (int)std::min<int64_t>(ntiles, 152 * 2);
+    // k_pass: two CTAs per SM; the register-phase kernel: one persistent CTA per SM (152 on GB300)
+    c->l_grid = (int)std::min<int64_t>(ntiles, c->sched.phased ? 152 : 152 * 2);
     c->t_inst[0].cl = 0;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = align256(off); off = o + std::max<size_t>(bytes, 1); return o; };
@@ -308,6 +309,7 @@ qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
     c->o_slotfac = take(sizeof(double) * (size_t)c->sched.max_slots);
     c->o_pdesc = take(sizeof(large::PassDesc) * std::max<size_t>(c->sched.passes.size(), 1));
     c->o_pops = take(sizeof(large::PassOp) * std::max<size_t>(c->sched.ops.size(), 1));
+    c->o_phases = take(sizeof(large::PassPhase) * std::max<size_t>(c->sched.phases.size(), 1));
     c->o_red = take(sizeof(large::ReduceItem) * std::max<size_t>(c->sched.reds.size(), 1));
     for (int r = 0; r < large::kRegs; ++r) c->o_reg[r] = take(ab << h.n);
     c->o_ckpt = c->o_eta = 0;
@@ -572,6 +574,8 @@ qng_status upload(qng_ctx *c) {
         const large::Schedule &S = c->sched;
         if ((e = put(c->o_pdesc, S.passes.data(), sizeof(large::PassDesc) * S.passes.size())) != cudaSuccess) return cuda_status(e);
         if ((e = put(c->o_pops, S.ops.data(), sizeof(large::PassOp) * S.ops.size())) != cudaSuccess) return cuda_status(e);
+        if ((e = put(c->o_phases, S.phases.data(), sizeof(large::PassPhase) * S.phases.size())) != cudaSuccess)
+            return cuda_status(e);
         std::vector<large::ReduceItem> items(S.reds.size());
         for (size_t k = 0; k < S.reds.size(); ++k) {
             const large::RedSpec &r = S.reds[k];
@@ -591,6 +595,7 @@ qng_status upload(qng_ctx *c) {
         for (const large::PassDesc &pd : S.passes)
             pass_smem = std::max(pass_smem, (size_t)__builtin_popcount(pd.regmask) * (amp_bytes(c->precision) << pd.t));
         if ((e = large::prepare_pass(c->precision, std::max<size_t>(pass_smem, 1))) != cudaSuccess) return cuda_status(e);
+        if (S.phased && (e = large::prepare_pass_phased()) != cudaSuccess) return cuda_status(e);
         const int scl = solve_cluster_log2(c->max_P);
         if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
         if (c->bsolve && (e = prepare_sblock(c->inst[0].P, c->bs_C)) != cudaSuccess) return cuda_status(e);
@@ -705,6 +710,8 @@ qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
     pa.regscale = reinterpret_cast<double *>(c->ws + c->o_regscale);
     pa.partial = reinterpret_cast<double *>(c->ws + c->o_partial);
     pa.slotfac = reinterpret_cast<double *>(c->ws + c->o_slotfac);
+    pa.phases = reinterpret_cast<const large::PassPhase *>(c->ws + c->o_phases);
+    pa.status = reinterpret_cast<int32_t *>(c->ws + c->o_status);
     const large::PassDesc *descs = reinterpret_cast<const large::PassDesc *>(c->ws + c->o_pdesc);
     const large::ReduceItem *items = reinterpret_cast<const large::ReduceItem *>(c->ws + c->o_red);
     const size_t ab = amp_bytes(c->precision);
@@ -722,7 +729,12 @@ qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
             pa.desc = descs + L.pass;
             const size_t smem = (size_t)__builtin_popcount(pd.regmask) * (ab << pd.t);
             const int mim = L.segment == large::kSegMetricIm ? 1 : 0;
-            e = timed(c, cls, [&] { return large::launch_pass(pa, c->precision, c->l_grid, 256, smem, mim, c->stream); });
+            if (S.phased)
+                e = timed(c, cls, [&] {
+                    return large::launch_pass_phased(pa, pd.regmask, c->l_grid, mim, c->stream);
+                });
+            else
+                e = timed(c, cls, [&] { return large::launch_pass(pa, c->precision, c->l_grid, 256, smem, mim, c->stream); });
         } else if (L.kind == large::Launch::Hpsi) {
             e = timed(c, 1, [&] {
                 return large::launch_hpsi(c->ws + c->o_reg[large::kRegB], c->ws + c->o_reg[large::kRegA],

@@ -38,7 +38,10 @@ struct PassOp {
     int32_t param;
     int32_t fixed_kind;
     int32_t slot;
-    int32_t pad;
+    // register-phase kernel (complex64 tiles of 2^12): position 0..3 among the phase's register
+    // bits of the op's non-diagonal target qubit (kt), and of q0 / q1 where a diagonal part reads
+    // their bit (dk0 / dk1); -1 where the qubit is not a register bit of the phase
+    int8_t kt, dk0, dk1, pad8;
 };
 
 struct PassDesc {
@@ -48,7 +51,25 @@ struct PassDesc {
     int32_t op_begin, nops;
     int32_t nslots, slot_base;
     int32_t parity;
-    int32_t pad;
+    int32_t phase_begin, nphases;  // register phases (complex64 tiles of 2^12 only)
+};
+
+// Register-phase kernel of complex64 passes (tiles of 2^12 amplitudes, 256 threads). Within a phase
+// thread i holds, of every register the phase touches, the 16 amplitudes at the tile's local indices
+// l = tl(i) | dep(m), m = 0..15, where dep puts bit k of m at local bit rbit[k] and tl puts bit b of
+// i at local bit tbit[b]. Every non-diagonal target of the phase's operations is one of the rbit, so
+// the phase runs in registers; phases exchange amplitudes through the shared-memory tile.
+constexpr int kPhaseAmps = 16;
+constexpr int kPhaseTile = 12;      // local qubits of a register-phase tile
+constexpr int kPhaseThreads = 256;
+constexpr int kMaxPhaseOps = 96;    // operations per pass of the register-phase kernel
+constexpr int kMaxPhases = 16;      // phases per pass
+struct PassPhase {
+    int32_t op_begin, op_end;  // the pass's operations [op_begin, op_end), relative to the pass
+    int8_t rbit[4];            // local bits held in registers; rbit[0] == 0 selects 16-byte accesses
+    int8_t tbit[8];            // local bits of the thread index bits 0..7
+    int32_t rmask;             // registers the phase reads or writes (gathered from the tile)
+    int32_t wmask;             // registers the phase writes (scattered back)
 };
 
 struct ReduceItem {
@@ -66,11 +87,20 @@ struct PassArgs {
     double *regscale;  // [2][kRegs]
     double *partial;   // [slots][grid]
     double *slotfac;   // [slots]
+    const PassPhase *phases;  // register-phase kernel only
+    int32_t *status;          // device status word (register-phase kernel: a malformed pass)
 };
 
 cudaError_t prepare_pass(int precision, size_t smem);
 cudaError_t launch_pass(const PassArgs &pa, int precision, int grid, int threads, size_t smem, int metric_im,
                         cudaStream_t st);
+// Register-phase kernel (complex64, tiles of 2^12): the pass's register mask picks the instantiation
+// (stages of the shared-memory tile ring, psi held or not); grid CTAs of kPhaseThreads threads, each
+// taking tiles b, b + grid, ...
+size_t phased_smem_bytes(int nreg);
+int phased_stages(int nreg);
+cudaError_t prepare_pass_phased();
+cudaError_t launch_pass_phased(const PassArgs &pa, int regmask, int grid, int metric_im, cudaStream_t st);
 cudaError_t launch_hpsi(const void *in, void *out, const DevTerm *terms, int nterms, int n, int precision,
                         double *partial, int grid, cudaStream_t st);
 cudaError_t launch_reduce(const double *partial, const double *slotfac, int nctas, const ReduceItem *items, int nitems,
@@ -98,8 +128,10 @@ struct RedSpec {
 
 struct Schedule {
     int n = 0, t = 0, low = 0;
+    bool phased = false;  // complex64 with tiles of 2^12: the register-phase kernel runs every pass
     std::vector<PassDesc> passes;
     std::vector<PassOp> ops;
+    std::vector<PassPhase> phases;
     std::vector<Launch> launches;
     std::vector<RedSpec> reds;
     int max_slots = 1;

@@ -13,6 +13,7 @@
 // Consecutive steps of a segment share a pass while the qubits their non-diagonal operations act on
 // fit in the tile window and their inner products fit in the slot budget.
 #include <algorithm>
+#include <cstdint>
 #include <set>
 
 #include "qng_large.h"
@@ -54,6 +55,118 @@ void access(const PassOp &o, int &rd, int &wr) {
     case kOpStep: rd = (1 << o.r0) | (1 << o.r1); wr = o.param >= 0 ? rd : 0; break;
     default: break;
     }
+}
+
+// Local bit of qubit q in a pass's tile (low qubits, then the window), or -1 outside the tile.
+int local_bit(const PassDesc &pd, int q) {
+    if (q < 0) return -1;
+    if (q < pd.low) return q;
+    for (int k = 0; k < pd.win; ++k)
+        if (pd.wq[k] == q) return pd.low + k;
+    return -1;
+}
+
+// The qubit whose amplitude pairs an operation mixes (-1 when it is diagonal or touches no qubit).
+int pair_target(const PassOp &o) {
+    switch (o.kind) {
+    case kOpRot:
+    case kOpSigma:
+    case kOpIp:
+    case kOpStep: return (o.axis == kAxisX || o.axis == kAxisY) ? o.q0 : -1;
+    case kOpFixed:
+        if (o.fixed_kind == QNG_GATE_CNOT) return o.q1;
+        if (o.fixed_kind == QNG_GATE_CZ || o.fixed_kind == QNG_GATE_Z) return -1;
+        return o.q0;
+    default: return -1;
+    }
+}
+
+// Bank classes of the register-phase tile layout: the 16-byte chunk index c = l >> 1 is stored at
+// c ^ ((c >> 3 ^ c >> 6 ^ c >> 9) & 7), so local bit b >= 1 moves the chunk's bank group along bit
+// (b - 1) % 3 and local bit 0 picks the 8-byte half of the chunk. Threads of a half-warp (8-byte
+// accesses) or quarter-warp (16-byte accesses) hit distinct banks when their thread-index bits are
+// one local bit of each class.
+int bank_class(int b) { return b == 0 ? 3 : (b - 1) % 3; }
+
+// Split a pass's operations into register phases (see PassPhase): a phase takes operations while
+// their pair targets fit in four register bits. ops are annotated with their register positions.
+// Returns false when the pass needs more than kMaxPhases phases.
+bool make_phases(const PassDesc &pd, std::vector<PassOp> &ops, std::vector<PassPhase> &out, size_t *fit_ops) {
+    std::vector<PassPhase> ph;
+    size_t i = 0;
+    while (i < ops.size() || (ops.empty() && ph.empty())) {
+        std::vector<int> R;
+        size_t j = i;
+        for (; j < ops.size(); ++j) {
+            const int lb = local_bit(pd, pair_target(ops[j]));
+            if (pair_target(ops[j]) < 0 || std::count(R.begin(), R.end(), lb)) continue;
+            if (R.size() == 4) break;
+            R.push_back(lb);
+        }
+        // fill to four register bits from the top, keeping a thread bit in every bank class
+        auto left_in_class = [&](int cls) {
+            int c = 0;
+            for (int b = 0; b < kPhaseTile; ++b)
+                if (bank_class(b) == cls && !std::count(R.begin(), R.end(), b)) ++c;
+            return c;
+        };
+        for (int pass = 0; pass < 2 && R.size() < 4; ++pass)
+            for (int b = kPhaseTile - 1; b >= 0 && R.size() < 4; --b) {
+                if (std::count(R.begin(), R.end(), b)) continue;
+                if (pass == 0 && (b == 0 || left_in_class(bank_class(b)) <= 1)) continue;
+                R.push_back(b);
+            }
+        // local bit 0, when held, is register position 0 (16-byte accesses of amplitude pairs)
+        auto z = std::find(R.begin(), R.end(), 0);
+        if (z != R.end()) std::iter_swap(R.begin(), z);
+        PassPhase p = {};
+        p.op_begin = (int32_t)i;
+        p.op_end = (int32_t)j;
+        for (int k = 0; k < 4; ++k) p.rbit[k] = (int8_t)R[k];
+        // thread bits: first one local bit of each bank class (16-byte mode: the three chunk
+        // classes; 8-byte mode: the half bit too), then the rest in increasing order
+        std::vector<int> T;
+        const bool vmode = R[0] == 0;
+        const int want[4] = {3, 0, 1, 2};
+        for (int w = vmode ? 1 : 0; w < 4; ++w)
+            for (int b = 0; b < kPhaseTile; ++b)
+                if (bank_class(b) == want[w] && !std::count(R.begin(), R.end(), b) && !std::count(T.begin(), T.end(), b)) {
+                    T.push_back(b);
+                    break;
+                }
+        for (int b = 0; b < kPhaseTile; ++b)
+            if (!std::count(R.begin(), R.end(), b) && !std::count(T.begin(), T.end(), b)) T.push_back(b);
+        for (int k = 0; k < 8; ++k) p.tbit[k] = (int8_t)T[k];
+        int rm = 0, wm = 0;
+        for (size_t o = i; o < j; ++o) {
+            PassOp &op = ops[o];
+            auto pos = [&](int q) -> int8_t {
+                const int lb = local_bit(pd, q);
+                for (int k = 0; k < 4; ++k)
+                    if (lb >= 0 && R[k] == lb) return (int8_t)k;
+                return (int8_t)-1;
+            };
+            op.kt = pair_target(op) >= 0 ? pos(pair_target(op)) : (int8_t)-1;
+            op.dk0 = pos(op.q0);
+            op.dk1 = pos(op.q1);
+            op.pad8 = 0;
+            int rd, wr;
+            access(op, rd, wr);
+            rm |= rd | wr;
+            wm |= wr;
+        }
+        p.rmask = rm;
+        p.wmask = wm;
+        ph.push_back(p);
+        if ((int)ph.size() > kMaxPhases) {
+            *fit_ops = (size_t)ph[kMaxPhases].op_begin;
+            return false;
+        }
+        if (ops.empty()) break;
+        i = j;
+    }
+    out.insert(out.end(), ph.begin(), ph.end());
+    return true;
 }
 
 struct Builder {
@@ -157,6 +270,7 @@ struct Builder {
         size_t i0 = 0;
         int slot_base = 0;
         const int red_begin = (int)S.reds.size();
+        size_t limit = SIZE_MAX;  // operations of the next pass at most (register-phase limits)
         while (i0 < items.size()) {
             std::set<int> win_set;
             std::vector<PassOp> ops;
@@ -166,6 +280,7 @@ struct Builder {
                 const Item &it = items[i1];
                 const bool new_q = it.need >= 0 && !win_set.count(it.need);
                 if (i1 > i0 && ((new_q && (int)win_set.size() >= win) || ((int)reds.size() + it.nred > kMaxSlots))) break;
+                if (i1 > i0 && (i1 - i0 >= limit || (S.phased && i1 - i0 >= (size_t)kMaxPhaseOps))) break;
                 if (new_q) win_set.insert(it.need);
                 PassOp o = it.op;
                 if (it.nred) o.slot = (int)reds.size();
@@ -199,6 +314,17 @@ struct Builder {
             pd.loadmask = first_read;
             pd.storemask = written;
             if (i1 == items.size()) pd.storemask &= ~dead_at_end;
+            pd.phase_begin = (int)S.phases.size();
+            pd.nphases = 0;
+            if (S.phased) {
+                size_t fit = 0;
+                if (!make_phases(pd, ops, S.phases, &fit)) {
+                    limit = fit;  // form this pass again with the operations its phases can take
+                    continue;
+                }
+                pd.nphases = (int)S.phases.size() - pd.phase_begin;
+            }
+            limit = SIZE_MAX;
             pd.op_begin = (int)S.ops.size();
             pd.nops = (int)ops.size();
             pd.nslots = (int)reds.size();
@@ -242,6 +368,7 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
     S.n = n;
     S.low = B.low;
     S.t = B.t;
+    S.phased = precision == QNG_C64 && B.t == kPhaseTile;
     const int PSI = 1 << kRegPsi, A = 1 << kRegA, Bm = 1 << kRegB;
 
     // forward: psi <- U_{P-1} ... U_0 |0>

@@ -55,9 +55,10 @@ def test_streaming_small_configs(qng, oracle, precision):
 
 
 @pytest.mark.parametrize("precision", [W.C128, W.C64])
-@pytest.mark.parametrize("n,seed", [(6, 1), (9, 2), (13, 3), (15, 4)])
+@pytest.mark.parametrize("n,seed", [(6, 1), (9, 2), (12, 5), (13, 3), (15, 4), (17, 6)])
 def test_streaming_random_circuits(qng, oracle, n, seed, precision):
-    """Every gate kind, on instances that span 1 to 16 tiles."""
+    """Every gate kind, on instances that span 1 to 64 tiles (complex64 from 12 qubits on runs the
+    register-phase kernel: one tile at 12 qubits, 32 tiles over 152 CTAs at 17)."""
     p = W.random_problem(n, 50 + 4 * n, 10, 3000 + seed, precision)
     run_streaming(qng, oracle, p, precision)
 
@@ -92,3 +93,23 @@ def test_streaming_matches_onchip(qng):
     b.sync()
     for k in ("g", "grad", "dtheta", "energy"):
         assert rel(ob[k].cpu(), oa[k].cpu()) <= 1e-11, k
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_streaming_c64_matches_onchip_c64(qng, seed):
+    """Complex64 at 12-14 qubits: the register-phase streaming kernel against the on-chip path, both
+    at complex64, on g, grad and <E> (within the complex64 tolerance of each other)."""
+    n = 12 + seed % 3
+    p = W.random_problem(n, 140, 16, 4100 + seed, W.C64)
+    a = qng.Context(p, path=1)
+    b = qng.Context(p, path=2)
+    ga, sa = a.metric(a.theta0(), want_sigma=True)
+    gb, sb = b.metric(b.theta0(), want_sigma=True)
+    ra, ea = a.gradient(a.theta0())
+    rb, eb = b.gradient(b.theta0())
+    a.sync()
+    b.sync()
+    assert rel(gb.cpu(), ga.cpu()) <= TOL[W.C64]
+    assert rel(sb.cpu(), sa.cpu()) <= TOL[W.C64]
+    assert rel(rb.cpu(), ra.cpu()) <= TOL[W.C64]
+    assert rel(eb.cpu(), ea.cpu()) <= TOL[W.C64]

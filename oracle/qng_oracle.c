@@ -311,10 +311,15 @@ int oracle_qgt(int n, const ogate_t *gates, int G, const double *theta, const in
     cplx *d = (cplx *)malloc(sizeof(cplx) * N * (size_t)m);
     if (!psi || !d) { free(psi); free(d); return -1; }
     run_circuit(psi, n, gates, G, theta, -1);
+    /* Below 2^16 amplitudes the primitives run on one thread, so the independent derivative states
+     * and entries are spread over the threads instead; every entry is computed the same way. */
+#pragma omp parallel for schedule(dynamic) if (N < 65536)
     for (int a = 0; a < m; ++a) run_circuit(d + (size_t)a * N, n, gates, G, theta, idx[a]);
     cplx *T = (cplx *)T_out;
     cplx *Gm = (cplx *)G_out;
+#pragma omp parallel for schedule(static) if (N < 65536)
     for (int a = 0; a < m; ++a) T[a] = inner(psi, d + (size_t)a * N, n);
+#pragma omp parallel for schedule(dynamic) if (N < 65536)
     for (int a = 0; a < m; ++a)
         for (int b = 0; b < m; ++b)
             Gm[(size_t)a * m + b] = inner(d + (size_t)a * N, d + (size_t)b * N, n) - conj(T[a]) * T[b];
@@ -346,19 +351,27 @@ int oracle_gradient(int n, const ogate_t *gates, int G, const double *theta, int
     const size_t N = (size_t)1 << n;
     cplx *psi = (cplx *)malloc(sizeof(cplx) * N);
     cplx *hpsi = (cplx *)malloc(sizeof(cplx) * N);
-    cplx *d = (cplx *)malloc(sizeof(cplx) * N);
-    if (!psi || !hpsi || !d) { free(psi); free(hpsi); free(d); return -1; }
+    if (!psi || !hpsi) { free(psi); free(hpsi); return -1; }
     run_circuit(psi, n, gates, G, theta, -1);
     int rc = hamiltonian_apply(hpsi, psi, n, T, coeff, xm, zm);
     if (E_out) *E_out = creal(inner(psi, hpsi, n));
-    for (int a = 0; a < m; ++a) {
-        run_circuit(d, n, gates, G, theta, idx[a]);
-        grad_out[a] = 2.0 * creal(inner(hpsi, d, n));
+    int bad = 0;
+    /* one derivative state per parameter, on one thread each below 2^16 amplitudes (see oracle_qgt) */
+#pragma omp parallel if (N < 65536) reduction(| : bad)
+    {
+        cplx *d = (cplx *)malloc(sizeof(cplx) * N);
+        if (!d) bad = 1;
+#pragma omp for schedule(dynamic)
+        for (int a = 0; a < m; ++a) {
+            if (!d) continue;
+            run_circuit(d, n, gates, G, theta, idx[a]);
+            grad_out[a] = 2.0 * creal(inner(hpsi, d, n));
+        }
+        free(d);
     }
     free(psi);
     free(hpsi);
-    free(d);
-    return rc;
+    return bad ? -1 : rc;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -588,12 +601,14 @@ int oracle_sampled(int n, const ogate_t *gates, int G, const double *theta, int 
     int rc = hamiltonian_apply(hpsi, psi, n, T, coeff, xm, zm);
     *E_out = creal(inner(psi, hpsi, n));
     cplx *Tc = (cplx *)T_out, *Gc = (cplx *)G_out;
+#pragma omp parallel for schedule(dynamic) if (N < 65536)
     for (int a = 0; a < m; ++a) {
         cplx *da = d + (size_t)a * N;
         run_circuit(da, n, gates, G, theta, idx[a]);
         Tc[a] = inner(psi, da, n);
         grad_out[a] = 2.0 * creal(inner(hpsi, da, n));
     }
+#pragma omp parallel for schedule(dynamic) if (N < 65536)
     for (int a = 0; a < m; ++a)
         for (int b = 0; b < m; ++b)
             Gc[(size_t)a * m + b] = inner(d + (size_t)a * N, d + (size_t)b * N, n) - conj(Tc[a]) * Tc[b];

@@ -1,16 +1,20 @@
 #!/usr/bin/env python3
-"""Benchmark: QNG steps per second on the 12-qubit, P = 192, complex128 workload.
+"""Benchmark: QNG steps per second per configuration; the headline line is the largest single-GPU
+configuration, 28 qubits complex64 (3 x [Ry, Rx, Rz all, CNOT ladder], P = 252, 2 GiB per state).
 
-One step = the whole hot path for one instance: per-parameter coefficients, the checkpoint /
-energy / adjoint-seed sweep, the O(P^2) recurrence of Algorithm 1 plus the reverse gradient
-sweep, the assembly of g = Re G and the Cholesky solve of (g + lambda I) dtheta = -dt grad<E>.
+One step = the whole hot path for one instance (or a batch): per-parameter coefficients, the forward
+sweep, the energy and the reverse gradient sweep, the O(P^2) recurrence of Algorithm 1, the assembly
+of g = Re G and the solve of (g + lambda I) dtheta = -dt grad<E>.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 Prints one JSON line (rank 0). Under torchrun each rank runs an independent replica of the
 workload (no collective on the data path); the timed region is bracketed by barriers and the
-slowest rank's time is used. ``--impl reference`` times the CPU oracle (the plain complex128
-definition) on the host cores instead.
+slowest rank's time is used. The line carries a per_config block: the other configurations
+(12 qubits complex128 and complex64, the 256-instance batch in both precisions, 26 qubits
+complex128) measured in the same run, so the batched and complex64 forms are reported next to the
+plain complex128 form. ``--impl reference`` times the CPU oracle (the plain complex128 definition)
+on the host cores instead.
 """
 from __future__ import annotations
 
@@ -199,17 +203,44 @@ def oracle_check(kind, problems, ctx, outs):
             "sample": f"parameters {idx.tolist()} (sampled oracle entries)"}
 
 
+def cpu_info() -> dict:
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k, _, v = ln.partition(":")
+                if k.strip() in ("model name", "Model Name"):
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.startswith("Model name:"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    import platform
+    return {"cores": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
 def oracle_baseline(kind, problems, budget_s):
-    """Oracle throughput on the host cores: (steps/s, sample description)."""
+    """Oracle throughput on all host cores: (steps/s, sample description, threads used)."""
     from oracle import oracle as O
     O.build()
+    O.set_num_threads(os.cpu_count() or 1)
+    threads = O.num_threads()
     if kind == "single":
         times, t_all = [], time.perf_counter()
         while len(times) < 30 and (not times or time.perf_counter() - t_all < budget_s):
             t0 = time.perf_counter()
             O.qng_step(problems[0])
             times.append(time.perf_counter() - t0)
-        return len(times) / sum(times), f"{len(times)} full oracle QNG steps of the same workload ({sum(times):.1f} s)"
+        return len(times) / sum(times), f"{len(times)} full oracle QNG steps of the same workload ({sum(times):.1f} s)", threads
     if kind == "batch":
         ids, times, t_all = sample_ids(kind, problems), [], time.perf_counter()
         k = 0
@@ -221,16 +252,32 @@ def oracle_baseline(kind, problems, budget_s):
         per_instance = sum(times) / len(times)
         return 1.0 / (per_instance * len(problems)), (
             f"{len(times)} oracle QNG steps of {len(ids)} sampled instances ({sum(times):.1f} s), "
-            f"extrapolated to all {len(problems)} instances")
+            f"extrapolated to all {len(problems)} instances"), threads
     p = problems[0]
-    idx = np.array(sample_ids(kind, problems), dtype=np.int32)
+    idx = np.array([p.P // 2], dtype=np.int32)
     t0 = time.perf_counter()
     O.sampled(p, idx)
     t = time.perf_counter() - t0
     m = len(idx)
-    full = t * (p.P + 2) / (m + 2)  # one derivative state per parameter dominates the definition's cost
-    return 1.0 / full, (f"oracle sampled-entry mode, {m} derivative states + psi + H psi in {t:.1f} s, "
-                        f"extrapolated to the P + 2 states of a full step")
+    full = t * (p.P + 2) / (m + 2)  # one circuit run per derivative state dominates the definition's cost
+    return 1.0 / full, (f"oracle sampled-entry mode at the full size: psi, H psi and {m} derivative state "
+                        f"in {t:.1f} s, extrapolated to the P + 2 circuit runs of a full step"), threads
+
+
+def alg1_mirror(problem, budget_s=20.0):
+    """The literal Algorithm 1 (Sec. 3) on the CPU: metric recurrences per second (L and T, no
+    gradient or solve), the same algorithm the GPU runs, timed on the host for context."""
+    from oracle import oracle as O
+    O.build()
+    O.set_num_threads(os.cpu_count() or 1)
+    times, t_all = [], time.perf_counter()
+    while len(times) < 10 and (not times or time.perf_counter() - t_all < budget_s):
+        t0 = time.perf_counter()
+        O.alg1(problem.circuit, problem.theta)
+        times.append(time.perf_counter() - t0)
+    return {"value": len(times) / sum(times), "unit": "metric recurrences/s",
+            "sample": f"{len(times)} runs of the literal Algorithm 1 ({sum(times):.1f} s)",
+            "threads": O.num_threads() if problem.n >= 16 else 1}
 
 
 def run_reference(args, name, problems, kind, rank, world):
@@ -238,7 +285,8 @@ def run_reference(args, name, problems, kind, rank, world):
         return
     from oracle import oracle as O
     O.build()
-    threads = O.num_threads() if problems[0].n >= 16 else 1
+    O.set_num_threads(os.cpu_count() or 1)
+    threads = O.num_threads()
     if kind == "single":
         p = problems[0]
         warm, tw = 0, time.perf_counter()
@@ -256,31 +304,46 @@ def run_reference(args, name, problems, kind, rank, world):
         value, steps, sample = k / el, k, f"{k} full oracle QNG steps (of {args.steps} requested, capped at ~100 s)"
         ms = 1e3 * el / k
     else:
-        value, sample = oracle_baseline(kind, problems, budget_s=60.0)
+        value, sample, threads = oracle_baseline(kind, problems, budget_s=60.0)
         steps, ms, warm = 1, 1e3 / value, 0
+    info = cpu_info()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": steps, "steps_requested": args.steps, "warmup": warm, "warmup_requested": args.warmup,
             "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{name}: {DESCRIPTION[name]}", "parallelism": "single host process"},
-            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "cpu_model": info["cpu_model"],
+                             "host_cores": info["cores"], "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, name, problems, kind, rank, world, local_rank):
+def make_problems(name, world, rank, shard):
+    make, kind = workloads()[name]
+    loop = kind == "loop"
+    if loop:
+        kind = "single"
+    made = make()
+    problems = made if isinstance(made, list) else [made]
+    sharded = False
+    if shard and kind == "batch" and world > 1:
+        from paper_2011_02991_gb300 import dist as D
+        problems = [problems[b] for b in D.shard_batch(problems, world)[rank]]
+        sharded = True
+    return problems, kind, loop, sharded
+
+
+def measure(name, steps, warmup, dev, rank, world, local_rank, check=True, shard=False, e2e_steps=None,
+            clocks=False):
+    """Time `steps` QNG steps of workload `name` (after `warmup` untimed ones) on `dev`; returns a dict."""
     import torch
     import torch.distributed as dist
-    from paper_2011_02991_gb300 import build as B
     from paper_2011_02991_gb300 import qng
-    from paper_2011_02991_gb300 import workloads as W
 
-    B.build()
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
+    problems, kind, loop, sharded = make_problems(name, world, rank, shard)
     stream = torch.cuda.Stream(device=dev)
-    prec = problems[0].precision
     dt, lam = problems[0].dt, problems[0].lam
+    res = {"name": name, "kind": kind, "problems": problems, "sharded": sharded}
     with torch.cuda.stream(stream):
         ctx = qng.Context(problems if kind == "batch" else problems[0], device=dev, stream=stream)
         theta = ctx.theta0()
@@ -288,157 +351,244 @@ def run_ours(args, name, problems, kind, rank, world, local_rank):
                 "grad": ctx._f64(ctx.total_params), "energy": ctx._f64(ctx.count)}
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
-        err = None
-        if rank == 0 and not args.no_check:
+        res["err"] = None
+        if rank == 0 and check:
             ctx.step(theta, dt, lam, outs)
             ctx.sync()
-            err = oracle_check(kind, problems, ctx, outs)
+            res["err"] = oracle_check(kind, problems, ctx, outs)
 
         theta_loop = theta.clone()
-        if args.loop:  # one descent iteration per step, theta updated on the device
+        if loop:  # one descent iteration per step, theta updated on the device
             def one_step():
                 ctx.optimize(theta_loop, dt, lam, 1)
         else:
             def one_step():
                 ctx.step(theta, dt, lam, outs)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             flush.zero_()
             one_step()
         ctx.sync()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
-        clocks = ClockSampler(local_rank)
-        clocks.start()
-        time.sleep(0.25)
+        sampler = ClockSampler(local_rank) if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.25)
         ctx.profile(True)
-        launches0 = 0
-        for k in range(args.steps):
+        launches = 0
+        for k in range(steps):
             flush.zero_()
             ev[k][0].record(stream)
             one_step()
-            launches0 += ctx.last_launch_count()
+            launches += ctx.last_launch_count()
             ev[k][1].record(stream)
         torch.cuda.synchronize(dev)
         prof = ctx.profile_read()
         ctx.profile(False)
-        ck = clocks.stop()
+        res["clocks"] = sampler.stop() if sampler else None
         ctx.sync()
         ms = sum(a.elapsed_time(b) for a, b in ev)
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dist.barrier()
-        ms_max = float(t.item())
+        res["ms_total"] = float(t.item())
+        res["launches"] = launches
+        res["prof"] = prof
+        res["pipeline"] = ctx.pipeline() if kind != "stream" else 0
+        res["sizes"] = (ctx.total_params, ctx.total_metric, ctx.count)
+        if kind == "stream":
+            res["traffic"] = ctx.stream_traffic()
+            res["segments"] = ctx.stream_segments()
 
         # end to end through the public host-buffer entry point (pinned host memory)
-        th_host = torch.from_numpy(np.concatenate([p.theta for p in problems]).astype(np.float64)).pin_memory().numpy()
-        hout = {"dtheta": torch.empty(ctx.total_params, dtype=torch.float64).pin_memory().numpy(),
-                "g": torch.empty(ctx.total_metric, dtype=torch.float64).pin_memory().numpy(),
-                "grad": torch.empty(ctx.total_params, dtype=torch.float64).pin_memory().numpy(),
-                "energy": torch.empty(ctx.count, dtype=torch.float64).pin_memory().numpy()}
-        e2e_steps = args.steps if kind != "stream" else min(args.steps, 2)
-        for _ in range(max(1, min(args.warmup, 2) // 2)):
+        res["e2e_ms"] = None
+        if e2e_steps:
+            th_host = torch.from_numpy(np.concatenate([p.theta for p in problems]).astype(np.float64)).pin_memory().numpy()
+            hout = {"dtheta": torch.empty(ctx.total_params, dtype=torch.float64).pin_memory().numpy(),
+                    "g": torch.empty(ctx.total_metric, dtype=torch.float64).pin_memory().numpy(),
+                    "grad": torch.empty(ctx.total_params, dtype=torch.float64).pin_memory().numpy(),
+                    "energy": torch.empty(ctx.count, dtype=torch.float64).pin_memory().numpy()}
             ctx.step_host(th_host, dt, lam, hout)
-        if world > 1:
-            dist.barrier()
-        e2e_ms = 0.0
-        for _ in range(e2e_steps):
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            ctx.step_host(th_host, dt, lam, hout)
-            e2e_ms += 1e3 * (time.perf_counter() - t0)
-        te = torch.tensor([e2e_ms / e2e_steps], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_ms_per_step = float(te.item())
+            if world > 1:
+                dist.barrier()
+            e2e_ms = 0.0
+            for _ in range(e2e_steps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                ctx.step_host(th_host, dt, lam, hout)
+                e2e_ms += 1e3 * (time.perf_counter() - t0)
+            te = torch.tensor([e2e_ms / e2e_steps], dtype=torch.float64, device=dev)
+            if world > 1:
+                dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            res["e2e_ms"] = float(te.item())
+            res["e2e_steps"] = e2e_steps
+        ctx.close()
+        del flush, outs, theta, theta_loop
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    return res
 
-    if rank != 0:
-        return
-    # replicas: every rank does a whole step; sharded batch: the ranks together do one step
-    value = args.steps * (1 if args.sharded else world) / (ms_max / 1e3)
+
+def roofline(res, steps):
+    """Roofline of the step's dominant kernel class (see DESIGN: algorithmic work per unit)."""
+    from paper_2011_02991_gb300 import workloads as W
+    problems, kind, prof, name = res["problems"], res["kind"], res["prof"], res["name"]
+    prec64 = problems[0].precision == W.C128
     col_ms, col_n = prof["columns"]
-    prec64 = prec == W.C128
     if kind == "stream":
-        mb, ob, mp = ctx.stream_traffic()
+        mb, ob, mp = res["traffic"]
         p = problems[0]
-        met_s = col_ms / args.steps / 1e3
+        met_s = col_ms / steps / 1e3
         if prec64:
             elems = p.P * (p.P - 1) / 2
             flops = (1 << p.n) * 12.0 * elems  # inner product 2 FMA + two scaled rotations 2 FMA each, per amplitude
             achieved = flops / met_s / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                    "kernel": "k_pass metric passes + column reductions", "kernel_avg_ms": met_s * 1e3,
-                    "flops_per_step": flops, "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz"}
-        else:
-            achieved = mb / met_s / 1e9
-            roof = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                    "frac": achieved / HBM_PEAK_GBS, "traffic": None,
-                    "kernel": "k_pass metric passes (registers loaded and stored per pass)", "kernel_avg_ms": met_s * 1e3,
-                    "bytes_per_step": mb, "passes_per_step": mp, "peak_source": "measured copy bandwidth"}
+                    "kernel": "k_pass metric passes", "kernel_avg_ms": met_s * 1e3 * steps / max(col_n, 1),
+                    "flops_per_step": flops, "launches_per_step": col_n / steps,
+                    "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz"}
+        achieved = mb / met_s / 1e9
+        traffic = TRAFFIC.get(name)
+        return {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                "frac": achieved / HBM_PEAK_GBS, "traffic": traffic,
+                "kernel": "k_pass_phased metric passes (registers loaded and stored per pass)",
+                "kernel_avg_ms": col_ms / max(col_n, 1), "bytes_per_launch": mb / max(mp, 1),
+                "bytes_per_step": mb, "launches_per_step": mp, "peak_source": "measured copy bandwidth (of measured)"}
+    col_avg_s = col_ms / max(col_n, 1) / 1e3
+    launches_per_step = col_n / max(steps, 1)
+    flops_step = sum(column_flops(p.P, p.n) for p in problems)  # all instances, all column launches of a step
+    flops = flops_step / max(launches_per_step, 1)                # per launch, averaged
+    peak = FP64_PEAK_TFLOPS if prec64 else FP32_PEAK_TFLOPS
+    achieved = flops_step * steps / (col_ms / 1e3) / 1e12 if col_ms > 0 else 0.0
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": TRAFFIC.get(name), "kernel": "k_columns (recurrence + gradient sweep)",
+            "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz" if prec64 else
+                           "derived: float32 128 FMA/clk/SM x 152 SMs x 2.07 GHz",
+            "kernel_avg_ms": col_avg_s * 1e3, "flops_per_launch": flops, "launches_per_step": launches_per_step}
+    if res["pipeline"]:
+        roof["note"] = ("pipelined sweep: the column launches overlap one another and the sweep; achieved divides "
+                        "the step's column flops by the sum of their durations, a lower bound")
+    return roof
+
+
+def segment_rates(res, steps):
+    """Streaming path: algorithmic HBM bytes and GB/s of every kernel class in one step."""
+    out = {}
+    for k, (b, n) in res["segments"].items():
+        ms, launches = res["prof"][k]
+        if n == 0 or launches == 0:
+            continue
+        out[k] = {"bytes_per_step": int(b), "launches_per_step": int(n), "ms_per_step": ms / steps,
+                  "GBps": b / (ms / steps / 1e3) / 1e9 if ms > 0 else None,
+                  "frac_of_hbm": (b / (ms / steps / 1e3) / 1e9) / HBM_PEAK_GBS if ms > 0 else None}
+    return out
+
+
+# configurations reported beside the headline (per_config): name -> (timed steps, warm-up steps)
+PER_CONFIG = {
+    "rand12_p192_c128": (100, 10),
+    "rand12_p192_c64": (100, 10),
+    "batch256_c128": (6, 3),
+    "batch256_c64": (20, 3),
+    "tfim26_p208_c128": (2, 3),
+}
+
+
+def run_ours(args, name, rank, world, local_rank):
+    import torch
+    from paper_2011_02991_gb300 import build as B
+    from paper_2011_02991_gb300 import workloads as W
+
+    B.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    kind0 = workloads()[name][1]
+    e2e_steps = args.steps if kind0 != "stream" else min(args.steps, 2)
+    res = measure(name, args.steps, args.warmup, dev, rank, world, local_rank, check=not args.no_check,
+                  shard=args.shard, e2e_steps=e2e_steps, clocks=True)
+    per = {}
+    if rank == 0 and world == 1 and not args.no_per_config:
+        plain = None
+        for other, (k, w) in PER_CONFIG.items():
+            if other == name:
+                continue
+            r = measure(other, k, w, dev, rank, world, local_rank, check=not args.no_check)
+            v = k / (r["ms_total"] / 1e3)
+            rf = roofline(r, k)
+            per[other] = {"value": v, "unit": "steps/s", "ms_per_step": r["ms_total"] / k, "steps": k, "warmup": w,
+                          "workload": DESCRIPTION[other], "max_err_vs_oracle": r["err"],
+                          "roofline": {key: rf[key] for key in ("bound", "achieved", "peak", "unit", "frac")}}
+            if r["kind"] == "stream":
+                per[other]["segments"] = segment_rates(r, k)
+            if other == "rand12_p192_c128":
+                plain = v
+        if plain:
+            for other in per:
+                if other.startswith("rand12") or other.startswith("batch256"):
+                    per[other]["vs_rand12_c128_steps"] = per[other]["value"] / plain
+        if "rand12_p192_c128" in per:
+            per["rand12_p192_c128"]["cpu_alg1_mirror"] = alg1_mirror(W.config_rand12())
+    if rank != 0:
+        return
+    problems, kind, prof = res["problems"], res["kind"], res["prof"]
+    steps = args.steps
+    value = steps * (1 if res["sharded"] else world) / (res["ms_total"] / 1e3)
+    prec64 = problems[0].precision == W.C128
+    roof = roofline(res, steps)
+    total_prof = max(sum(x[0] for x in prof.values()), 1e-12)
+    kernel_share = {k: round(v[0] / total_prof, 4) for k, v in prof.items() if v[1] > 0}
+    if args.cpu_budget > 0:
+        cpu_value, cpu_sample, cpu_threads = oracle_baseline(kind, problems, args.cpu_budget)
     else:
-        col_avg_s = col_ms / max(col_n, 1) / 1e3
-        launches_per_step = col_n / max(args.steps, 1)
-        flops_step = sum(column_flops(p.P, p.n) for p in problems)  # all instances, all column launches of a step
-        flops = flops_step / max(launches_per_step, 1)                # per launch, averaged
-        peak = FP64_PEAK_TFLOPS if prec64 else FP32_PEAK_TFLOPS
-        achieved = flops_step * args.steps / (col_ms / 1e3) / 1e12 if col_ms > 0 else 0.0
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC.get(name), "kernel": "k_columns (recurrence + gradient sweep)",
-                "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz" if prec64 else
-                               "derived: float32 128 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                "kernel_avg_ms": col_avg_s * 1e3, "flops_per_launch": flops,
-                "launches_per_step": launches_per_step}
-        if ctx.pipeline():
-            roof["note"] = ("pipelined sweep: the column launches overlap one another and the sweep; achieved divides "
-                            "the step's column flops by the sum of their durations, a lower bound")
-    kernel_share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4) for k, v in prof.items()}
-    cpu_value, cpu_sample = (None, "skipped") if args.cpu_budget <= 0 else oracle_baseline(kind, problems, args.cpu_budget)
-    P_tot, M_tot, cnt = ctx.total_params, ctx.total_metric, ctx.count
+        cpu_value, cpu_sample, cpu_threads = None, "skipped", None
+    P_tot, M_tot, cnt = res["sizes"]
+    info = cpu_info()
     line = {
-        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_total"] / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec64 else "f32 (f64 accumulation, assembly, solve)",
         "data": "synthetic",
         "config": {"workload": f"{name}: {DESCRIPTION[name]}", "instances": cnt,
                    "n_qubits": sorted({p.n for p in problems}), "P_total": P_tot,
                    "precision": "c128" if prec64 else "c64",
                    "path": "streaming" if kind == "stream" else "on-chip",
-                   "sweep_chunks": ctx.pipeline() if kind != "stream" else 0,
-                   "l2": "flushed between timed steps (256 MiB write, untimed)",
+                   "sweep_chunks": res["pipeline"],
+                   "l2": ("inputs larger than L2 (2^n-amplitude registers) and L2 flushed between timed steps "
+                          "(256 MiB write, untimed)"),
                    "parallelism": ("batch instances sharded over GPUs (LPT by work), no collective on the data path"
-                                   if args.sharded else "independent replica per GPU" if world > 1 else "single GPU")},
-        "max_err_vs_oracle": err,
+                                   if res["sharded"] else "independent replica per GPU" if world > 1 else "single GPU")},
+        "max_err_vs_oracle": res["err"],
         "roofline": roof,
         "kernel_share": kernel_share,
-        "cpu_baseline": {"value": cpu_value, "unit": "steps/s",
-                         "cores": cpu_threads_used(max(p.n for p in problems)), "kind": "oracle", "sample": cpu_sample},
-        "e2e": {"value": world / (e2e_ms_per_step / 1e3), "unit": "steps/s", "h2d_bytes_per_step": 8 * P_tot,
-                "d2h_bytes_per_step": 8 * (M_tot + 2 * P_tot + cnt)},
-        "gpu_launches": int(launches0),
-        "clocks": {k: ck[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "cpu_baseline": {"value": cpu_value, "unit": "steps/s", "cores": cpu_threads, "host_cores": info["cores"],
+                         "cpu_model": info["cpu_model"], "kind": "oracle", "sample": cpu_sample},
+        "e2e": {"value": world / (res["e2e_ms"] / 1e3), "unit": "steps/s", "h2d_bytes_per_step": 8 * P_tot,
+                "d2h_bytes_per_step": 8 * (M_tot + 2 * P_tot + cnt), "steps": res["e2e_steps"]},
+        "gpu_launches": int(res["launches"]),
+        "clocks": {k: res["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
+    if kind == "stream":
+        line["segments"] = segment_rates(res, steps)
+    if per:
+        line["per_config"] = per
     print(json.dumps(line), flush=True)
-
-
-def cpu_threads_used(n: int) -> int:
-    # the oracle's loops only go parallel for states of at least 2^16 amplitudes
-    from oracle import oracle as O
-    return O.num_threads() if n >= 16 else 1
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rand12_p192_c128", choices=sorted(DESCRIPTION))
-    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline (0: skip)")
-    ap.add_argument("--no-check", action="store_true", help="skip the oracle accuracy check")
+    ap.add_argument("--workload", default="rand28_p252_c64", choices=sorted(DESCRIPTION))
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle time for cpu_baseline (0: skip)")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle accuracy checks")
+    ap.add_argument("--no-per-config", action="store_true", help="skip the per_config block")
     ap.add_argument("--shard", action="store_true",
                     help="batch workloads under torchrun: split the instances over the ranks (strong scaling) "
                          "instead of one replica per rank")
@@ -449,18 +599,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     name = args.workload
-    make, kind = workloads()[name]
-    args.loop = kind == "loop"
-    if args.loop:
-        kind = "single"
-    made = make()
-    problems = made if isinstance(made, list) else [made]
-    args.sharded = False
-    if args.shard and kind == "batch" and world > 1:
-        from paper_2011_02991_gb300 import dist as D
-        problems = [problems[b] for b in D.shard_batch(problems, world)[rank]]
-        args.sharded = True
     if args.impl == "reference":
+        problems, kind, _, _ = make_problems(name, world, rank, args.shard)
         run_reference(args, name, problems, kind, rank, world)
         return
     if world > 1:
@@ -469,7 +609,7 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", init_method="env://")
     try:
-        run_ours(args, name, problems, kind, rank, world, local_rank)
+        run_ours(args, name, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

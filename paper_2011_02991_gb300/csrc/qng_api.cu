@@ -161,8 +161,8 @@ struct qng_ctx {
     struct Mark { int cls; cudaEvent_t a, b; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> spare;
-    double prof_ms[QNG_KERNEL_CLASSES] = {0, 0, 0, 0};
-    int64_t prof_n[QNG_KERNEL_CLASSES] = {0, 0, 0, 0};
+    double prof_ms[QNG_KERNEL_CLASSES] = {};
+    int64_t prof_n[QNG_KERNEL_CLASSES] = {};
 
     qng_ctx() {
         for (int k = 0; k <= kMaxQubits; ++k) { tuned_cl[k] = -1; tuned_threads[k] = 0; tuned_fwd[k] = 0; tuned_fcl[k] = -1; }
@@ -696,6 +696,18 @@ bool pipe_ranges(const qng_ctx *c, const Group &g, int wm, int wg, int S, const 
     return true;
 }
 
+// Kernel class (qng_profile_read) of a launch of the streaming schedule.
+int stream_class(const large::Launch &L) {
+    if (L.kind == large::Launch::Hpsi) return 5;
+    if (L.kind == large::Launch::Reduce) return 7;
+    switch (L.segment) {
+    case large::kSegForward: return 1;
+    case large::kSegEnergy: return 4;
+    case large::kSegAdjoint: return 6;
+    default: return 2;
+    }
+}
+
 // The streaming schedule's launches for the requested jobs.
 qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
     const large::Schedule &S = c->sched;
@@ -721,7 +733,7 @@ qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
                         : L.segment == large::kSegAdjoint ? grad
                         : L.segment == large::kSegMetric ? metric && !metric_im
                                                          : metric && metric_im;
-        const int cls = (L.segment == large::kSegMetric || L.segment == large::kSegMetricIm) ? 2 : 1;
+        const int cls = stream_class(L);
         if (!want) continue;
         cudaError_t e = cudaSuccess;
         if (L.kind == large::Launch::Pass) {
@@ -736,7 +748,7 @@ qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
             else
                 e = timed(c, cls, [&] { return large::launch_pass(pa, c->precision, c->l_grid, 256, smem, mim, c->stream); });
         } else if (L.kind == large::Launch::Hpsi) {
-            e = timed(c, 1, [&] {
+            e = timed(c, cls, [&] {
                 return large::launch_hpsi(c->ws + c->o_reg[large::kRegB], c->ws + c->o_reg[large::kRegA],
                                           reinterpret_cast<const DevTerm *>(c->ws + c->o_term), (int)h.terms.size(), h.n,
                                           c->precision, pa.partial, c->l_grid, c->stream);
@@ -1314,6 +1326,32 @@ qng_status qng_stream_traffic(const qng_ctx *c, int64_t *metric_bytes, int64_t *
     if (metric_bytes) *metric_bytes = mb;
     if (other_bytes) *other_bytes = ob;
     if (metric_passes) *metric_passes = mp;
+    return QNG_OK;
+}
+
+qng_status qng_stream_segments(const qng_ctx *c, int64_t *bytes, int64_t *launches) {
+    if (!c) return QNG_ERR_ARG;
+    int64_t b[QNG_KERNEL_CLASSES] = {}, n[QNG_KERNEL_CLASSES] = {};
+    if (c->streaming) {
+        const int64_t reg = (int64_t)amp_bytes(c->precision) << c->inst[0].n;
+        for (const large::Launch &L : c->sched.launches) {
+            if (L.segment == large::kSegMetricIm) continue;  // a complex-metric call's, not a step's
+            const int k = stream_class(L);
+            if (L.kind == large::Launch::Pass) {
+                const large::PassDesc &pd = c->sched.passes[L.pass];
+                b[k] += reg * (__builtin_popcount(pd.loadmask & pd.regmask) + __builtin_popcount(pd.storemask & pd.regmask));
+            } else if (L.kind == large::Launch::Hpsi) {
+                b[k] += 2 * reg;
+            } else {
+                b[k] += (int64_t)sizeof(double) * (int64_t)L.nitems * c->l_grid;
+            }
+            ++n[k];
+        }
+    }
+    for (int k = 0; k < QNG_KERNEL_CLASSES; ++k) {
+        if (bytes) bytes[k] = b[k];
+        if (launches) launches[k] = n[k];
+    }
     return QNG_OK;
 }
 

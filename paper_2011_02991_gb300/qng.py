@@ -78,6 +78,7 @@ SYMBOLS = {
     "qng_profile": [_vp, ctypes.c_int],
     "qng_set_path": [_vp, ctypes.c_int],
     "qng_stream_traffic": [_vp, _i64p, _i64p, _i64p],
+    "qng_stream_segments": [_vp, _i64p, _i64p],
     "qng_graph_capture": [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp],
     "qng_graph_launch": [_vp],
     "qng_autotune": [_vp, _vp, ctypes.c_int, _i64p],
@@ -365,17 +366,27 @@ class Context:
     def set_tuning(self, min_qubits: int, cluster_log2: int, threads: int):
         _chk(load().qng_set_tuning(self._h, min_qubits, cluster_log2, threads), "qng_set_tuning")
 
-    KERNEL_CLASSES = ("coef", "forward", "columns", "finish")
+    # kernel classes of qng_profile_read (include/qng.h); 4-7 are streaming-path segments
+    KERNEL_CLASSES = ("coef", "forward", "columns", "finish", "energy", "hpsi", "adjoint", "reduce")
 
     def profile(self, enable: bool):
         _chk(load().qng_profile(self._h, int(bool(enable))), "qng_profile")
 
     def profile_read(self) -> dict:
         """Per kernel class: (milliseconds, launches) since the last read; waits for the stream."""
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_int64 * 4)()
+        k = len(self.KERNEL_CLASSES)
+        ms = (ctypes.c_double * k)()
+        n = (ctypes.c_int64 * k)()
         _chk(load().qng_profile_read(self._h, ms, n), "qng_profile_read")
-        return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+        return {name: (ms[i], n[i]) for i, name in enumerate(self.KERNEL_CLASSES)}
+
+    def stream_segments(self) -> dict:
+        """Per kernel class: (HBM bytes the schedule moves in one step, launches); streaming path."""
+        k = len(self.KERNEL_CLASSES)
+        b = (ctypes.c_int64 * k)()
+        n = (ctypes.c_int64 * k)()
+        _chk(load().qng_stream_segments(self._h, b, n), "qng_stream_segments")
+        return {name: (b[i], n[i]) for i, name in enumerate(self.KERNEL_CLASSES)}
 
     def last_launch_count(self) -> int:
         v = ctypes.c_int64()

@@ -26,6 +26,7 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +58,7 @@ def lib():
             L.oracle_gradient.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, ctypes.c_int, _dp, _u64p, _u64p,
                                           _i32p, ctypes.c_int, _dp, _dp]
             L.oracle_alg1.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _i64p, _dp]
+            L.oracle_alg1_columns.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, _u8p, _dp, _dp]
             L.oracle_alg3.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, _dp, _i64p]
             L.oracle_alg6.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, ctypes.c_int, _dp, _i64p]
             L.oracle_alg8.argtypes = [ctypes.c_int, _i32p, ctypes.c_int, _dp, _dp, _i64p]
@@ -247,6 +249,21 @@ def alg1(circuit, theta, skip_diag: bool = True):
                              _p(L.view(np.float64), _dp), _p(T.view(np.float64), _dp), _p(cnt, _i64p),
                              _p(psi.view(np.float64), _dp)))
     return L, T, tuple(int(v) for v in cnt), psi
+
+
+def alg1_columns(circuit, theta, cols):
+    """Algorithm 1 with only the inner loops of columns `cols` (0-based) run: (L, T), the other
+    columns zero. psi still advances through every gate (Sec. 3's inner loop reads only psi_{j-1})."""
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    g = _gates(circuit)
+    P = circuit.num_params
+    want = np.zeros(max(P, 1), dtype=np.uint8)
+    want[np.asarray(cols, dtype=np.int64)] = 1
+    L = np.zeros((P, P), dtype=np.complex128)
+    T = np.zeros(P, dtype=np.complex128)
+    _check(lib().oracle_alg1_columns(circuit.n, _p(g, _i32p), len(g), _p(theta, _dp), _p(want, _u8p),
+                                     _p(L.view(np.float64), _dp), _p(T.view(np.float64), _dp)))
+    return L, T
 
 
 def _alg_L(fn, circuit, theta, *extra):

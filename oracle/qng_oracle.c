@@ -434,8 +434,29 @@ static void op_clone_in(circ_t *c, cplx *dst) { c->counts[1]++; zero_state(dst, 
  * counts. With skip_diag = 1 the diagonal is taken a priori as 1/4 (Eq. L_diag_when_single_pauli)
  * instead of <phi|phi>. psi_out (optional) receives register psi = U_P ... U_1 |in>.
  */
+static int alg1_impl(int n, const ogate_t *gates, int G, const double *theta, int skip_diag, const uint8_t *want,
+                     double *L_out, double *T_out, int64_t *counts, double *psi_out);
+
 int oracle_alg1(int n, const ogate_t *gates, int G, const double *theta, int skip_diag, double *L_out,
                 double *T_out, int64_t *counts, double *psi_out) {
+    return alg1_impl(n, gates, G, theta, skip_diag, NULL, L_out, T_out, counts, psi_out);
+}
+
+/*
+ * Algorithm 1 for a subset of its columns (Sec. 3: the inner loop over i for column j reads only
+ * psi = psi_{j-1} and the gate list, so columns may be computed apart and gathered). want[j] != 0
+ * (j = 0..P-1, the paper's j + 1) selects the columns whose inner loop runs; register psi still
+ * advances through every gate. Column j's entries L_ij (i <= j) and T_j are written for the
+ * selected columns only; the others are left zero. With every column selected this is Algorithm 1
+ * exactly as oracle_alg1 runs it, operation for operation.
+ */
+int oracle_alg1_columns(int n, const ogate_t *gates, int G, const double *theta, const uint8_t *want,
+                        double *L_out, double *T_out) {
+    return alg1_impl(n, gates, G, theta, 1, want, L_out, T_out, NULL, NULL);
+}
+
+static int alg1_impl(int n, const ogate_t *gates, int G, const double *theta, int skip_diag, const uint8_t *want,
+                     double *L_out, double *T_out, int64_t *counts, double *psi_out) {
     circ_t c;
     if (circ_init(&c, n, gates, G, theta)) { circ_free(&c); return -1; }
     const int P = c.P;
@@ -445,15 +466,22 @@ int oracle_alg1(int n, const ogate_t *gates, int G, const double *theta, int ski
     if (!chi || !psi || !phi || !lam || !mu) { free(chi); free(psi); free(phi); free(lam); free(mu); circ_free(&c); return -1; }
     cplx *L = (cplx *)L_out, *T = (cplx *)T_out;
     memset(L, 0, sizeof(cplx) * (size_t)P * (size_t)P);
+    if (want) memset(T, 0, sizeof(cplx) * (size_t)P);
     if (P > 0) {
         op_clone_in(&c, chi);                 /* chi := |in>            */
         op_U(&c, chi, 0, 0);                  /* chi <- U_1             */
         op_clone(&c, psi, chi);               /* psi := chi             */
-        op_clone_in(&c, phi);                 /* phi := |in>            */
-        op_U(&c, phi, 0, 2);                  /* phi <- dU_1            */
-        T[0] = op_inner(&c, chi, phi);        /* T_1 = <chi|phi>        */
-        L[0] = skip_diag ? 0.25 : op_inner(&c, phi, phi);
+        if (!want || want[0]) {
+            op_clone_in(&c, phi);             /* phi := |in>            */
+            op_U(&c, phi, 0, 2);              /* phi <- dU_1            */
+            T[0] = op_inner(&c, chi, phi);    /* T_1 = <chi|phi>        */
+            L[0] = skip_diag ? 0.25 : op_inner(&c, phi, phi);
+        }
         for (int j = 1; j < P; ++j) {         /* paper's j = 2..P       */
+            if (want && !want[j]) {           /* another rank's column: */
+                op_U(&c, psi, j, 0);          /* psi <- U_j only        */
+                continue;
+            }
             op_clone(&c, lam, psi);           /* lambda := psi          */
             op_clone(&c, phi, psi);           /* phi := psi             */
             op_U(&c, phi, j, 2);              /* phi <- dU_j            */

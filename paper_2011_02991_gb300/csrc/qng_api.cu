@@ -124,6 +124,7 @@ struct qng_ctx {
     // tuning
     int tune_min_qubits = 0, tune_cl = -1, tune_threads = 0;
     int path = 0;             // 0 automatic, 1 on-chip, 2 streaming
+    std::vector<uint8_t> col_want;  // column subset of a single instance (empty: every column)
     // streaming path (one instance, registers in HBM)
     bool streaming = false;
     large::Schedule sched;
@@ -274,7 +275,7 @@ qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
     const HostInst &h = c->inst[0];
     const size_t ab = amp_bytes(c->precision);
     c->sched = large::Schedule();
-    large::build_schedule(h.gates, h.n, h.P, c->precision, c->sched);
+    large::build_schedule(h.gates, h.n, h.P, c->precision, c->sched, c->col_want.empty() ? nullptr : &c->col_want);
     const int64_t ntiles = 1ll << (h.n - c->sched.t);
     // k_pass: two CTAs per SM; the register-phase kernel: one persistent CTA per SM (152 on GB300)
     c->l_grid = (int)std::min<int64_t>(ntiles, c->sched.phased ? 152 : 152 * 2);
@@ -479,7 +480,8 @@ qng_status plan(qng_ctx *c) {
             g.max_n = std::max(g.max_n, c->inst[b].n);
             g.max_P = std::max(g.max_P, c->inst[b].P);
             if (c->inst[b].P > 0)
-                for (int j = 0; j <= c->inst[b].P; ++j) items.push_back(DevWork{b, j});
+                for (int j = 0; j <= c->inst[b].P; ++j)
+                    if (j == c->inst[b].P || c->col_want.empty() || c->col_want[j]) items.push_back(DevWork{b, j});
         }
         g.num_inst = (int)c->t_group_inst.size() - g.first_inst;
         // longest first: steps x amplitudes (column j has j steps, the gradient column P)
@@ -659,7 +661,7 @@ template <class F> cudaError_t timed(qng_ctx *c, int cls, F &&launch) { return t
 
 // Chunks of the pipelined sweep for this call (0: one sweep, then one column launch).
 int pipe_chunks(const qng_ctx *c) {
-    if (!c->pipe_ready || c->streaming || c->count != 1 || c->groups.size() != 1) return 0;
+    if (!c->pipe_ready || c->streaming || c->count != 1 || c->groups.size() != 1 || !c->col_want.empty()) return 0;
     const int P = c->inst[0].P;
     // automatic: only for circuits with generalised rotations (measured faster there; with plain
     // rotations the column phase ends on the latency of its longest items, which cannot start
@@ -769,6 +771,9 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
     if (!c) return QNG_ERR_ARG;
     if (!c->ws || !c->prepared) return QNG_ERR_WORKSPACE;
     if (!args.theta && c->total_params > 0) return QNG_ERR_ARG;
+    // with a column subset only the partial metric (kJobParts) and the step from gathered parts run
+    if (!c->col_want.empty() && (jobs & (kJobMetric | kJobSolve | kJobMetricIm)) && !(jobs & (kJobParts | kJobFromParts)))
+        return QNG_ERR_UNSUPPORTED;
     const Work w = c->work();
     int64_t launches = 0;
     cudaError_t e = cudaSuccess;
@@ -777,16 +782,26 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
         if (e != cudaSuccess) return cuda_status(e);
         launches += 1;
     }
-    const bool need_cols = jobs & (kJobMetric | kJobGradient | kJobSolve);
+    if (jobs & kJobFromParts) {
+        // the metric columns, sigma and the gradient were computed apart (column partition) and
+        // gathered: place them where the assembly and the solve read them, then solve
+        const HostInst &h = c->inst[0];
+        const size_t PP = sizeof(double) * (size_t)h.P * h.P, P1 = sizeof(double) * (size_t)h.P;
+        if ((e = cudaMemcpyAsync(w.L, args.parts_L, PP, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(w.sigma, args.parts_sigma, P1, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(w.gradraw, args.parts_grad, P1, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    const bool need_cols = !(jobs & kJobFromParts) && (jobs & (kJobMetric | kJobGradient | kJobSolve));
     const bool want_eta = jobs & (kJobGradient | kJobSolve);
-    if (c->streaming) {
+    if (c->streaming && !(jobs & kJobFromParts)) {
         qng_status st = run_streaming(c, jobs, launches);
         if (st != QNG_OK) return st;
     }
     const int wm = (jobs & (kJobMetric | kJobSolve)) ? 1 : 0;
     const int wg = (jobs & (kJobGradient | kJobSolve)) ? 1 : 0;
     const int wim = (jobs & kJobMetricIm) ? 1 : 0;
-    int S = wm ? pipe_chunks(c) : 0;
+    int S = (wm && !(jobs & kJobFromParts)) ? pipe_chunks(c) : 0;
     std::vector<int> K;
     std::vector<std::array<int, 2>> rng;
     if (S) {
@@ -819,7 +834,7 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
             if ((e = cudaStreamWaitEvent(c->stream, c->pipe_evc[s], 0)) != cudaSuccess) return cuda_status(e);
             launches += 1;
         }
-    } else {
+    } else if (!(jobs & kJobFromParts)) {
         for (const Group &g : c->groups) {
             if (g.num_inst == 0) continue;
             e = timed(c, 1, [&] { return launch_forward(w, g, c->precision, want_eta, c->stream); });
@@ -836,6 +851,17 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
             if (e != cudaSuccess) return cuda_status(e);
             launches += 1;
         }
+    }
+    if (jobs & kJobParts) {  // partial metric of a column subset: the raw parts go out, no assembly
+        const HostInst &h = c->inst[0];
+        const size_t PP = sizeof(double) * (size_t)h.P * h.P, P1 = sizeof(double) * (size_t)h.P;
+        if ((args.parts_L && (e = cudaMemcpyAsync(args.parts_L, w.L, PP, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) ||
+            (args.parts_sigma && (e = cudaMemcpyAsync(args.parts_sigma, w.sigma, P1, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) ||
+            (args.grad_out && (e = cudaMemcpyAsync(args.grad_out, w.gradraw, P1, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) ||
+            (args.energy_out && (e = cudaMemcpyAsync(args.energy_out, w.energy, sizeof(double), cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess))
+            return cuda_status(e);
+        c->last_launches = launches;
+        return QNG_OK;
     }
     const int scl = solve_cluster_log2(c->max_P);
     if (jobs & kJobSolve)
@@ -1126,6 +1152,75 @@ qng_status qng_set_path(qng_ctx *c, int path) {
     }
     if (c->ws) return upload(c);
     return QNG_OK;
+}
+
+qng_status qng_column_partition(int P, int ranks, int rank, int32_t *cols, int *ncols) {
+    if (P < 0 || ranks < 1 || rank < 0 || rank >= ranks || !ncols || (P > 0 && !cols)) return QNG_ERR_ARG;
+    // pair k = {k, P-1-k} (k < P/2) has P-1 recurrence steps whatever k: pairs go round robin,
+    // and the middle column of an odd P (half a pair's steps) to the next rank in turn
+    int m = 0;
+    std::vector<int32_t> mine;
+    for (int k = 0; k < P / 2; ++k)
+        if (k % ranks == rank) { mine.push_back(k); mine.push_back(P - 1 - k); }
+    if ((P & 1) && (P / 2) % ranks == rank) mine.push_back(P / 2);
+    std::sort(mine.begin(), mine.end());
+    for (int32_t j : mine) cols[m++] = j;
+    *ncols = m;
+    return QNG_OK;
+}
+
+qng_status qng_set_column_subset(qng_ctx *c, const int32_t *cols, int ncols) {
+    if (!c) return QNG_ERR_ARG;
+    if (c->count != 1) return QNG_ERR_UNSUPPORTED;
+    if (c->inst[0].general) return QNG_ERR_UNSUPPORTED;
+    const int P = c->inst[0].P;
+    std::vector<uint8_t> want;
+    if (cols && ncols >= 0) {
+        want.assign(std::max(P, 1), 0);
+        for (int k = 0; k < ncols; ++k) {
+            if (cols[k] < 0 || cols[k] >= P || want[cols[k]]) return QNG_ERR_ARG;
+            want[cols[k]] = 1;
+        }
+    }
+    std::vector<uint8_t> old = c->col_want;
+    c->col_want = want;
+    qng_status s = plan(c);
+    if (s != QNG_OK || (c->ws && c->ws_bytes > c->ws_cap)) {
+        c->col_want = old;
+        plan(c);
+        if (c->ws) upload(c);
+        return s != QNG_OK ? s : QNG_ERR_WORKSPACE;
+    }
+    if (c->ws) return upload(c);
+    return QNG_OK;
+}
+
+qng_status qng_metric_columns(qng_ctx *c, const double *theta, double *L, double *sigma, double *grad, double *energy) {
+    if (!c || !L || !sigma) return QNG_ERR_ARG;
+    if (c->count != 1) return QNG_ERR_UNSUPPORTED;
+    LaunchArgs a = {};
+    a.theta = theta;
+    a.parts_L = L;
+    a.parts_sigma = sigma;
+    a.grad_out = grad;
+    a.energy_out = energy;
+    return run(c, kJobMetric | kJobGradient | kJobParts, a);
+}
+
+qng_status qng_step_from_parts(qng_ctx *c, const double *theta, const double *L, const double *sigma,
+                               const double *grad, double dt, double lambda, double *dtheta, double *g_opt) {
+    if (!c || !L || !sigma || !grad || !dtheta || !(lambda >= 0.0) || !std::isfinite(dt)) return QNG_ERR_ARG;
+    if (c->count != 1) return QNG_ERR_UNSUPPORTED;
+    LaunchArgs a = {};
+    a.theta = theta;
+    a.parts_L = const_cast<double *>(L);
+    a.parts_sigma = const_cast<double *>(sigma);
+    a.parts_grad = grad;
+    a.dt = dt;
+    a.lambda = lambda;
+    a.dtheta_out = dtheta;
+    a.g_out = g_opt;
+    return run(c, kJobSolve | kJobFromParts, a);
 }
 
 qng_status qng_graph_capture(qng_ctx *c, const double *theta, double dt, double lambda, double *dtheta, double *g_opt,

@@ -165,6 +165,8 @@ enum Job : int {
     kJobEnergy = 4,
     kJobSolve = 8,
     kJobMetricIm = 16,  // with kJobMetric: Im G as well (no solve in the same call)
+    kJobParts = 32,     // column partition: the raw L, sigma, grad and <E> go out, no assembly
+    kJobFromParts = 64, // column partition: assemble and solve from gathered L, sigma and grad
 };
 
 struct LaunchArgs {
@@ -176,6 +178,9 @@ struct LaunchArgs {
     double *energy_out;   // may be null
     double *dtheta_out;   // may be null
     const double *grad_scale;  // device, one per instance (energy backward), may be null
+    double *parts_L;           // column partition: L (P x P) out (kJobParts) or in (kJobFromParts)
+    double *parts_sigma;       //   sigma (P), likewise
+    const double *parts_grad;  //   grad (P) in (kJobFromParts)
     int ir_gate;               // k_solve: only the instances the mixed-precision solve handed over
     double dt, lambda;
     int jobs;

@@ -137,8 +137,11 @@ struct Schedule {
     int max_slots = 1;
 };
 
-// Build the streaming schedule of one instance: gates (circuit order), P parameters.
-void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precision, Schedule &out);
+// Build the streaming schedule of one instance: gates (circuit order), P parameters. want (P
+// entries, may be null: all) selects the metric columns whose recurrence runs; for the others the
+// metric segment only advances psi through U_j.
+void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precision, Schedule &out,
+                    const std::vector<uint8_t> *want = nullptr);
 
 }  // namespace large
 }  // namespace qng

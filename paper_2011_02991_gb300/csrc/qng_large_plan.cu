@@ -360,7 +360,8 @@ struct Builder {
 
 }  // namespace
 
-void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precision, Schedule &S) {
+void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precision, Schedule &S,
+                    const std::vector<uint8_t> *want) {
     Builder B(gates, n, P, S);
     B.low = std::min(n, precision == QNG_C128 ? 4 : 5);
     B.win = std::min(kMaxWin, n - B.low);
@@ -431,7 +432,26 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
     // metric columns (segment kSegMetric, Re L), then the same with Im L (kSegMetricIm)
     for (const int im : {0, 2}) {
     B.parity = 0;
+    // columns another rank computes: psi only advances through U_j (runs of them share passes)
+    std::vector<Group> skipped;
+    auto flush_skipped = [&]() {
+        if (!skipped.empty()) B.emit(skipped, im ? kSegMetricIm : kSegMetric, 0);
+        skipped.clear();
+    };
     for (int j = 0; j < P; ++j) {
+        if (want && !(*want)[j]) {
+            skipped.emplace_back();
+            Group &g = skipped.back();
+            if (j == 0) {
+                PassOp z = mk(kOpZero);
+                z.r0 = kRegPsi;
+                g.ops.push_back(z);
+            }
+            for (int gi : B.fixed_of[j]) B.add_fixed(g, gi, PSI);
+            B.add_rot(g, j, false, PSI);
+            continue;
+        }
+        flush_skipped();
         std::vector<Group> gs(j + 1);
         Group &g0 = gs[0];
         if (j == 0) {
@@ -468,6 +488,7 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
         }
         B.emit(gs, im ? kSegMetricIm : kSegMetric, A | Bm);
     }
+    flush_skipped();
     }
 }
 

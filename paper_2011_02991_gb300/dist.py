@@ -1,10 +1,15 @@
 """Multi-process helpers: one process per GPU, launched by torch.distributed.run.
 
-The QNG path shards without any collective on its data path. Batch instances are independent problems.
-`shard_batch` gives each rank a balanced share of them, and `gather_per_instance` brings the
-per-instance results to every rank after the step, once per step, outside the compute path. Timing
-follows the benchmark contract: a barrier on both sides of the timed region and the slowest rank's
-time (`max_over_ranks`).
+Two ways the path shards:
+  - batches: instances are independent problems. `shard_batch` gives each rank a balanced share of
+    them, and `gather_per_instance` brings the per-instance results to every rank after the step,
+    once per step, outside the compute path (no collective on the data path);
+  - one instance (the column partition, Sec. 3: Algorithm 1's inner loop for column j reads only
+    psi_{j-1}, so the columns of L are independent): every rank computes its balanced column pairs
+    (`column_partition`, qng_column_partition), then one all-gather of the columns of L and of
+    sigma (`gather_columns`) lets each rank assemble G and solve (`sharded_step`).
+Timing follows the benchmark contract: a barrier on both sides of the timed region and the slowest
+rank's time (`max_over_ranks`).
 """
 from __future__ import annotations
 
@@ -92,3 +97,55 @@ def max_over_ranks(value: float, device=None) -> float:
 def barrier():
     if world()[1] > 1:
         dist.barrier()
+
+
+def column_owners(P: int, world_size: int) -> np.ndarray:
+    """owner[j]: the rank that computes metric column j (qng_column_partition)."""
+    from . import qng
+    owner = np.full(P, -1, dtype=np.int64)
+    for r in range(world_size):
+        owner[qng.column_partition(P, world_size, r)] = r
+    return owner
+
+
+def merge_columns(L_all, sigma_all, owner: np.ndarray):
+    """Every rank's L (P x P) and sigma (P) -> one L and sigma: column j (its entries i < j, the
+    only ones the recurrence writes) and sigma[j] from the rank that owns j."""
+    P = owner.size
+    L = torch.zeros(P, P, dtype=L_all[0].dtype, device=L_all[0].device)
+    sigma = torch.zeros(P, dtype=sigma_all[0].dtype, device=sigma_all[0].device)
+    iu = torch.triu_indices(P, P, offset=1, device=L.device)
+    own = torch.as_tensor(owner, device=L.device)
+    for r, (Lr, sr) in enumerate(zip(L_all, sigma_all)):
+        Lr = Lr.reshape(P, P)
+        sel = own[iu[1]] == r
+        L[iu[0][sel], iu[1][sel]] = Lr[iu[0][sel], iu[1][sel]]
+        sigma[own == r] = sr.reshape(P)[own == r]
+    return L, sigma
+
+
+def gather_columns(L_local, sigma_local, owner: np.ndarray):
+    """All-gather every rank's partial L and sigma (one collective each) and merge them."""
+    rank, ws = world()
+    if ws == 1:
+        return merge_columns([L_local], [sigma_local], owner)
+    L_all = [torch.empty_like(L_local) for _ in range(ws)]
+    s_all = [torch.empty_like(sigma_local) for _ in range(ws)]
+    dist.all_gather(L_all, L_local.contiguous())
+    dist.all_gather(s_all, sigma_local.contiguous())
+    return merge_columns(L_all, s_all, owner)
+
+
+def sharded_step(ctx, theta, dt: float, lam: float):
+    """One QNG step of a single-instance context with the metric columns split over the ranks: the
+    rank's columns (qng_metric_columns), one all-gather, assembly and solve on every rank
+    (qng_step_from_parts). Returns dict(dtheta, g, grad, energy). The context must have been
+    restricted to this rank's columns with ctx.set_column_subset(column_partition(...))."""
+    rank, ws = world()
+    P = ctx.total_params
+    parts = ctx.metric_columns(theta)
+    owner = column_owners(P, ws)
+    L, sigma = gather_columns(parts["L"], parts["sigma"], owner)
+    out = ctx.step_from_parts(theta, L.reshape(-1), sigma, parts["grad"], dt, lam)
+    out["grad"], out["energy"] = parts["grad"], parts["energy"]
+    return out

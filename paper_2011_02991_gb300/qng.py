@@ -79,6 +79,10 @@ SYMBOLS = {
     "qng_set_path": [_vp, ctypes.c_int],
     "qng_stream_traffic": [_vp, _i64p, _i64p, _i64p],
     "qng_stream_segments": [_vp, _i64p, _i64p],
+    "qng_column_partition": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, ctypes.POINTER(ctypes.c_int)],
+    "qng_set_column_subset": [_vp, _i32p, ctypes.c_int],
+    "qng_metric_columns": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "qng_step_from_parts": [_vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp],
     "qng_graph_capture": [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp],
     "qng_graph_launch": [_vp],
     "qng_autotune": [_vp, _vp, ctypes.c_int, _i64p],
@@ -102,6 +106,14 @@ def _close_live_contexts():
             ctx.close()
         except Exception:
             pass
+
+
+def column_partition(P: int, ranks: int, rank: int) -> list[int]:
+    """The metric columns rank `rank` of `ranks` computes (qng_column_partition: balanced pairs)."""
+    cols = (ctypes.c_int32 * max(P, 1))()
+    n = ctypes.c_int()
+    _chk(load().qng_column_partition(int(P), int(ranks), int(rank), cols, ctypes.byref(n)), "qng_column_partition")
+    return [int(cols[k]) for k in range(n.value)]
 
 
 def load(path: str = LIB_PATH):
@@ -365,6 +377,37 @@ class Context:
 
     def set_tuning(self, min_qubits: int, cluster_log2: int, threads: int):
         _chk(load().qng_set_tuning(self._h, min_qubits, cluster_log2, threads), "qng_set_tuning")
+
+    # -- column partition (one instance over several ranks) -----------------------------------
+    def set_column_subset(self, cols=None):
+        """Restrict the metric recurrence to columns `cols` (0-based); None restores every column."""
+        L = load()
+        if cols is None:
+            _chk(L.qng_set_column_subset(self._h, None, -1), "qng_set_column_subset")
+            return
+        c = np.ascontiguousarray(np.asarray(cols, dtype=np.int32))
+        self._subset = c
+        _chk(L.qng_set_column_subset(self._h, c.ctypes.data_as(_i32p), int(c.size)), "qng_set_column_subset")
+
+    def metric_columns(self, theta):
+        """The subset's columns: dict(L (P x P, (1/4) Re L_ij for i < j of the subset's columns),
+        sigma (P), grad (P), energy (1)) as device tensors."""
+        theta = self._theta(theta)
+        P = self.total_params
+        out = {"L": self._f64(P * P), "sigma": self._f64(P), "grad": self._f64(P), "energy": self._f64(1)}
+        _chk(load().qng_metric_columns(self._h, _ptr(theta), _ptr(out["L"]), _ptr(out["sigma"]), _ptr(out["grad"]),
+                                       _ptr(out["energy"])), "qng_metric_columns")
+        return out
+
+    def step_from_parts(self, theta, L, sigma, grad, dt: float = 0.1, lam: float = 1e-3):
+        """Assembly and solve from gathered parts (device tensors): dict(dtheta, g)."""
+        theta = self._theta(theta)
+        P = self.total_params
+        out = {"dtheta": self._f64(P), "g": self._f64(P * P)}
+        L, sigma, grad = (t.to(self.device, torch.float64).contiguous() for t in (L, sigma, grad))
+        _chk(load().qng_step_from_parts(self._h, _ptr(theta), _ptr(L), _ptr(sigma), _ptr(grad), float(dt), float(lam),
+                                        _ptr(out["dtheta"]), _ptr(out["g"])), "qng_step_from_parts")
+        return out
 
     # kernel classes of qng_profile_read (include/qng.h); 4-7 are streaming-path segments
     KERNEL_CLASSES = ("coef", "forward", "columns", "finish", "energy", "hpsi", "adjoint", "reduce")

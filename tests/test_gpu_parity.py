@@ -656,3 +656,39 @@ def test_live_contexts_of_different_sizes(qng, oracle):
             assert rel(out["dtheta"].cpu(), ref["dtheta"]) <= TOL[W.C128], p.name
         ctx_stream.metric(ctx_stream.theta0())
         ctx_stream.sync()
+
+
+@pytest.mark.parametrize("ranks", [2, 3])
+@pytest.mark.parametrize("which", ["rand12", "random6"])
+def test_column_partition_onchip(qng, oracle, ranks, which):
+    """The column partition (Sec. 3, columns independent given psi_{j-1}) emulated on one GPU: each
+    rank's context computes its balanced column pairs (qng_set_column_subset, qng_metric_columns),
+    the parts are merged by owner as the all-gather would, and qng_step_from_parts gives the step.
+    Every column is computed by the same kernel whatever the subset, so g and dtheta equal the
+    unpartitioned step bit for bit."""
+    from paper_2011_02991_gb300 import dist as D
+    p = W.config_rand12() if which == "rand12" else W.random_problem(6, 80, 8, 6161)
+    full = qng.Context(p)
+    ref = full.step(full.theta0(), p.dt, p.lam)
+    full.sync()
+    owner = D.column_owners(p.P, ranks)
+    Ls, ss, grads = [], [], []
+    for r in range(ranks):
+        ctx = qng.Context(p)
+        ctx.set_column_subset(qng.column_partition(p.P, ranks, r))
+        with pytest.raises(qng.QngError):  # a subset context runs no whole metric
+            ctx.step(ctx.theta0(), p.dt, p.lam)
+        parts = ctx.metric_columns(ctx.theta0())
+        ctx.sync()
+        Ls.append(parts["L"])
+        ss.append(parts["sigma"])
+        grads.append(parts["grad"])
+        ctx.close()
+    L, sigma = D.merge_columns(Ls, ss, owner)
+    for g in grads[1:]:
+        assert torch.equal(g, grads[0])
+    out = full.step_from_parts(full.theta0(), L.reshape(-1), sigma, grads[0], p.dt, p.lam)
+    full.sync()
+    assert torch.equal(out["g"], ref["g"])
+    assert torch.equal(out["dtheta"], ref["dtheta"])
+    assert rel(out["g"].cpu(), oracle.qng_step(p)["g"]) <= TOL[W.C128]

@@ -113,3 +113,37 @@ def test_streaming_c64_matches_onchip_c64(qng, seed):
     assert rel(sb.cpu(), sa.cpu()) <= TOL[W.C64]
     assert rel(rb.cpu(), ra.cpu()) <= TOL[W.C64]
     assert rel(eb.cpu(), ea.cpu()) <= TOL[W.C64]
+
+
+@pytest.mark.parametrize("precision", [W.C128, W.C64])
+def test_column_partition_streaming(qng, oracle, precision):
+    """The column partition on the streaming path: a rank's schedule runs the recurrence for its
+    columns and only advances psi through the others' gates; merged, the parts give the same step
+    as the unpartitioned schedule (psi takes the same operations in either schedule)."""
+    from paper_2011_02991_gb300 import dist as D
+    n = 14 if precision == W.C128 else 13
+    rng = np.random.Generator(np.random.PCG64(515))
+    c = W.layered_ansatz(n, 2, rotation_kinds=(W.RY, W.RX, W.RZ), entangler=W.CNOT)
+    p = W.Problem("partition_stream", c, W.random_pauli_hamiltonian(n, 12, rng), W.uniform_theta(c.num_params, rng),
+                  precision=precision)
+    full = qng.Context(p, path=2)
+    ref = full.step(full.theta0(), p.dt, p.lam)
+    full.sync()
+    ranks = 3
+    owner = D.column_owners(p.P, ranks)
+    Ls, ss, grads = [], [], []
+    for r in range(ranks):
+        ctx = qng.Context(p, path=2)
+        ctx.set_column_subset(qng.column_partition(p.P, ranks, r))
+        parts = ctx.metric_columns(ctx.theta0())
+        ctx.sync()
+        Ls.append(parts["L"])
+        ss.append(parts["sigma"])
+        grads.append(parts["grad"])
+        ctx.close()
+    L, sigma = D.merge_columns(Ls, ss, owner)
+    out = full.step_from_parts(full.theta0(), L.reshape(-1), sigma, grads[0], p.dt, p.lam)
+    full.sync()
+    assert torch.equal(out["g"], ref["g"])
+    assert torch.equal(out["dtheta"], ref["dtheta"])
+    assert rel(out["g"].cpu(), oracle.qng_step(p)["g"]) <= TOL[precision]

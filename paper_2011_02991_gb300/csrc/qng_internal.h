@@ -105,6 +105,8 @@ struct DevCoef {
     double c, s, t, f;
     int32_t caseB;
     int32_t pad;
+    float cf, sf, tf;  // c, s, t rounded to float32 once here, for the complex64 kernels
+    int32_t pad2;
 };
 
 // Pointers into the workspace.

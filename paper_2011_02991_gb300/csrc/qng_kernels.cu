@@ -115,12 +115,21 @@ template <typename R, int CB> struct RotC {
 // adjoint (R^dag) or forward (R) coefficients of parameter k; f receives the scale factor
 template <typename R> __device__ __forceinline__ Rot<R> make_rot(const DevCoef &co, bool adjoint, double &f) {
     Rot<R> r;
-    const double sg = adjoint ? 1.0 : -1.0;
-    r.c = (R)co.c;
-    r.s = (R)(sg * co.s);
-    r.t = (R)(sg * co.t);
-    r.caseB = co.caseB;
-    f = co.caseB ? sg * co.f : co.f;
+    if constexpr (std::is_same<R, float>::value) {  // the float32 copies: no float64 work per step
+        const float sg = adjoint ? 1.0f : -1.0f;
+        r.c = co.cf;
+        r.s = sg * co.sf;
+        r.t = sg * co.tf;
+        r.caseB = co.caseB;
+        f = 1.0;  // complex64 registers carry no float64 factor
+    } else {
+        const double sg = adjoint ? 1.0 : -1.0;
+        r.c = (R)co.c;
+        r.s = (R)(sg * co.s);
+        r.t = (R)(sg * co.t);
+        r.caseB = co.caseB;
+        f = co.caseB ? sg * co.f : co.f;
+    }
     return r;
 }
 
@@ -676,6 +685,10 @@ __global__ void k_coef(const double *theta, DevCoef *coef, double *pctrl, int64_
     if (fabs(c) >= fabs(s)) { co.caseB = 0; co.f = c; co.t = s / c; }
     else                    { co.caseB = 1; co.f = s; co.t = c / s; }
     co.pad = 0;
+    co.cf = (float)co.c;
+    co.sf = (float)co.s;
+    co.tf = (float)co.t;
+    co.pad2 = 0;
     coef[k] = co;
 }
 
@@ -1021,11 +1034,19 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
     int cnt = 0;
     constexpr bool kScaled = std::is_same<R, double>::value;
     __shared__ int rn_flag[2];  // renormalise b after step s (written by thread 0, parity of s)
+    const uint32_t slice_bytes = e.Nl * (uint32_t)sizeof(cx);
     for (int s = 0; s < nsteps; ++s) {
         const int i = i0 - s;
         const DevParam pi = w.param[in.param_tab + i];
         const double sci = scales[i + 1];
         const cx *a = ckpt + (uint64_t)(i + 1) * N;
+        // the next step reads this CTA's slice of checkpoint i: start it towards L1 now, so the
+        // step after this one does not wait on L2
+        if (s + 1 < nsteps) {
+            const char *nxt = reinterpret_cast<const char *>(ckpt + (uint64_t)i * N + e.base);
+            for (uint32_t off = threadIdx.x * 128u; off < slice_bytes; off += blockDim.x * 128u)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + off));
+        }
         const bool rot_on = (i > 0);
         const bool gen = GEN && pi.axis == kAxisGen;  // generalised rotation: plain (cos, sin) form, factor 1
         double fs = 1.0;

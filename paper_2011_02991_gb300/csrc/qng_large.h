@@ -70,7 +70,13 @@ struct PassPhase {
     int8_t tbit[8];            // local bits of the thread index bits 0..7
     int32_t rmask;             // registers the phase reads or writes (gathered from the tile)
     int32_t wmask;             // registers the phase writes (scattered back)
+    int32_t macro;             // 0, or a straight-line form of the whole phase (kMacro* | axis << 4 | count)
 };
+// Straight-line phases: kMacroSteps, m recurrence steps (a, b, Re) on one axis with pair targets
+// at register bits 0..m-1 in order; kMacroCnot, m CNOTs on a and b with targets at register bits
+// 0..m-1 in order, the controls of the first m - 1 at register bits 1..m-1 and the last control a
+// thread-uniform bit.
+constexpr int32_t kMacroSteps = 1 << 8, kMacroCnot = 2 << 8;
 
 struct ReduceItem {
     int32_t slot;

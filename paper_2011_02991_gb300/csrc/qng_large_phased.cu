@@ -396,6 +396,49 @@ __device__ __forceinline__ int axis_variant(int ax, int kt, int dk) {
     return -1;
 }
 
+// Straight-line phases (PassPhase::macro): the whole phase is one basic block, so the compiler keeps
+// the amplitudes in place from step to step and nothing is decoded per operation.
+template <int AX, int K, int M>
+__device__ __forceinline__ void steps_run(Regs &X, const OpD *d, float *part, int lane, int tid) {
+    if constexpr (K < M) {
+        const OpD o = d[K];
+        float re = 0.0f, im = 0.0f;
+        step_pairs<1, 2, 0, true, K, AX>(X, o.a, o.b, re, im);
+        re += __shfl_xor_sync(0xffffffffu, re, 1);
+        if (!(lane & 1)) part[o.slot * (kNT / 2) + (tid >> 1)] = re;
+        steps_run<AX, K + 1, M>(X, d, part, lane, tid);
+    }
+}
+template <int AX>
+__device__ __forceinline__ void macro_steps(Regs &X, int m, const OpD *d, float *part, int lane, int tid) {
+    switch (m) {
+    case 1: steps_run<AX, 0, 1>(X, d, part, lane, tid); break;
+    case 2: steps_run<AX, 0, 2>(X, d, part, lane, tid); break;
+    case 3: steps_run<AX, 0, 3>(X, d, part, lane, tid); break;
+    default: steps_run<AX, 0, 4>(X, d, part, lane, tid); break;
+    }
+}
+template <int K, int M> __device__ __forceinline__ void cnots_run(Regs &X, uint32_t ulast) {
+    if constexpr (K < M) {
+        if constexpr (K < M - 1) {
+            cnot_pairs<1, K, K + 1>(X);
+            cnot_pairs<2, K, K + 1>(X);
+        } else if (ulast) {
+            cnot_pairs<1, K, -1>(X);
+            cnot_pairs<2, K, -1>(X);
+        }
+        cnots_run<K + 1, M>(X, ulast);
+    }
+}
+__device__ __forceinline__ void macro_cnots(Regs &X, int m, uint32_t ulast) {
+    switch (m) {
+    case 1: cnots_run<0, 1>(X, ulast); break;
+    case 2: cnots_run<0, 2>(X, ulast); break;
+    case 3: cnots_run<0, 3>(X, ulast); break;
+    default: cnots_run<0, 4>(X, ulast); break;
+    }
+}
+
 // S: stages of the shared-memory tile ring; PSI: the pass touches register psi (passes of the
 // metric columns do not, and their instantiation keeps only a and b in registers)
 template <int S, bool PSI>
@@ -608,11 +651,6 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
         return;
     }
 
-    Regs X;
-#pragma unroll
-    for (int r = 0; r < kRegs; ++r)
-#pragma unroll
-        for (int m = 0; m < kA; ++m) X[r][m] = make_float2(0.0f, 0.0f);
     double dacc[kMaxSlots / kNW];  // lane 0 of warp w: running float64 sums of slots w, w + 8, ...
 #pragma unroll
     for (int k = 0; k < kMaxSlots / kNW; ++k) dacc[k] = 0.0;
@@ -635,13 +673,26 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
                                   wpos(1u << P.rbit[3])};
             const bool vm = P.rbit[0] == 0;
             const int rm = P.rmask & pd.regmask, wm = P.wmask & pd.regmask;
+            // the phase's registers: every phase gathers the ones it touches and scatters the ones it
+            // writes, so nothing is carried from one phase (or tile) to the next in registers
+            Regs X;
             if (PSI && (rm & 1)) gather<0>(X, reinterpret_cast<const float2 *>(stage_reg(stage, 0)), ad, vm);
             if (rm & 2) gather<1>(X, reinterpret_cast<const float2 *>(stage_reg(stage, 1)), ad, vm);
             if (rm & 4) gather<2>(X, reinterpret_cast<const float2 *>(stage_reg(stage, 2)), ad, vm);
             // global index of the thread's amplitude m = 0: the bit of every qubit that is not a
             // register bit is the same for the thread's 16 amplitudes
             const uint64_t gl = base | rowoff[tl >> 5] | (tl & 31u);
-            for (int o = P.op_begin; o < P.op_end; ++o) {
+            if (P.macro) {
+                const int m = P.macro & 15;
+                if ((P.macro & ~0xFF) == kMacroSteps) {
+                    if (((P.macro >> 4) & 15) == kAxisX) macro_steps<kAxisX>(X, m, opd + P.op_begin, part, lane, tid);
+                    else macro_steps<kAxisY>(X, m, opd + P.op_begin, part, lane, tid);
+                } else {
+                    const int q = opd[P.op_begin + m - 1].q0u;
+                    macro_cnots(X, m, q < 0 ? 1u : (uint32_t)(gl >> q) & 1u);
+                }
+            }
+            for (int o = P.macro ? P.op_end : P.op_begin; o < P.op_end; ++o) {
                 const OpD d = opd[o];
                 // the thread-uniform bits of q0 / q1, for the variants that read them
                 auto ubit = [&](int q) -> uint32_t { return q < 0 ? 1u : (uint32_t)(gl >> q) & 1u; };

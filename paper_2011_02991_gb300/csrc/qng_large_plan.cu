@@ -88,6 +88,24 @@ int pair_target(const PassOp &o) {
 // one local bit of each class.
 int bank_class(int b) { return b == 0 ? 3 : (b - 1) % 3; }
 
+// The straight-line form of operations [i, j) of a phase (PassPhase::macro), or 0.
+int32_t macro_form(const std::vector<PassOp> &ops, size_t i, size_t j) {
+    const int m = (int)(j - i);
+    if (m < 1 || m > 4) return 0;
+    bool steps = true, cnots = true;
+    const int ax = ops[i].axis;
+    for (int k = 0; k < m; ++k) {
+        const PassOp &o = ops[i + k];
+        steps = steps && o.kind == kOpStep && o.r0 == kRegA && o.r1 == kRegB && o.adjoint == 0 && o.axis == ax &&
+                (ax == kAxisX || ax == kAxisY) && o.kt == k;
+        cnots = cnots && o.kind == kOpFixed && o.fixed_kind == QNG_GATE_CNOT && o.regs == ((1 << kRegA) | (1 << kRegB)) &&
+                o.kt == k && (k < m - 1 ? o.dk0 == k + 1 : o.dk0 < 0);
+    }
+    if (steps) return kMacroSteps | (ax << 4) | m;
+    if (cnots) return kMacroCnot | m;
+    return 0;
+}
+
 // Split a pass's operations into register phases (see PassPhase): a phase takes operations while
 // their pair targets fit in four register bits. ops are annotated with their register positions.
 // Returns false when the pass needs more than kMaxPhases phases.
@@ -157,6 +175,7 @@ bool make_phases(const PassDesc &pd, std::vector<PassOp> &ops, std::vector<PassP
         }
         p.rmask = rm;
         p.wmask = wm;
+        p.macro = macro_form(ops, i, j);
         ph.push_back(p);
         if ((int)ph.size() > kMaxPhases) {
             *fit_ops = (size_t)ph[kMaxPhases].op_begin;

@@ -125,11 +125,12 @@ struct qng_ctx {
     int tune_min_qubits = 0, tune_cl = -1, tune_threads = 0;
     int path = 0;             // 0 automatic, 1 on-chip, 2 streaming
     std::vector<uint8_t> col_want;  // column subset of a single instance (empty: every column)
+    std::vector<int> group_order;   // launch groups by decreasing work
     // streaming path (one instance, registers in HBM)
     bool streaming = false;
     large::Schedule sched;
     int l_grid = 0;
-    size_t o_reg[large::kRegs] = {0, 0, 0};
+    size_t o_reg[large::kRegs] = {0, 0, 0, 0};
     size_t o_regscale = 0, o_partial = 0, o_slotfac = 0, o_pdesc = 0, o_pops = 0, o_red = 0, o_phases = 0;
     size_t o_queue = 0;
     // mixed-precision solve: cluster size (0 = not used: P < 48 or its float32 matrix does not fit)
@@ -312,7 +313,8 @@ qng_status plan_streaming(qng_ctx *c, int64_t scale_n) {
     c->o_pops = take(sizeof(large::PassOp) * std::max<size_t>(c->sched.ops.size(), 1));
     c->o_phases = take(sizeof(large::PassPhase) * std::max<size_t>(c->sched.phases.size(), 1));
     c->o_red = take(sizeof(large::ReduceItem) * std::max<size_t>(c->sched.reds.size(), 1));
-    for (int r = 0; r < large::kRegs; ++r) c->o_reg[r] = take(ab << h.n);
+    // b2 only for a schedule whose metric columns walk in pairs
+    for (int r = 0; r < large::kRegs; ++r) c->o_reg[r] = (r != large::kRegB2 || c->sched.pairs) ? take(ab << h.n) : 0;
     c->o_ckpt = c->o_eta = 0;
     c->ws_bytes = align256(off);
     c->groups.clear();
@@ -591,7 +593,7 @@ qng_status upload(qng_ctx *c) {
             items[k].dst = reinterpret_cast<double *>(c->ws + region) + r.index;
         }
         if ((e = put(c->o_red, items.data(), sizeof(large::ReduceItem) * items.size())) != cudaSuccess) return cuda_status(e);
-        static const double ones[2 * large::kRegs] = {1, 1, 1, 1, 1, 1};
+        static const double ones[2 * large::kRegs] = {1, 1, 1, 1, 1, 1, 1, 1};
         if ((e = put(c->o_regscale, ones, sizeof(ones))) != cudaSuccess) return cuda_status(e);
         size_t pass_smem = 0;
         for (const large::PassDesc &pd : S.passes)
@@ -616,9 +618,9 @@ qng_status upload(qng_ctx *c) {
     if (scl >= 0 && (e = prepare_solve(solve_smem_bytes(c->max_P, scl))) != cudaSuccess) return cuda_status(e);
     if (c->bsolve && (e = prepare_sblock(c->inst[0].P, c->bs_C)) != cudaSuccess) return cuda_status(e);
     if (c->ir_C > 0 && (e = prepare_solve_ir(c->max_P, c->ir_C)) != cudaSuccess) return cuda_status(e);
-    // single instance: streams and events of the pipelined sweep, made here so that no stream is
-    // created inside a graph capture
-    if (c->count == 1 && !c->pipe_ready) {
+    // streams and events of the pipelined sweep (single instance) and of the launch groups side by
+    // side (batches), made here so that no stream is created inside a graph capture
+    if (!c->pipe_ready) {
         int lo = 0, hi = 0;
         if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return cuda_status(e);
         if ((e = cudaStreamCreateWithPriority(&c->pipe_fwd, cudaStreamNonBlocking, hi)) != cudaSuccess) return cuda_status(e);
@@ -630,6 +632,20 @@ qng_status upload(qng_ctx *c) {
                 return cuda_status(e);
         }
         c->pipe_ready = true;
+    }
+    // launch groups, most work first (they run side by side on their own streams)
+    c->group_order.resize(c->groups.size());
+    for (size_t k = 0; k < c->groups.size(); ++k) c->group_order[k] = (int)k;
+    {
+        std::vector<double> work(c->groups.size(), 0.0);
+        for (size_t k = 0; k < c->groups.size(); ++k) {
+            const Group &g = c->groups[k];
+            for (int t = 0; t < g.num_inst; ++t) {
+                const HostInst &h = c->inst[c->t_group_inst[g.first_inst + t]];
+                work[k] += (double)h.P * h.P * (double)(1ll << h.n);
+            }
+        }
+        std::stable_sort(c->group_order.begin(), c->group_order.end(), [&](int a, int b) { return work[a] > work[b]; });
     }
     // batched contexts: persistent column launches fed by a device work counter per group
     for (size_t k = 0; k < c->groups.size(); ++k) {
@@ -720,7 +736,7 @@ qng_status run_streaming(qng_ctx *c, int jobs, int64_t &launches) {
     large::PassArgs pa = {};
     pa.ops = reinterpret_cast<const large::PassOp *>(c->ws + c->o_pops);
     pa.coef = reinterpret_cast<const DevCoef *>(c->ws + c->o_coef);
-    for (int r = 0; r < large::kRegs; ++r) pa.reg[r] = c->ws + c->o_reg[r];
+    for (int r = 0; r < large::kRegs; ++r) pa.reg[r] = (r != large::kRegB2 || S.pairs) ? c->ws + c->o_reg[r] : nullptr;
     pa.regscale = reinterpret_cast<double *>(c->ws + c->o_regscale);
     pa.partial = reinterpret_cast<double *>(c->ws + c->o_partial);
     pa.slotfac = reinterpret_cast<double *>(c->ws + c->o_slotfac);
@@ -834,7 +850,36 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
             if ((e = cudaStreamWaitEvent(c->stream, c->pipe_evc[s], 0)) != cudaSuccess) return cuda_status(e);
             launches += 1;
         }
-    } else if (!(jobs & kJobFromParts)) {
+    }
+    // batches: each launch group's sweep and columns on a stream of its own, most work first, so that
+    // the groups fill one another's tails; joined before the solve. Automatic for complex128, whose
+    // float64-bound groups leave the SMs room (batch256: 198 -> 172 ms per step); complex64 runs the
+    // groups in turn, which measured as fast or faster (47.2 against 49.1 ms). qng_set_pipeline(ctx, 1)
+    // runs them in turn, 2..8 side by side.
+    const bool side_by_side = !S && !(jobs & kJobFromParts) && !c->streaming && c->count > 1 && c->pipe_ready &&
+                              c->groups.size() > 1 && c->groups.size() <= (size_t)kPipeMax &&
+                              (c->pipe_req >= 2 || (c->pipe_req == 0 && c->precision == QNG_C128));
+    if (side_by_side) {
+        if ((e = cudaEventRecord(c->pipe_ev0, c->stream)) != cudaSuccess) return cuda_status(e);
+        for (size_t idx = 0; idx < c->group_order.size(); ++idx) {
+            const Group &g = c->groups[c->group_order[idx]];
+            if (g.num_inst == 0) continue;
+            cudaStream_t gs = idx == 0 ? c->stream : c->pipe_col[idx];
+            if (idx > 0 && (e = cudaStreamWaitEvent(gs, c->pipe_ev0, 0)) != cudaSuccess) return cuda_status(e);
+            e = timed_on(c, 1, gs, [&] { return launch_forward(w, g, c->precision, want_eta, gs); });
+            if (e != cudaSuccess) return cuda_status(e);
+            launches += 1;
+            if (need_cols && (wm && wg ? g.num_work : (wm ? g.num_met : g.num_grad)) > 0) {
+                e = timed_on(c, 2, gs, [&] { return launch_columns(w, g, c->precision, wm, wg, wim, gs); });
+                if (e != cudaSuccess) return cuda_status(e);
+                launches += 1;
+            }
+            if (idx > 0) {
+                if ((e = cudaEventRecord(c->pipe_evc[idx], gs)) != cudaSuccess) return cuda_status(e);
+                if ((e = cudaStreamWaitEvent(c->stream, c->pipe_evc[idx], 0)) != cudaSuccess) return cuda_status(e);
+            }
+        }
+    } else if (!S && !(jobs & kJobFromParts)) {
         for (const Group &g : c->groups) {
             if (g.num_inst == 0) continue;
             e = timed(c, 1, [&] { return launch_forward(w, g, c->precision, want_eta, c->stream); });
@@ -844,7 +889,7 @@ qng_status run(qng_ctx *c, int jobs, const LaunchArgs &args) {
     }
     LaunchArgs a = args;
     a.jobs = jobs;
-    if (need_cols && !S) {
+    if (need_cols && !S && !side_by_side) {
         for (const Group &g : c->groups) {
             if ((wm && wg ? g.num_work : (wm ? g.num_met : g.num_grad)) == 0) continue;
             e = timed(c, 2, [&] { return launch_columns(w, g, c->precision, wm, wg, wim, c->stream); });
@@ -1327,6 +1372,19 @@ qng_status qng_autotune(qng_ctx *c, const double *theta, int reps, int64_t *repo
         float best = 3.4e38f;
         int best_req = c->pipe_req;
         for (int req : {1, 2, 3, 4}) {
+            c->pipe_req = req;
+            float ms = 0.f;
+            if ((st = time_step(ms)) != QNG_OK) break;
+            ++tried;
+            if (ms < best) { best = ms; best_req = req; }
+        }
+        c->pipe_req = best_req;
+    }
+    // a batch of several launch groups: the groups in turn (1) or side by side on their own streams (2)
+    if (st == QNG_OK && c->count > 1 && (st = plan(c)) == QNG_OK && (st = upload(c)) == QNG_OK && c->groups.size() > 1) {
+        float best = 3.4e38f;
+        int best_req = c->pipe_req;
+        for (int req : {1, 2}) {
             c->pipe_req = req;
             float ms = 0.f;
             if ((st = time_step(ms)) != QNG_OK) break;

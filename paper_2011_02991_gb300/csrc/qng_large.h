@@ -9,10 +9,10 @@
 namespace qng {
 namespace large {
 
-constexpr int kRegs = 3;      // register slots: 0 psi, 1 a (lambda / eta), 2 b (phi)
+constexpr int kRegs = 4;      // register slots: 0 psi, 1 a (lambda / eta), 2 b (phi), 3 b2 (a second phi)
 constexpr int kMaxWin = 7;    // tile qubits beyond the contiguous low block
 constexpr int kMaxSlots = 32; // inner products per pass
-constexpr int kRegPsi = 0, kRegA = 1, kRegB = 2;
+constexpr int kRegPsi = 0, kRegA = 1, kRegB = 2, kRegB2 = 3;
 
 enum OpKind : int32_t {
     kOpCopy = 0,       // r1 <- r0
@@ -26,6 +26,10 @@ enum OpKind : int32_t {
     kOpStep = 8,       // one recurrence step in one sweep: slot += Re/Im <r0|sigma_{axis}(q0)|r1> (adjoint
                        // 0/1; 2: Re into slot and Im into slot + 1), then, if param >= 0, the adjoint
                        // rotation of param (same axis and qubit) on r0 and r1
+    kOpStep2 = 9,      // the step of two columns that share a (registers a, b and b2): Re <a|sigma|b> into
+                       // slot and Re <a|sigma|b2> into slot + 1 (adjoint 0), or Re, Im of the first into
+                       // slot, slot + 1 and of the second into slot + 2, slot + 3 (adjoint 2); then the
+                       // adjoint rotation on a, b and b2 (register-phase kernel only)
 };
 
 struct PassOp {
@@ -40,8 +44,10 @@ struct PassOp {
     int32_t slot;
     // register-phase kernel (complex64 tiles of 2^12): position 0..3 among the phase's register
     // bits of the op's non-diagonal target qubit (kt), and of q0 / q1 where a diagonal part reads
-    // their bit (dk0 / dk1); -1 where the qubit is not a register bit of the phase
-    int8_t kt, dk0, dk1, pad8;
+    // their bit (dk0 / dk1); -1 where the qubit is not a register bit of the phase.
+    // zrun: the op starts a run of diagonal operations on a and b that the kernel composes (its
+    // length, plus kZrunIm when the run's steps take Im as well), -1 inside such a run, 0 otherwise
+    int8_t kt, dk0, dk1, zrun;
 };
 
 struct PassDesc {
@@ -77,6 +83,12 @@ struct PassPhase {
 // 0..m-1 in order, the controls of the first m - 1 at register bits 1..m-1 and the last control a
 // thread-uniform bit.
 constexpr int32_t kMacroSteps = 1 << 8, kMacroCnot = 2 << 8;
+// kMacroSteps2: the same with steps of two columns (kOpStep2, Re).
+constexpr int32_t kMacroSteps2 = 3 << 8;
+// Runs of diagonal operations (PassOp::zrun): Z-axis recurrence steps and CZ / Z gates, either all on
+// (a, b) or all on (a, b, b2) (kZrunDual), at least two steps, at most kMaxZrun operations, all steps
+// Re (adjoint 0) or all Re and Im (2, kZrunIm).
+constexpr int kMaxZrun = 31, kZrunIm = 32, kZrunDual = 64;
 
 struct ReduceItem {
     int32_t slot;
@@ -135,6 +147,7 @@ struct RedSpec {
 struct Schedule {
     int n = 0, t = 0, low = 0;
     bool phased = false;  // complex64 with tiles of 2^12: the register-phase kernel runs every pass
+    bool pairs = false;   // metric columns walk in pairs sharing a (register b2 in use)
     std::vector<PassDesc> passes;
     std::vector<PassOp> ops;
     std::vector<PassPhase> phases;

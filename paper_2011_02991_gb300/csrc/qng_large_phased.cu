@@ -59,7 +59,8 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-typedef float2 Regs[kRegs][kA];
+// the registers a phase holds: slot 0 psi (passes that touch psi) or b2 (passes that do not), 1 a, 2 b
+typedef float2 Regs[3][kA];
 
 // ---- data movement between the shared-memory tile and the registers of a phase ----------------
 // Word of amplitude m: P0 ^ (e0 if bit 0 of m) ^ (e1 if bit 1) ^ ..., the swizzled positions of the
@@ -183,6 +184,82 @@ __device__ __forceinline__ void step_diag(Regs &X, float a, float b, float &re, 
         }
     }
 }
+// The step of two columns sharing a: inner products <a|sigma|b> and <a|sigma|b2> (b2 in slot 0), then,
+// when ROT, the rotation on a, b and b2. acc: Re ab, Im ab, Re ab2, Im ab2 (Im only for IM 2).
+template <int IM, bool ROT, int K, int AX>
+__device__ __forceinline__ void step2_pairs(Regs &X, float a, float b, float (&acc)[4]) {
+    float pr[2] = {0.0f, 0.0f}, pi[2] = {0.0f, 0.0f}, qr[2] = {0.0f, 0.0f}, qi[2] = {0.0f, 0.0f};
+    int j = 0;
+#pragma unroll
+    for (int m0 = 0; m0 < kA; ++m0) {
+        if (m0 & (1 << K)) continue;
+        const int m1 = m0 | (1 << K);
+        const float2 a0 = X[1][m0], a1 = X[1][m1], b0 = X[2][m0], b1 = X[2][m1], c0 = X[0][m0], c1 = X[0][m1];
+        float2 s0, s1, t0, t1;  // sigma b, sigma b2 at m0, m1
+        if (AX == kAxisX) { s0 = b1; s1 = b0; t0 = c1; t1 = c0; }
+        else {
+            s0 = make_float2(b1.y, -b1.x); s1 = make_float2(-b0.y, b0.x);
+            t0 = make_float2(c1.y, -c1.x); t1 = make_float2(-c0.y, c0.x);
+        }
+        pr[j & 1] = fmaf(a0.x, s0.x, fmaf(a0.y, s0.y, fmaf(a1.x, s1.x, fmaf(a1.y, s1.y, pr[j & 1]))));
+        qr[j & 1] = fmaf(a0.x, t0.x, fmaf(a0.y, t0.y, fmaf(a1.x, t1.x, fmaf(a1.y, t1.y, qr[j & 1]))));
+        if (IM == 2) {
+            pi[j & 1] = fmaf(a0.x, s0.y, fmaf(-a0.y, s0.x, fmaf(a1.x, s1.y, fmaf(-a1.y, s1.x, pi[j & 1]))));
+            qi[j & 1] = fmaf(a0.x, t0.y, fmaf(-a0.y, t0.x, fmaf(a1.x, t1.y, fmaf(-a1.y, t1.x, qi[j & 1]))));
+        }
+        ++j;
+    }
+    const float r1 = pr[0] + pr[1], r2 = qr[0] + qr[1];
+    acc[0] += r1;
+    acc[2] += r2;
+    if (IM == 2) {
+        acc[1] += pi[0] + pi[1];
+        acc[3] += qi[0] + qi[1];
+    }
+    if (ROT) {
+        after(a, b, r1, r2);
+#pragma unroll
+        for (int m0 = 0; m0 < kA; ++m0) {
+            if (m0 & (1 << K)) continue;
+            const int m1 = m0 | (1 << K);
+            rot_pair<AX>(X[1][m0], X[1][m1], a, b);
+            rot_pair<AX>(X[2][m0], X[2][m1], a, b);
+            rot_pair<AX>(X[0][m0], X[0][m1], a, b);
+        }
+    }
+}
+template <int IM, bool ROT, uint32_t PT>
+__device__ __forceinline__ void step2_diag(Regs &X, float a, float b, float (&acc)[4]) {
+    float pr[2] = {0.0f, 0.0f}, pi[2] = {0.0f, 0.0f}, qr[2] = {0.0f, 0.0f}, qi[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int m = 0; m < kA; ++m) {
+        const bool sb = ((PT >> m) & 1u) != 0;
+        const float2 av = X[1][m], bv = X[2][m], cv = X[0][m];
+        const float2 af = sb ? make_float2(-av.x, -av.y) : av;
+        pr[m & 1] = fmaf(af.x, bv.x, fmaf(af.y, bv.y, pr[m & 1]));
+        qr[m & 1] = fmaf(af.x, cv.x, fmaf(af.y, cv.y, qr[m & 1]));
+        if (IM == 2) {
+            pi[m & 1] = fmaf(af.x, bv.y, fmaf(-af.y, bv.x, pi[m & 1]));
+            qi[m & 1] = fmaf(af.x, cv.y, fmaf(-af.y, cv.x, qi[m & 1]));
+        }
+    }
+    const float r1 = pr[0] + pr[1], r2 = qr[0] + qr[1];
+    acc[0] += r1;
+    acc[2] += r2;
+    if (IM == 2) {
+        acc[1] += pi[0] + pi[1];
+        acc[3] += qi[0] + qi[1];
+    }
+    if (ROT) {
+        after(a, b, r1, r2);
+#pragma unroll
+        for (int m = 0; m < kA; ++m) {
+            if ((PT >> m) & 1u) { rot_amp<true>(X[1][m], a, b); rot_amp<true>(X[2][m], a, b); rot_amp<true>(X[0][m], a, b); }
+            else                { rot_amp<false>(X[1][m], a, b); rot_amp<false>(X[2][m], a, b); rot_amp<false>(X[0][m], a, b); }
+        }
+    }
+}
+
 // rotation of register R about axis AX (X or Y) on register bit K
 template <int R, int K, int AX> __device__ __forceinline__ void rot_pairs(Regs &X, float a, float b) {
 #pragma unroll
@@ -295,6 +372,28 @@ __device__ __forceinline__ void step_av(Regs &X, int av, float a, float b, uint3
     }
 }
 
+template <int IM>
+__device__ __forceinline__ void step2_av(Regs &X, int av, float a, float b, uint32_t u0, float (&acc)[4]) {
+    switch (av) {
+#define QNG_SP2(K, AX) step2_pairs<IM, true, K, AX>(X, a, b, acc); break;
+    case 0: QNG_SP2(0, kAxisX) case 1: QNG_SP2(1, kAxisX) case 2: QNG_SP2(2, kAxisX) case 3: QNG_SP2(3, kAxisX)
+    case 4: QNG_SP2(0, kAxisY) case 5: QNG_SP2(1, kAxisY) case 6: QNG_SP2(2, kAxisY) case 7: QNG_SP2(3, kAxisY)
+#undef QNG_SP2
+    case 8: {  // Z on a thread-uniform bit: its sign goes into the angle and the inner products
+        float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        step2_diag<IM, true, 0u>(X, u0 ? -a : a, u0 ? -b : b, t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += u0 ? -t[k] : t[k];
+        break;
+    }
+    case 9: step2_diag<IM, true, pat<0>()>(X, a, b, acc); break;
+    case 10: step2_diag<IM, true, pat<1>()>(X, a, b, acc); break;
+    case 11: step2_diag<IM, true, pat<2>()>(X, a, b, acc); break;
+    case 12: step2_diag<IM, true, pat<3>()>(X, a, b, acc); break;
+    default: break;
+    }
+}
+
 template <int R> __device__ __forceinline__ void rot_av(Regs &X, int av, float a, float b, uint32_t u0) {
     switch (av) {
     case 0: rot_pairs<R, 0, kAxisX>(X, a, b); break;
@@ -376,16 +475,20 @@ __device__ __forceinline__ void set_status(int32_t *status, int code) {
 // An operation of the pass, decoded once per CTA: one 16-byte shared-memory load.
 struct __align__(16) OpD {
     uint8_t cat;    // kCat*
-    uint8_t sub;    // step: register combo (0 (a, b, Re), 1 (a, b, Re and Im), 2 (psi, a, Im)); fixed: fv
+    uint8_t sub;    // step: register combo (0 (a, b, Re), 1 (a, b, Re and Im), 2 (psi, a, Im)); step of two
+                    // columns: 0 Re, 1 Re and Im; inner product, sigma: 0 on b, 1 on b2; fixed: fv
     uint8_t var;    // step, rotation, inner product, sigma: av
     uint8_t regs;   // fixed gate: register mask
     int8_t q0u, q1u;  // qubit whose thread-uniform bit the variant reads, or -1 (a register bit: 1)
     uint8_t slot;
-    uint8_t pad;
+    uint8_t pad;      // first operation of a diagonal run: PassOp::zrun, else 0
     float a, b;     // rotation: tan(phi / 2), sin(phi) of its plane rotations (see shear3)
 };
 static_assert(sizeof(OpD) == 16, "one 16-byte shared-memory load per operation");
-enum : uint8_t { kCatNop = 0, kCatCopyA, kCatCopyB, kCatZero, kCatStep, kCatIp, kCatRot, kCatSigma, kCatFixed, kCatBad };
+enum : uint8_t {
+    kCatNop = 0, kCatCopyA, kCatCopyB, kCatZero, kCatStep, kCatIp, kCatRot, kCatSigma, kCatFixed, kCatStep2, kCatCopyAB2,
+    kCatBad
+};
 
 // axis variant (see the numbering above) of an operation on axis ax with pair target kt and the
 // diagonal qubit at register position dk
@@ -438,6 +541,184 @@ __device__ __forceinline__ void macro_cnots(Regs &X, int m, uint32_t ulast) {
     default: cnots_run<0, 4>(X, ulast); break;
     }
 }
+// the same two forms for the steps of two columns and for CNOTs on b2 as well (slot 0)
+template <int AX, int K, int M>
+__device__ __forceinline__ void steps2_run(Regs &X, const OpD *d, float *part, int lane, int tid) {
+    if constexpr (K < M) {
+        const OpD o = d[K];
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        step2_pairs<0, true, K, AX>(X, o.a, o.b, acc);
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+        acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], 1);
+        if (!(lane & 1)) {
+            part[o.slot * (kNT / 2) + (tid >> 1)] = acc[0];
+            part[(o.slot + 1) * (kNT / 2) + (tid >> 1)] = acc[2];
+        }
+        steps2_run<AX, K + 1, M>(X, d, part, lane, tid);
+    }
+}
+template <int AX>
+__device__ __forceinline__ void macro_steps2(Regs &X, int m, const OpD *d, float *part, int lane, int tid) {
+    switch (m) {
+    case 1: steps2_run<AX, 0, 1>(X, d, part, lane, tid); break;
+    case 2: steps2_run<AX, 0, 2>(X, d, part, lane, tid); break;
+    case 3: steps2_run<AX, 0, 3>(X, d, part, lane, tid); break;
+    default: steps2_run<AX, 0, 4>(X, d, part, lane, tid); break;
+    }
+}
+template <int K, int M> __device__ __forceinline__ void cnots3_run(Regs &X, uint32_t ulast) {
+    if constexpr (K < M) {
+        if constexpr (K < M - 1) {
+            cnot_pairs<1, K, K + 1>(X);
+            cnot_pairs<2, K, K + 1>(X);
+            cnot_pairs<0, K, K + 1>(X);
+        } else if (ulast) {
+            cnot_pairs<1, K, -1>(X);
+            cnot_pairs<2, K, -1>(X);
+            cnot_pairs<0, K, -1>(X);
+        }
+        cnots3_run<K + 1, M>(X, ulast);
+    }
+}
+__device__ __forceinline__ void macro_cnots3(Regs &X, int m, uint32_t ulast) {
+    switch (m) {
+    case 1: cnots3_run<0, 1>(X, ulast); break;
+    case 2: cnots3_run<0, 2>(X, ulast); break;
+    case 3: cnots3_run<0, 3>(X, ulast); break;
+    default: cnots3_run<0, 4>(X, ulast); break;
+    }
+}
+
+// ---- runs of diagonal operations (PassOp::zrun) ------------------------------------------------
+// Z-axis recurrence steps on (a, b) and CZ / Z gates on a and b commute with one another, so every
+// step's inner product <a|Z_q|b> equals the one on the run's starting registers, and the run's
+// adjoint rotations (cos + i sin Z) and signs compose into one factor per amplitude. For the
+// thread's amplitude m that factor is U times, for each register bit k, R_k (bit k of m clear) or its
+// conjugate (set), times the sign of the run's gates at m: U collects the rotations on qubits whose
+// bit is the same for all 16 amplitudes, R_k those on register bit k. The composed factors are exact
+// (cos, sin) products, so a run leaves the registers' float64 signs as they were.
+__device__ __forceinline__ float2 cmul(float2 x, float2 y) {
+    return make_float2(fmaf(x.x, y.x, -(x.y * y.y)), fmaf(x.x, y.y, x.y * y.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 x, float2 y) {  // x conj(y)
+    return make_float2(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
+}
+// T = sum of v, W[k] = sum over m of (-1)^(bit k of m) v[m]: a butterfly over the four register bits
+__device__ __forceinline__ void walsh4(const float (&v)[kA], float &T, float (&W)[4]) {
+    float e1[8], e2[4], w0a = 0.0f, w0b = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        e1[i] = v[2 * i] + v[2 * i + 1];
+        if (i & 1) w0b += v[2 * i] - v[2 * i + 1];
+        else       w0a += v[2 * i] - v[2 * i + 1];
+    }
+    float w1 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        e2[i] = e1[2 * i] + e1[2 * i + 1];
+        w1 += e1[2 * i] - e1[2 * i + 1];
+    }
+    const float e30 = e2[0] + e2[1], e31 = e2[2] + e2[3];
+    W[0] = w0a + w0b;
+    W[1] = w1;
+    W[2] = (e2[0] - e2[1]) + (e2[2] - e2[3]);
+    W[3] = e30 - e31;
+    T = e30 + e31;
+}
+// sign pattern (bit m: amplitude m changes sign) of a CZ (fv 0..10) or Z (fv 11..15) gate
+__device__ __forceinline__ uint32_t diag_mask(int fv, uint32_t u0, uint32_t u1) {
+    if (fv <= 10) {
+        uint32_t p = 0xFFFFu;
+        switch (fv) {
+#define QNG_CZP(F) case F: p = cz_pattern(F); break;
+        QNG_CZP(1) QNG_CZP(2) QNG_CZP(3) QNG_CZP(4) QNG_CZP(5) QNG_CZP(6) QNG_CZP(7) QNG_CZP(8) QNG_CZP(9) QNG_CZP(10)
+#undef QNG_CZP
+        default: break;
+        }
+        return (u0 & u1) ? p : 0u;
+    }
+    if (fv == 11) return u0 ? 0xFFFFu : 0u;
+    return fv == 12 ? pat<0>() : (fv == 13 ? pat<1>() : (fv == 14 ? pat<2>() : pat<3>()));
+}
+// Inner products of a run with register R (b in slot 2, b2 in slot 0): T, W of Re conj(a) b and, for
+// IM 2, of Im conj(a) b.
+template <int R, int IM>
+__device__ __forceinline__ void zsums(const Regs &X, float &T, float (&W)[4], float &Ti, float (&Wi)[4]) {
+    float v[kA];
+#pragma unroll
+    for (int m = 0; m < kA; ++m) v[m] = fmaf(X[1][m].x, X[R][m].x, X[1][m].y * X[R][m].y);
+    walsh4(v, T, W);
+    if (IM == 2) {
+#pragma unroll
+        for (int m = 0; m < kA; ++m) v[m] = fmaf(X[1][m].x, X[R][m].y, -(X[1][m].y * X[R][m].x));
+        walsh4(v, Ti, Wi);
+    }
+}
+__device__ __forceinline__ float zpick(int k, uint32_t u0, float T, const float (&W)[4]) {
+    return k == 0 ? W[0] : (k == 1 ? W[1] : (k == 2 ? W[2] : (k == 3 ? W[3] : (u0 ? -T : T))));
+}
+// IM 0: each step's Re into its slot; IM 2: Re into its slot and Im into the next. DUAL: steps of two
+// columns (b and b2), their values in the order of kOpStep2's slots.
+template <int IM, bool DUAL>
+__device__ __forceinline__ void zrun(Regs &X, const OpD *d, int len, uint64_t gl, float *part, int lane, int tid) {
+    float T, W[4], Ti = 0.0f, Wi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float T2 = 0.0f, W2[4] = {0.0f, 0.0f, 0.0f, 0.0f}, T2i = 0.0f, W2i[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    zsums<2, IM>(X, T, W, Ti, Wi);
+    if (DUAL) zsums<0, IM>(X, T2, W2, T2i, W2i);
+    float2 U = make_float2(1.0f, 0.0f), R0 = U, R1 = U, R2 = U, R3 = U;
+    uint32_t sg = 0;
+    for (int r = 0; r < len; ++r) {
+        const OpD o = d[r];
+        const uint32_t u0 = o.q0u < 0 ? 1u : (uint32_t)(gl >> o.q0u) & 1u;
+        if (o.cat == kCatStep || o.cat == kCatStep2) {
+            const int k = (int)o.var - 9;  // register bit of the qubit, or -1: thread-uniform (variant 8)
+            float v[4];
+            int nv = 0;
+            v[nv++] = zpick(k, u0, T, W);
+            if (IM == 2) v[nv++] = zpick(k, u0, Ti, Wi);
+            if (DUAL) {
+                v[nv++] = zpick(k, u0, T2, W2);
+                if (IM == 2) v[nv++] = zpick(k, u0, T2i, W2i);
+            }
+#pragma unroll
+            for (int x = 0; x < nv; ++x) v[x] += __shfl_xor_sync(0xffffffffu, v[x], 1);
+            if (!(lane & 1)) {
+#pragma unroll
+                for (int x = 0; x < nv; ++x) part[(o.slot + x) * (kNT / 2) + (tid >> 1)] = v[x];
+            }
+            const float2 f = make_float2(o.a, o.b);  // cos, sin of the step's half angle (1, 0 without rotation)
+            if (k < 0) U = cmul(U, make_float2(f.x, u0 ? -f.y : f.y));
+            else if (k == 0) R0 = cmul(R0, f);
+            else if (k == 1) R1 = cmul(R1, f);
+            else if (k == 2) R2 = cmul(R2, f);
+            else R3 = cmul(R3, f);
+        } else {
+            const uint32_t u1 = o.q1u < 0 ? 1u : (uint32_t)(gl >> o.q1u) & 1u;
+            sg ^= diag_mask(o.sub, u0, u1);
+        }
+    }
+    float2 ph[kA];
+    ph[0] = U;
+    ph[1] = cmulc(ph[0], R0);
+    ph[0] = cmul(ph[0], R0);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) { ph[e | 2] = cmulc(ph[e], R1); ph[e] = cmul(ph[e], R1); }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { ph[e | 4] = cmulc(ph[e], R2); ph[e] = cmul(ph[e], R2); }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) { ph[e | 8] = cmulc(ph[e], R3); ph[e] = cmul(ph[e], R3); }
+    if (sg) {
+#pragma unroll
+        for (int m = 0; m < kA; ++m)
+            if ((sg >> m) & 1u) ph[m] = make_float2(-ph[m].x, -ph[m].y);
+    }
+#pragma unroll
+    for (int m = 0; m < kA; ++m) {
+        X[1][m] = cmul(X[1][m], ph[m]);
+        X[2][m] = cmul(X[2][m], ph[m]);
+        if (DUAL) X[0][m] = cmul(X[0][m], ph[m]);
+    }
+}
 
 // S: stages of the shared-memory tile ring; PSI: the pass touches register psi (passes of the
 // metric columns do not, and their instantiation keeps only a and b in registers)
@@ -456,7 +737,7 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool well_formed = pd.t == kPhaseTile && pd.low == 5 && pd.win == kMaxWin && pd.nops >= 1 &&
                              pd.nops <= kMaxPhaseOps && pd.nphases >= 1 && pd.nphases <= kMaxPhases &&
-                             pd.nslots <= kMaxSlots;
+                             pd.nslots <= kMaxSlots && (pd.regmask & 9) != 9;
     if (!well_formed) {
         if (tid == 0 && blockIdx.x == 0) set_status(pa.status, QNG_ERR_UNSUPPORTED);
         return;
@@ -470,7 +751,7 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
         uint32_t dyn = 0;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
         const size_t need = (size_t)S * nreg * kRegTile + (size_t)kMaxSlots * (kNT / 2) * sizeof(float);
-        if (dyn < need || (!PSI && (pd.regmask & 1))) {
+        if (dyn < need || (!PSI && (pd.regmask & 1)) || (PSI && (pd.regmask & 8))) {
             if (tid == 0 && blockIdx.x == 0) set_status(pa.status, QNG_ERR_UNSUPPORTED);
             return;
         }
@@ -545,12 +826,17 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
         d.q0u = (int8_t)((op.dk0 >= 0 || op.q0 < 0) ? -1 : op.q0);
         d.q1u = (int8_t)((op.dk1 >= 0 || op.q1 < 0) ? -1 : op.q1);
         d.slot = (uint8_t)(op.slot >= 0 ? op.slot : 0);
-        if ((op.kind == kOpRot || op.kind == kOpStep) && op.param >= 0) {
+        d.pad = op.zrun > 0 ? (uint8_t)op.zrun : 0;
+        if (op.zrun != 0 && (op.kind == kOpStep || op.kind == kOpStep2)) {
+            // a step of a diagonal run: the exact cos, sin of its adjoint rotation (1, 0 without one)
+            d.a = op.param >= 0 ? (float)pa.coef[op.param].c : 1.0f;
+            d.b = op.param >= 0 ? (float)pa.coef[op.param].s : 0.0f;
+        } else if ((op.kind == kOpRot || op.kind == kOpStep || op.kind == kOpStep2) && op.param >= 0) {
             // steps take the adjoint rotation cos + i sin sigma; kOpRot R (adjoint 0, cos - i sin
             // sigma) or R^dag (adjoint 1). alpha = theta / 2 in (-pi/2, pi/2]: when cos < 0 the
             // rotation by alpha - pi is used and the register's sign flips (decided below).
             const DevCoef co = pa.coef[op.param];
-            const double sg = (op.kind == kOpStep || op.adjoint) ? 1.0 : -1.0;
+            const double sg = (op.kind == kOpStep || op.kind == kOpStep2 || op.adjoint) ? 1.0 : -1.0;
             const double flip = co.c < 0.0 ? -1.0 : 1.0;
             const double c = flip * co.c, sn = flip * sg * co.s;  // cos, sin of the plane angle phi
             d.a = (float)(sn / (1.0 + c));
@@ -560,6 +846,7 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
         switch (op.kind) {
         case kOpCopy:
             d.cat = op.r0 == kRegPsi && op.r1 == kRegA ? kCatCopyA : (op.r0 == kRegPsi && op.r1 == kRegB ? kCatCopyB : kCatBad);
+            if (op.r0 == kRegA && op.r1 == kRegB2) d.cat = kCatCopyAB2;
             break;
         case kOpZero: d.cat = op.r0 == kRegPsi ? kCatZero : kCatBad; break;
         case kOpRot:
@@ -567,11 +854,18 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
             d.var = (uint8_t)av;
             break;
         case kOpSigma:
-            d.cat = (op.r0 == kRegB && av >= 0) ? kCatSigma : kCatBad;
+            d.cat = ((op.r0 == kRegB || op.r0 == kRegB2) && av >= 0) ? kCatSigma : kCatBad;
+            d.sub = op.r0 == kRegB2 ? 1 : 0;
             d.var = (uint8_t)av;
             break;
         case kOpIp:
-            d.cat = (op.r0 == kRegB && op.r1 == kRegB && op.adjoint == 0 && av >= 0) ? kCatIp : kCatBad;
+            d.cat = ((op.r0 == kRegB || op.r0 == kRegB2) && op.r1 == op.r0 && op.adjoint == 0 && av >= 0) ? kCatIp : kCatBad;
+            d.sub = op.r0 == kRegB2 ? 1 : 0;
+            d.var = (uint8_t)av;
+            break;
+        case kOpStep2:
+            d.cat = (av >= 0 && (op.adjoint == 0 || op.adjoint == 2)) ? kCatStep2 : kCatBad;
+            d.sub = op.adjoint == 2 ? 1 : 0;
             d.var = (uint8_t)av;
             break;
         case kOpStep:
@@ -617,7 +911,9 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
             const PassOp op = pa.ops[pd.op_begin + o];
             bad |= opd[o].cat == kCatBad;
             double f = 1.0;
-            if ((op.kind == kOpRot || op.kind == kOpStep) && op.param >= 0 && pa.coef[op.param].c < 0.0) f = -1.0;
+            if ((op.kind == kOpRot || op.kind == kOpStep || op.kind == kOpStep2) && op.param >= 0 && op.zrun == 0 &&
+                pa.coef[op.param].c < 0.0)
+                f = -1.0;
             switch (op.kind) {
             case kOpCopy: sc[op.r1] = sc[op.r0]; break;
             case kOpZero: sc[op.r0] = 1.0; break;
@@ -636,6 +932,20 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
                     sc[op.r1] *= f;
                 }
                 break;
+            case kOpStep2: {
+                const int nv = op.adjoint == 2 ? 2 : 1;  // values per column
+                if (rec)
+                    for (int k = 0; k < nv; ++k) {
+                        pa.slotfac[pd.slot_base + op.slot + k] = sc[kRegA] * sc[kRegB];
+                        pa.slotfac[pd.slot_base + op.slot + nv + k] = sc[kRegA] * sc[kRegB2];
+                    }
+                if (op.param >= 0) {
+                    sc[kRegA] *= f;
+                    sc[kRegB] *= f;
+                    sc[kRegB2] *= f;
+                }
+                break;
+            }
             case kOpSetScale: sc[op.r1] = sc[op.r0]; break;
             default: break;
             }
@@ -677,6 +987,7 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
             // writes, so nothing is carried from one phase (or tile) to the next in registers
             Regs X;
             if (PSI && (rm & 1)) gather<0>(X, reinterpret_cast<const float2 *>(stage_reg(stage, 0)), ad, vm);
+            if (!PSI && (rm & 8)) gather<0>(X, reinterpret_cast<const float2 *>(stage_reg(stage, 3)), ad, vm);
             if (rm & 2) gather<1>(X, reinterpret_cast<const float2 *>(stage_reg(stage, 1)), ad, vm);
             if (rm & 4) gather<2>(X, reinterpret_cast<const float2 *>(stage_reg(stage, 2)), ad, vm);
             // global index of the thread's amplitude m = 0: the bit of every qubit that is not a
@@ -687,13 +998,38 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
                 if ((P.macro & ~0xFF) == kMacroSteps) {
                     if (((P.macro >> 4) & 15) == kAxisX) macro_steps<kAxisX>(X, m, opd + P.op_begin, part, lane, tid);
                     else macro_steps<kAxisY>(X, m, opd + P.op_begin, part, lane, tid);
+                } else if ((P.macro & ~0xFF) == kMacroSteps2) {
+                    if constexpr (!PSI) {
+                        if (((P.macro >> 4) & 15) == kAxisX) macro_steps2<kAxisX>(X, m, opd + P.op_begin, part, lane, tid);
+                        else macro_steps2<kAxisY>(X, m, opd + P.op_begin, part, lane, tid);
+                    }
                 } else {
                     const int q = opd[P.op_begin + m - 1].q0u;
-                    macro_cnots(X, m, q < 0 ? 1u : (uint32_t)(gl >> q) & 1u);
+                    const uint32_t ul = q < 0 ? 1u : (uint32_t)(gl >> q) & 1u;
+                    if ((P.macro >> 4) & 1) {
+                        if constexpr (!PSI) macro_cnots3(X, m, ul);
+                    } else {
+                        macro_cnots(X, m, ul);
+                    }
                 }
             }
             for (int o = P.macro ? P.op_end : P.op_begin; o < P.op_end; ++o) {
                 const OpD d = opd[o];
+                if (d.pad) {  // a run of diagonal operations, composed
+                    const int len = d.pad & kMaxZrun;
+                    if (d.pad & kZrunDual) {
+                        if constexpr (!PSI) {
+                            if (d.pad & kZrunIm) zrun<2, true>(X, opd + o, len, gl, part, lane, tid);
+                            else zrun<0, true>(X, opd + o, len, gl, part, lane, tid);
+                        }
+                    } else if (d.pad & kZrunIm) {
+                        zrun<2, false>(X, opd + o, len, gl, part, lane, tid);
+                    } else {
+                        zrun<0, false>(X, opd + o, len, gl, part, lane, tid);
+                    }
+                    o += len - 1;
+                    continue;
+                }
                 // the thread-uniform bits of q0 / q1, for the variants that read them
                 auto ubit = [&](int q) -> uint32_t { return q < 0 ? 1u : (uint32_t)(gl >> q) & 1u; };
                 const uint32_t u0 = ubit(d.q0u), u1 = ubit(d.q1u);
@@ -722,16 +1058,47 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
                     break;
                 }
                 case kCatRot: if (PSI) rot_av<0>(X, d.var, d.a, d.b, u0); break;
-                case kCatSigma: sigma_av<2>(X, d.var, u0); break;
+                case kCatSigma:
+                    if (d.sub == 0) sigma_av<2>(X, d.var, u0);
+                    else if constexpr (!PSI) sigma_av<0>(X, d.var, u0);
+                    break;
                 case kCatFixed:
                     if (PSI && (d.regs & 1)) fixed_fv<0>(X, d.sub, u0, u1);
+                    if (!PSI && (d.regs & 8)) fixed_fv<0>(X, d.sub, u0, u1);
                     if (d.regs & 2) fixed_fv<1>(X, d.sub, u0, u1);
                     if (d.regs & 4) fixed_fv<2>(X, d.sub, u0, u1);
+                    break;
+                case kCatCopyAB2:
+                    if constexpr (!PSI) {
+#pragma unroll
+                        for (int m = 0; m < kA; ++m) X[0][m] = X[1][m];
+                    }
+                    break;
+                case kCatStep2:
+                    if constexpr (!PSI) {
+                        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                        if (d.sub) step2_av<2>(X, d.var, d.a, d.b, u0, acc);
+                        else step2_av<0>(X, d.var, d.a, d.b, u0, acc);
+                        // slots: Re ab, Re ab2; or Re ab, Im ab, Re ab2, Im ab2
+                        float v[4] = {acc[0], d.sub ? acc[1] : acc[2], acc[2], acc[3]};
+                        const int nv = d.sub ? 4 : 2;
+#pragma unroll
+                        for (int x = 0; x < 4; ++x)
+                            if (x < nv) v[x] += __shfl_xor_sync(0xffffffffu, v[x], 1);
+                        if (!(lane & 1)) {
+#pragma unroll
+                            for (int x = 0; x < 4; ++x)
+                                if (x < nv) part[(d.slot + x) * (kNT / 2) + (tid >> 1)] = v[x];
+                        }
+                    }
                     break;
                 case kCatIp:
                 case kCatStep: {
                     float re = 0.0f, im = 0.0f;
-                    if (d.cat == kCatIp) step_av<2, 2, 0, false>(X, d.var, 0.0f, 0.0f, u0, re, im);
+                    if (d.cat == kCatIp) {
+                        if (d.sub == 0) step_av<2, 2, 0, false>(X, d.var, 0.0f, 0.0f, u0, re, im);
+                        else if constexpr (!PSI) step_av<0, 0, 0, false>(X, d.var, 0.0f, 0.0f, u0, re, im);
+                    }
                     else if (d.sub == 0) step_av<1, 2, 0, true>(X, d.var, d.a, d.b, u0, re, im);
                     else if (d.sub == 1) step_av<1, 2, 2, true>(X, d.var, d.a, d.b, u0, re, im);
                     else if (PSI) { step_av<0, 1, 1, true>(X, d.var, d.a, d.b, u0, re, im); re = im; }
@@ -750,6 +1117,7 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
                 }
             }
             if (PSI && (wm & 1)) scatter<0>(X, reinterpret_cast<float2 *>(stage_reg(stage, 0)), ad, vm);
+            if (!PSI && (wm & 8)) scatter<0>(X, reinterpret_cast<float2 *>(stage_reg(stage, 3)), ad, vm);
             if (wm & 2) scatter<1>(X, reinterpret_cast<float2 *>(stage_reg(stage, 1)), ad, vm);
             if (wm & 4) scatter<2>(X, reinterpret_cast<float2 *>(stage_reg(stage, 2)), ad, vm);
             __syncthreads();
@@ -800,6 +1168,8 @@ size_t phased_smem_bytes(int nreg) {
 cudaError_t prepare_pass_phased() {
     cudaError_t e = raise_smem_limit(reinterpret_cast<const void *>(k_pass_phased<2, true>), phased_smem_bytes(3));
     if (e != cudaSuccess) return e;
+    if ((e = raise_smem_limit(reinterpret_cast<const void *>(k_pass_phased<2, false>), phased_smem_bytes(3))) != cudaSuccess)
+        return e;
     if ((e = raise_smem_limit(reinterpret_cast<const void *>(k_pass_phased<3, true>), phased_smem_bytes(2))) != cudaSuccess)
         return e;
     return raise_smem_limit(reinterpret_cast<const void *>(k_pass_phased<3, false>), phased_smem_bytes(2));
@@ -807,10 +1177,11 @@ cudaError_t prepare_pass_phased() {
 
 cudaError_t launch_pass_phased(const PassArgs &pa, int regmask, int grid, int metric_im, cudaStream_t st) {
     (void)metric_im;  // the complex-metric steps are compiled into the same kernel
-    const int nreg = __builtin_popcount(regmask & 7);
-    if (nreg < 1) return cudaErrorInvalidValue;
+    const int nreg = __builtin_popcount(regmask & 15);
+    if (nreg < 1 || nreg > 3 || (regmask & 9) == 9) return cudaErrorInvalidValue;
     const size_t smem = phased_smem_bytes(nreg);
-    if (phased_stages(nreg) == 2) k_pass_phased<2, true><<<grid, kNT, smem, st>>>(pa);
+    if (phased_stages(nreg) == 2 && (regmask & 1)) k_pass_phased<2, true><<<grid, kNT, smem, st>>>(pa);
+    else if (phased_stages(nreg) == 2) k_pass_phased<2, false><<<grid, kNT, smem, st>>>(pa);
     else if (regmask & 1) k_pass_phased<3, true><<<grid, kNT, smem, st>>>(pa);
     else k_pass_phased<3, false><<<grid, kNT, smem, st>>>(pa);
     return cudaGetLastError();

@@ -53,6 +53,7 @@ void access(const PassOp &o, int &rd, int &wr) {
     case kOpSigma: rd = wr = 1 << o.r0; break;
     case kOpIp: rd = (1 << o.r0) | (1 << o.r1); break;
     case kOpStep: rd = (1 << o.r0) | (1 << o.r1); wr = o.param >= 0 ? rd : 0; break;
+    case kOpStep2: rd = (1 << kRegA) | (1 << kRegB) | (1 << kRegB2); wr = o.param >= 0 ? rd : 0; break;
     default: break;
     }
 }
@@ -72,7 +73,8 @@ int pair_target(const PassOp &o) {
     case kOpRot:
     case kOpSigma:
     case kOpIp:
-    case kOpStep: return (o.axis == kAxisX || o.axis == kAxisY) ? o.q0 : -1;
+    case kOpStep:
+    case kOpStep2: return (o.axis == kAxisX || o.axis == kAxisY) ? o.q0 : -1;
     case kOpFixed:
         if (o.fixed_kind == QNG_GATE_CNOT) return o.q1;
         if (o.fixed_kind == QNG_GATE_CZ || o.fixed_kind == QNG_GATE_Z) return -1;
@@ -92,18 +94,66 @@ int bank_class(int b) { return b == 0 ? 3 : (b - 1) % 3; }
 int32_t macro_form(const std::vector<PassOp> &ops, size_t i, size_t j) {
     const int m = (int)(j - i);
     if (m < 1 || m > 4) return 0;
-    bool steps = true, cnots = true;
-    const int ax = ops[i].axis;
+    bool steps = true, steps2 = true, cnots = true;
+    const int ax = ops[i].axis, regs = ops[i].regs;
+    const int ab = (1 << kRegA) | (1 << kRegB), abb = ab | (1 << kRegB2);
     for (int k = 0; k < m; ++k) {
         const PassOp &o = ops[i + k];
-        steps = steps && o.kind == kOpStep && o.r0 == kRegA && o.r1 == kRegB && o.adjoint == 0 && o.axis == ax &&
-                (ax == kAxisX || ax == kAxisY) && o.kt == k;
-        cnots = cnots && o.kind == kOpFixed && o.fixed_kind == QNG_GATE_CNOT && o.regs == ((1 << kRegA) | (1 << kRegB)) &&
-                o.kt == k && (k < m - 1 ? o.dk0 == k + 1 : o.dk0 < 0);
+        const bool xy_k = o.adjoint == 0 && o.axis == ax && (ax == kAxisX || ax == kAxisY) && o.kt == k;
+        steps = steps && o.kind == kOpStep && o.r0 == kRegA && o.r1 == kRegB && xy_k;
+        steps2 = steps2 && o.kind == kOpStep2 && xy_k;
+        cnots = cnots && o.kind == kOpFixed && o.fixed_kind == QNG_GATE_CNOT && (regs == ab || regs == abb) &&
+                o.regs == regs && o.kt == k && (k < m - 1 ? o.dk0 == k + 1 : o.dk0 < 0);
     }
     if (steps) return kMacroSteps | (ax << 4) | m;
-    if (cnots) return kMacroCnot | m;
+    if (steps2) return kMacroSteps2 | (ax << 4) | m;
+    if (cnots) return kMacroCnot | (regs == abb ? 1 << 4 : 0) | m;
     return 0;
+}
+
+// Diagonal operations on a and b: 1 a Z-axis step taking Re, 2 one taking Re and Im, 3 a CZ or Z
+// gate; on a, b and b2 (two columns): 4, 5, 6 the same; 0 anything else.
+int diag_kind(const PassOp &o) {
+    const int ab = (1 << kRegA) | (1 << kRegB), abb = ab | (1 << kRegB2);
+    const bool zs = o.axis == kAxisZ && (o.adjoint == 0 || o.adjoint == 2);
+    if (o.kind == kOpStep && zs && o.r0 == kRegA && o.r1 == kRegB) return o.adjoint == 0 ? 1 : 2;
+    if (o.kind == kOpStep2 && zs) return o.adjoint == 0 ? 4 : 5;
+    if (o.kind == kOpFixed && (o.fixed_kind == QNG_GATE_CZ || o.fixed_kind == QNG_GATE_Z))
+        return o.regs == ab ? 3 : (o.regs == abb ? 6 : 0);
+    return 0;
+}
+
+// Mark the runs of diagonal operations among ops [i, j) of a phase (PassOp::zrun). Diagonal
+// operators commute with one another, so within such a run every step's inner product
+// <a|sigma_z|b> is the one on the run's starting registers, and the rotations and signs of the run
+// compose into one phase factor per amplitude: the kernel applies them once, after the run's inner
+// products.
+void mark_zruns(std::vector<PassOp> &ops, size_t i, size_t j) {
+    size_t o = i;
+    while (o < j) {
+        if (!diag_kind(ops[o])) {
+            ++o;
+            continue;
+        }
+        size_t e = o;
+        const int fam = diag_kind(ops[o]) >= 4 ? 3 : 0;  // the run's register family: (a, b) or (a, b, b2)
+        int im = 0, steps = 0;
+        while (e < j && e - o < (size_t)kMaxZrun) {
+            const int k = diag_kind(ops[e]);
+            if (!k || (k > 3 ? 3 : 0) != fam) break;
+            if (k - fam != 3) {
+                if (im && k - fam != im) break;
+                im = k - fam;
+                ++steps;
+            }
+            ++e;
+        }
+        if (steps >= 2) {
+            ops[o].zrun = (int8_t)((int)(e - o) | (im == 2 ? kZrunIm : 0) | (fam ? kZrunDual : 0));
+            for (size_t x = o + 1; x < e; ++x) ops[x].zrun = -1;
+        }
+        o = e;
+    }
 }
 
 // Split a pass's operations into register phases (see PassPhase): a phase takes operations while
@@ -167,7 +217,7 @@ bool make_phases(const PassDesc &pd, std::vector<PassOp> &ops, std::vector<PassP
             op.kt = pair_target(op) >= 0 ? pos(pair_target(op)) : (int8_t)-1;
             op.dk0 = pos(op.q0);
             op.dk1 = pos(op.q1);
-            op.pad8 = 0;
+            op.zrun = 0;
             int rd, wr;
             access(op, rd, wr);
             rm |= rd | wr;
@@ -176,6 +226,7 @@ bool make_phases(const PassDesc &pd, std::vector<PassOp> &ops, std::vector<PassP
         p.rmask = rm;
         p.wmask = wm;
         p.macro = macro_form(ops, i, j);
+        if (!p.macro) mark_zruns(ops, i, j);
         ph.push_back(p);
         if ((int)ph.size() > kMaxPhases) {
             *fit_ops = (size_t)ph[kMaxPhases].op_begin;
@@ -248,6 +299,47 @@ struct Builder {
         gr.reds.push_back(RedSpec{o.slot, mul, region, index});
         if (im == 2) gr.reds.push_back(RedSpec{o.slot + 1, mul, kRegionLim, index});
     }
+    // the step of two columns that share a (kOpStep2): column index_b's entry from <a|sigma_k|b>,
+    // column index_b2's from <a|sigma_k|b2>, then R_k^dag on a, b and b2 when rot
+    void add_step2(Group &gr, int k, int im, bool rot, int64_t index_b, int64_t index_b2) {
+        const qng_gate &g = gates[rot_at[k]];
+        PassOp o = mk(kOpStep2);
+        o.r0 = kRegA;
+        o.r1 = kRegB;
+        o.regs = (1 << kRegA) | (1 << kRegB) | (1 << kRegB2);
+        o.adjoint = im;
+        o.axis = axis_of(g.kind);
+        o.q0 = g.q0;
+        o.param = rot ? k : -1;
+        o.slot = (int)gr.reds.size();
+        gr.ops.push_back(o);
+        if (im == 2) {
+            gr.reds.push_back(RedSpec{o.slot, 0.25, kRegionL, index_b});
+            gr.reds.push_back(RedSpec{o.slot + 1, 0.25, kRegionLim, index_b});
+            gr.reds.push_back(RedSpec{o.slot + 2, 0.25, kRegionL, index_b2});
+            gr.reds.push_back(RedSpec{o.slot + 3, 0.25, kRegionLim, index_b2});
+        } else {
+            gr.reds.push_back(RedSpec{o.slot, 0.25, kRegionL, index_b});
+            gr.reds.push_back(RedSpec{o.slot + 1, 0.25, kRegionL, index_b2});
+        }
+    }
+    // b <- F_k^dag sigma_k F_k src and <sigma_k> = <F_k src|sigma_k|F_k src> into kRegionSigma[k]: the
+    // start of column k (src = psi or a, both Psi[k] there); also_src applies F_k to src as well
+    void add_column_start(Group &gr, int k, int src, int b, bool also_src) {
+        PassOp c = mk(kOpCopy);
+        c.r0 = src;
+        c.r1 = b;
+        gr.ops.push_back(c);
+        for (int gi : fixed_of[k]) add_fixed(gr, gi, (1 << b) | (also_src ? 1 << src : 0));
+        add_ip(gr, k, b, b, 0, 1.0, kRegionSigma, k);
+        const qng_gate &g = gates[rot_at[k]];
+        PassOp sg = mk(kOpSigma);
+        sg.r0 = b;
+        sg.axis = axis_of(g.kind);
+        sg.q0 = g.q0;
+        gr.ops.push_back(sg);
+        for (int f = (int)fixed_of[k].size() - 1; f >= 0; --f) add_fixed(gr, fixed_of[k][f], 1 << b);
+    }
     void add_ip(Group &gr, int k_axis_param, int r0, int r1, int im, double mul, int region, int64_t index, bool sigma = true) {
         PassOp o = mk(kOpIp);
         o.r0 = r0;
@@ -267,21 +359,25 @@ struct Builder {
     // qubits their non-diagonal parts act on fit in the tile window and its inner products fit in
     // the slot budget (a step may span several passes). Then launch the segment's reduction.
     void emit(std::vector<Group> &groups, int segment, int dead_at_end) {
-        struct Item { PassOp op; int need; int nred; RedSpec red[2]; };
+        struct Item { PassOp op; int need; int nred; int regs; RedSpec red[4]; };
         std::vector<Item> items;
         for (Group &g : groups) {
             for (const PassOp &o : g.ops) {
                 Item it;
                 it.op = o;
                 it.need = -1;
-                if (o.kind == kOpRot || o.kind == kOpSigma || o.kind == kOpIp || o.kind == kOpStep) {
+                if (o.kind == kOpRot || o.kind == kOpSigma || o.kind == kOpIp || o.kind == kOpStep || o.kind == kOpStep2) {
                     if (o.axis == kAxisX || o.axis == kAxisY) it.need = o.q0;
                 } else if (o.kind == kOpFixed) {
                     if (o.fixed_kind == QNG_GATE_CNOT) it.need = o.q1;
                     else if (o.fixed_kind != QNG_GATE_CZ && o.fixed_kind != QNG_GATE_Z) it.need = o.q0;
                 }
                 if (it.need >= 0 && it.need < low) it.need = -1;
-                it.nred = (o.kind == kOpIp || o.kind == kOpStep) ? (o.kind == kOpStep && o.adjoint == 2 ? 2 : 1) : 0;
+                it.nred = (o.kind == kOpIp || o.kind == kOpStep) ? (o.kind == kOpStep && o.adjoint == 2 ? 2 : 1)
+                        : (o.kind == kOpStep2 ? (o.adjoint == 2 ? 4 : 2) : 0);
+                int rd, wr;
+                access(o, rd, wr);
+                it.regs = rd | wr;
                 for (int r = 0; r < it.nred; ++r) it.red[r] = g.reds[o.slot + r];
                 items.push_back(it);
             }
@@ -294,11 +390,15 @@ struct Builder {
             std::set<int> win_set;
             std::vector<PassOp> ops;
             std::vector<RedSpec> reds;
+            int regs_used = 0;
             size_t i1 = i0;
             while (i1 < items.size()) {
                 const Item &it = items[i1];
                 const bool new_q = it.need >= 0 && !win_set.count(it.need);
                 if (i1 > i0 && ((new_q && (int)win_set.size() >= win) || ((int)reds.size() + it.nred > kMaxSlots))) break;
+                // the register-phase kernel holds at most three registers in a pass (psi and b2 share a slot)
+                if (i1 > i0 && S.phased && __builtin_popcount(regs_used | it.regs) > 3) break;
+                regs_used |= it.regs;
                 if (i1 > i0 && (i1 - i0 >= limit || (S.phased && i1 - i0 >= (size_t)kMaxPhaseOps))) break;
                 if (new_q) win_set.insert(it.need);
                 PassOp o = it.op;
@@ -389,6 +489,7 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
     S.low = B.low;
     S.t = B.t;
     S.phased = precision == QNG_C64 && B.t == kPhaseTile;
+    S.pairs = false;
     const int PSI = 1 << kRegPsi, A = 1 << kRegA, Bm = 1 << kRegB;
 
     // forward: psi <- U_{P-1} ... U_0 |0>
@@ -471,6 +572,36 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
             continue;
         }
         flush_skipped();
+        if (S.pairs && j >= 1 && j + 1 < P && (!want || (*want)[j + 1])) {
+            // columns u = j + 1 and l = j together (psi = Psi[l] here): psi advances through U_l and
+            // column u starts from it; u's first step (i = l) takes a to Psi[l], from which column l
+            // starts in b2; then for i = l - 1 .. 0 one step serves both columns, a rotated once
+            const int l = j, u = j + 1;
+            const int AB = A | Bm, AB2 = A | Bm | (1 << kRegB2);
+            std::vector<Group> gs(l + 2);
+            Group &g0 = gs[0];
+            for (int gi : B.fixed_of[l]) B.add_fixed(g0, gi, PSI);
+            B.add_rot(g0, l, false, PSI);
+            PassOp ca = mk(kOpCopy);
+            ca.r0 = kRegPsi;
+            ca.r1 = kRegA;
+            g0.ops.push_back(ca);
+            B.add_column_start(g0, u, kRegPsi, kRegB, true);
+            B.add_rot(g0, u, false, PSI);
+            B.add_step(gs[1], l, kRegA, kRegB, im, true, 0.25, kRegionL, (int64_t)l * P + u);
+            for (int f = (int)B.fixed_of[l].size() - 1; f >= 0; --f) B.add_fixed(gs[1], B.fixed_of[l][f], AB);
+            B.add_column_start(gs[1], l, kRegA, kRegB2, false);
+            for (int s = 1; s <= l; ++s) {
+                const int i = l - s;
+                Group &g = gs[1 + s];
+                B.add_step2(g, i, im, i > 0, (int64_t)i * P + u, (int64_t)i * P + l);
+                if (i > 0)
+                    for (int f = (int)B.fixed_of[i].size() - 1; f >= 0; --f) B.add_fixed(g, B.fixed_of[i][f], AB2);
+            }
+            B.emit(gs, im ? kSegMetricIm : kSegMetric, AB2);
+            ++j;
+            continue;
+        }
         std::vector<Group> gs(j + 1);
         Group &g0 = gs[0];
         if (j == 0) {

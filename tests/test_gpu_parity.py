@@ -692,3 +692,49 @@ def test_column_partition_onchip(qng, oracle, ranks, which):
     assert torch.equal(out["g"], ref["g"])
     assert torch.equal(out["dtheta"], ref["dtheta"])
     assert rel(out["g"].cpu(), oracle.qng_step(p)["g"]) <= TOL[W.C128]
+
+
+@pytest.mark.parametrize("precision", [W.C64, W.C128])
+def test_graph_capture_batch256(qng, oracle, precision):
+    """The 256-instance batch (6-14 qubits, 2-10 layers) captured whole in one CUDA graph: its launch
+    groups run side by side on their own streams inside the capture; replays equal the direct step
+    bit for bit, the side-by-side groups equal the groups run in turn, and sampled instances match
+    the oracle."""
+    probs = W.config_batch(precision=precision)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = qng.Context(probs, stream=stream)
+        th = ctx.theta0()
+        ref = ctx.step(th, 0.1, 1e-3)
+        ctx.sync()
+        ref = {k: v.clone() for k, v in ref.items()}
+        ctx.set_pipeline(1)  # the groups in turn
+        seq = ctx.step(th, 0.1, 1e-3)
+        ctx.sync()
+        for k in ref:
+            assert torch.equal(seq[k], ref[k]), k
+        ctx.set_pipeline(0)
+        out = ctx.graph_capture(th, 0.1, 1e-3)
+        for _ in range(2):
+            for v in out.values():
+                v.fill_(float("nan"))
+            ctx.graph_launch()
+            ctx.sync()
+            for k in ref:
+                assert torch.equal(out[k], ref[k]), k
+    g = ref["g"].cpu().numpy()
+    grad = ref["grad"].cpu().numpy()
+    dth = ref["dtheta"].cpu().numpy()
+    for b in (0, 101, 255):
+        r = oracle.qng_step(probs[b])
+        m0, m1 = ctx.metric_offsets[b], ctx.metric_offsets[b + 1]
+        p0, p1 = ctx.param_offsets[b], ctx.param_offsets[b + 1]
+        assert rel(g[m0:m1], r["g"]) <= TOL[precision]
+        assert rel(grad[p0:p1], r["grad"]) <= TOL[precision]
+        if precision == W.C128:
+            assert rel(dth[p0:p1], r["dtheta"]) <= TOL[precision]
+        else:  # complex64: dtheta solves its own float64 system (the tolerance reading for c64 dtheta)
+            P = p1 - p0
+            A = g[m0:m1].reshape(P, P) + 1e-3 * np.eye(P)
+            res = A @ dth[p0:p1] + 0.1 * grad[p0:p1]
+            assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(0.1 * grad[p0:p1])

@@ -77,6 +77,22 @@ def test_streaming_layered_14(qng, oracle, precision):
     run_streaming(qng, oracle, p, precision)
 
 
+@pytest.mark.parametrize("n,seed", [(12, 21), (14, 22)])
+def test_streaming_c64_diagonal_runs(qng, oracle, n, seed):
+    """Runs of 1-24 RZ steps with CZ / Z gates between them, some broken by a CNOT or H, at complex64
+    from 12 qubits: the register-phase kernel takes each run's inner products on its starting
+    registers and applies the run's rotations and signs as one composed factor per amplitude. Real
+    step and complex metric (Re and Im per step) against the oracle."""
+    p = W.z_run_problem(n, 160, seed, W.C64)
+    run_streaming(qng, oracle, p, W.C64)
+    ctx = qng.Context(p, precision=W.C64, path=2)
+    G = ctx.metric_complex(ctx.theta0()).reshape(p.P, p.P).cpu().numpy()
+    ctx.sync()
+    ref = oracle.qng_step(p)["G"]
+    assert float(np.abs(G - ref).max() / np.abs(ref).max()) <= TOL[W.C64]
+    assert np.all(G.imag == -G.imag.T)
+
+
 def test_streaming_long_circuit_renormalisation(qng, oracle):
     """P = 600 with angles near pi/2: the register scales fall below 2^-200 and are renormalised."""
     run_streaming(qng, oracle, W.z_run_problem(7, 600, 6, W.C128, near_half_pi=True), W.C128)

@@ -1201,14 +1201,37 @@ qng_status qng_set_path(qng_ctx *c, int path) {
 
 qng_status qng_column_partition(int P, int ranks, int rank, int32_t *cols, int *ncols) {
     if (P < 0 || ranks < 1 || rank < 0 || rank >= ranks || !ncols || (P > 0 && !cols)) return QNG_ERR_ARG;
-    // pair k = {k, P-1-k} (k < P/2) has P-1 recurrence steps whatever k: pairs go round robin,
-    // and the middle column of an odd P (half a pair's steps) to the next rank in turn
-    int m = 0;
+    // Units: the adjacent pairs (l, l + 1), l odd, whose walks share register a on the streaming
+    // complex64 path (a rank holding both columns of a unit pairs them exactly as the whole
+    // instance does), column 0 and, for even P, column P - 1 alone. Column j has j recurrence steps.
+    // Groups: the units t and T - 1 - t together (2(P - 1) steps for even P: two pairs {k, P-1-k});
+    // the middle unit of an odd count; columns 0 and P - 1 together. Groups go, largest first, to
+    // the rank with the fewest steps so far (ties: the lowest rank), the same on every rank.
+    std::vector<std::pair<int, int>> U;
+    for (int l = 1; l + 1 < P; l += 2) U.push_back({l, l + 1});
+    std::vector<std::vector<int32_t>> groups;
+    if (P > 0) groups.push_back((P % 2 == 0 && P >= 2) ? std::vector<int32_t>{0, P - 1} : std::vector<int32_t>{0});
+    const int T = (int)U.size();
+    for (int t = 0; t < T / 2; ++t)
+        groups.push_back({U[t].first, U[t].second, U[T - 1 - t].first, U[T - 1 - t].second});
+    if (T & 1) groups.push_back({U[T / 2].first, U[T / 2].second});
+    auto steps = [](const std::vector<int32_t> &g) {
+        int64_t s = 0;
+        for (int32_t j : g) s += j;
+        return s;
+    };
+    std::stable_sort(groups.begin(), groups.end(), [&](const std::vector<int32_t> &a, const std::vector<int32_t> &b) {
+        return steps(a) > steps(b);
+    });
+    std::vector<int64_t> load(ranks, 0);
     std::vector<int32_t> mine;
-    for (int k = 0; k < P / 2; ++k)
-        if (k % ranks == rank) { mine.push_back(k); mine.push_back(P - 1 - k); }
-    if ((P & 1) && (P / 2) % ranks == rank) mine.push_back(P / 2);
+    for (const std::vector<int32_t> &g : groups) {
+        const int r = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[r] += steps(g);
+        if (r == rank) mine.insert(mine.end(), g.begin(), g.end());
+    }
     std::sort(mine.begin(), mine.end());
+    int m = 0;
     for (int32_t j : mine) cols[m++] = j;
     *ncols = m;
     return QNG_OK;

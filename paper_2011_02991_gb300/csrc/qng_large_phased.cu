@@ -59,8 +59,28 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// An amplitude held in registers, the (re, im) half of one float4 of its register row: a row keeps
+// its amplitudes in pairs (m, m + 1) that are the operands of 16-byte shared-memory accesses, so the
+// compiler can keep each pair in the aligned register quad those accesses use.
+struct Amp {
+    float &x, &y;
+    __device__ __forceinline__ operator float2() const { return make_float2(x, y); }
+    __device__ __forceinline__ Amp &operator=(float2 v) { x = v.x; y = v.y; return *this; }
+    __device__ __forceinline__ Amp &operator=(const Amp &o) {
+        const float ox = o.x, oy = o.y;
+        x = ox;
+        y = oy;
+        return *this;
+    }
+};
+struct Row {
+    float4 q[kA / 2];
+    __device__ __forceinline__ Amp operator[](int m) {
+        return Amp{(m & 1) ? q[m >> 1].z : q[m >> 1].x, (m & 1) ? q[m >> 1].w : q[m >> 1].y};
+    }
+};
 // the registers a phase holds: slot 0 psi (passes that touch psi) or b2 (passes that do not), 1 a, 2 b
-typedef float2 Regs[3][kA];
+typedef Row Regs[3];
 
 // ---- data movement between the shared-memory tile and the registers of a phase ----------------
 // Word of amplitude m: P0 ^ (e0 if bit 0 of m) ^ (e1 if bit 1) ^ ..., the swizzled positions of the
@@ -74,21 +94,16 @@ struct PhaseAddr {
 template <int R> __device__ __forceinline__ void gather(Regs &X, const float2 *tile, const PhaseAddr &A, bool vmode) {
     if (vmode) {
 #pragma unroll
-        for (int m = 0; m < kA; m += 2) {
-            const float4 v = reinterpret_cast<const float4 *>(tile)[A.at(m) >> 1];
-            X[R][m] = make_float2(v.x, v.y);
-            X[R][m + 1] = make_float2(v.z, v.w);
-        }
+        for (int m = 0; m < kA; m += 2) X[R].q[m >> 1] = reinterpret_cast<const float4 *>(tile)[A.at(m) >> 1];
     } else {
 #pragma unroll
         for (int m = 0; m < kA; ++m) X[R][m] = tile[A.at(m)];
     }
 }
-template <int R> __device__ __forceinline__ void scatter(const Regs &X, float2 *tile, const PhaseAddr &A, bool vmode) {
+template <int R> __device__ __forceinline__ void scatter(Regs &X, float2 *tile, const PhaseAddr &A, bool vmode) {
     if (vmode) {
 #pragma unroll
-        for (int m = 0; m < kA; m += 2)
-            reinterpret_cast<float4 *>(tile)[A.at(m) >> 1] = make_float4(X[R][m].x, X[R][m].y, X[R][m + 1].x, X[R][m + 1].y);
+        for (int m = 0; m < kA; m += 2) reinterpret_cast<float4 *>(tile)[A.at(m) >> 1] = X[R].q[m >> 1];
     } else {
 #pragma unroll
         for (int m = 0; m < kA; ++m) tile[A.at(m)] = X[R][m];
@@ -114,12 +129,12 @@ template <bool NEG> __device__ __forceinline__ void shear3(float &u, float &v, f
 }
 // (cos alpha + i sin alpha sigma) on the pair (x0, x1): X blocks (x0.x, x1.y), (x1.x, x0.y);
 // Y blocks (x1.x, x0.x), (x1.y, x0.y); each turned by alpha
-template <int AX> __device__ __forceinline__ void rot_pair(float2 &x0, float2 &x1, float a, float b) {
+template <int AX> __device__ __forceinline__ void rot_pair(Amp x0, Amp x1, float a, float b) {
     if (AX == kAxisX) { shear3<false>(x0.x, x1.y, a, b); shear3<false>(x1.x, x0.y, a, b); }
     else              { shear3<false>(x1.x, x0.x, a, b); shear3<false>(x1.y, x0.y, a, b); }
 }
 // (cos alpha + i sin alpha (-1)^S) on one amplitude: the block (x.x, x.y) turned by +-alpha
-template <bool S> __device__ __forceinline__ void rot_amp(float2 &x, float a, float b) { shear3<S>(x.x, x.y, a, b); }
+template <bool S> __device__ __forceinline__ void rot_amp(Amp x, float a, float b) { shear3<S>(x.x, x.y, a, b); }
 
 // inner product <A| sigma |B> (IM 0: Re, 1: Im, 2: both) over the register-bit-K pairs, then, when
 // ROT, the rotation of the same axis on A and B
@@ -643,7 +658,7 @@ __device__ __forceinline__ uint32_t diag_mask(int fv, uint32_t u0, uint32_t u1) 
 // Inner products of a run with register R (b in slot 2, b2 in slot 0): T, W of Re conj(a) b and, for
 // IM 2, of Im conj(a) b.
 template <int R, int IM>
-__device__ __forceinline__ void zsums(const Regs &X, float &T, float (&W)[4], float &Ti, float (&Wi)[4]) {
+__device__ __forceinline__ void zsums(Regs &X, float &T, float (&W)[4], float &Ti, float (&Wi)[4]) {
     float v[kA];
 #pragma unroll
     for (int m = 0; m < kA; ++m) v[m] = fmaf(X[1][m].x, X[R][m].x, X[1][m].y * X[R][m].y);

@@ -489,7 +489,7 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
     S.low = B.low;
     S.t = B.t;
     S.phased = precision == QNG_C64 && B.t == kPhaseTile;
-    S.pairs = false;
+    S.pairs = S.phased;
     const int PSI = 1 << kRegPsi, A = 1 << kRegA, Bm = 1 << kRegB;
 
     // forward: psi <- U_{P-1} ... U_0 |0>
@@ -572,8 +572,9 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
             continue;
         }
         flush_skipped();
-        if (S.pairs && j >= 1 && j + 1 < P && (!want || (*want)[j + 1])) {
-            // columns u = j + 1 and l = j together (psi = Psi[l] here): psi advances through U_l and
+        if (S.pairs && (j & 1) && j + 1 < P && (!want || (*want)[j + 1])) {
+            // columns u = j + 1 and l = j together, for odd j only, so that a column subset pairs
+            // exactly as the whole instance does (psi = Psi[l] here): psi advances through U_l and
             // column u starts from it; u's first step (i = l) takes a to Psi[l], from which column l
             // starts in b2; then for i = l - 1 .. 0 one step serves both columns, a rotated once
             const int l = j, u = j + 1;

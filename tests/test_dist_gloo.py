@@ -133,4 +133,9 @@ def test_column_partition_is_balanced():
             parts = [qng.column_partition(P, R, r) for r in range(R)]
             assert sorted(j for c in parts for j in c) == list(range(P))
             work = [sum(j for j in c) for c in parts]  # column j has j recurrence steps
-            assert max(work) - min(work) <= max(P - 1, 0)  # at most one pair (P - 1 steps) apart
+            # at most one group (two balanced pairs, 2P steps at most) apart
+            assert max(work) - min(work) <= max(2 * P, 0)
+            # the adjacent pairs (l, l + 1), l odd, stay on one rank
+            for c in parts:
+                s = set(c)
+                assert all((l + 1 in s) == (l in s) for l in range(1, P - 1, 2))

@@ -147,8 +147,8 @@ __device__ __forceinline__ void after(float &a, float &b, float re, float im) {
 }
 template <int RA, int RB, int IM, bool ROT, int K, int AX>
 __device__ __forceinline__ void step_pairs(Regs &X, float a, float b, float &re, float &im) {
+    // four accumulators per part, one per product of a pair: chains of 8 dependent FMAs, not 16
     float pr[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    int j = 0;
 #pragma unroll
     for (int m0 = 0; m0 < kA; ++m0) {
         if (m0 & (1 << K)) continue;
@@ -157,9 +157,14 @@ __device__ __forceinline__ void step_pairs(Regs &X, float a, float b, float &re,
         float2 s0, s1;  // (sigma b)_0, (sigma b)_1
         if (AX == kAxisX) { s0 = b1; s1 = b0; }
         else              { s0 = make_float2(b1.y, -b1.x); s1 = make_float2(-b0.y, b0.x); }
-        if (IM != 1) pr[j & 3] = fmaf(a0.x, s0.x, fmaf(a0.y, s0.y, fmaf(a1.x, s1.x, fmaf(a1.y, s1.y, pr[j & 3]))));
-        if (IM != 0) pi[j & 3] = fmaf(a0.x, s0.y, fmaf(-a0.y, s0.x, fmaf(a1.x, s1.y, fmaf(-a1.y, s1.x, pi[j & 3]))));
-        ++j;
+        if (IM != 1) {
+            pr[0] = fmaf(a0.x, s0.x, pr[0]); pr[1] = fmaf(a0.y, s0.y, pr[1]);
+            pr[2] = fmaf(a1.x, s1.x, pr[2]); pr[3] = fmaf(a1.y, s1.y, pr[3]);
+        }
+        if (IM != 0) {
+            pi[0] = fmaf(a0.x, s0.y, pi[0]); pi[1] = fmaf(-a0.y, s0.x, pi[1]);
+            pi[2] = fmaf(a1.x, s1.y, pi[2]); pi[3] = fmaf(-a1.y, s1.x, pi[3]);
+        }
     }
     const float r = (pr[0] + pr[1]) + (pr[2] + pr[3]), i = (pi[0] + pi[1]) + (pi[2] + pi[3]);
     if (IM != 1) re += r;
@@ -203,8 +208,8 @@ __device__ __forceinline__ void step_diag(Regs &X, float a, float b, float &re, 
 // when ROT, the rotation on a, b and b2. acc: Re ab, Im ab, Re ab2, Im ab2 (Im only for IM 2).
 template <int IM, bool ROT, int K, int AX>
 __device__ __forceinline__ void step2_pairs(Regs &X, float a, float b, float (&acc)[4]) {
-    float pr[2] = {0.0f, 0.0f}, pi[2] = {0.0f, 0.0f}, qr[2] = {0.0f, 0.0f}, qi[2] = {0.0f, 0.0f};
-    int j = 0;
+    // the products of a pair go to separate accumulators: chains of 8 dependent FMAs, not 16
+    float pr[2][2] = {}, pi[2][2] = {}, qr[2][2] = {}, qi[2][2] = {};
 #pragma unroll
     for (int m0 = 0; m0 < kA; ++m0) {
         if (m0 & (1 << K)) continue;
@@ -216,20 +221,24 @@ __device__ __forceinline__ void step2_pairs(Regs &X, float a, float b, float (&a
             s0 = make_float2(b1.y, -b1.x); s1 = make_float2(-b0.y, b0.x);
             t0 = make_float2(c1.y, -c1.x); t1 = make_float2(-c0.y, c0.x);
         }
-        pr[j & 1] = fmaf(a0.x, s0.x, fmaf(a0.y, s0.y, fmaf(a1.x, s1.x, fmaf(a1.y, s1.y, pr[j & 1]))));
-        qr[j & 1] = fmaf(a0.x, t0.x, fmaf(a0.y, t0.y, fmaf(a1.x, t1.x, fmaf(a1.y, t1.y, qr[j & 1]))));
+        pr[0][0] = fmaf(a0.x, s0.x, pr[0][0]); pr[0][1] = fmaf(a0.y, s0.y, pr[0][1]);
+        pr[1][0] = fmaf(a1.x, s1.x, pr[1][0]); pr[1][1] = fmaf(a1.y, s1.y, pr[1][1]);
+        qr[0][0] = fmaf(a0.x, t0.x, qr[0][0]); qr[0][1] = fmaf(a0.y, t0.y, qr[0][1]);
+        qr[1][0] = fmaf(a1.x, t1.x, qr[1][0]); qr[1][1] = fmaf(a1.y, t1.y, qr[1][1]);
         if (IM == 2) {
-            pi[j & 1] = fmaf(a0.x, s0.y, fmaf(-a0.y, s0.x, fmaf(a1.x, s1.y, fmaf(-a1.y, s1.x, pi[j & 1]))));
-            qi[j & 1] = fmaf(a0.x, t0.y, fmaf(-a0.y, t0.x, fmaf(a1.x, t1.y, fmaf(-a1.y, t1.x, qi[j & 1]))));
+            pi[0][0] = fmaf(a0.x, s0.y, pi[0][0]); pi[0][1] = fmaf(-a0.y, s0.x, pi[0][1]);
+            pi[1][0] = fmaf(a1.x, s1.y, pi[1][0]); pi[1][1] = fmaf(-a1.y, s1.x, pi[1][1]);
+            qi[0][0] = fmaf(a0.x, t0.y, qi[0][0]); qi[0][1] = fmaf(-a0.y, t0.x, qi[0][1]);
+            qi[1][0] = fmaf(a1.x, t1.y, qi[1][0]); qi[1][1] = fmaf(-a1.y, t1.x, qi[1][1]);
         }
-        ++j;
     }
-    const float r1 = pr[0] + pr[1], r2 = qr[0] + qr[1];
+    const float r1 = (pr[0][0] + pr[0][1]) + (pr[1][0] + pr[1][1]);
+    const float r2 = (qr[0][0] + qr[0][1]) + (qr[1][0] + qr[1][1]);
     acc[0] += r1;
     acc[2] += r2;
     if (IM == 2) {
-        acc[1] += pi[0] + pi[1];
-        acc[3] += qi[0] + qi[1];
+        acc[1] += (pi[0][0] + pi[0][1]) + (pi[1][0] + pi[1][1]);
+        acc[3] += (qi[0][0] + qi[0][1]) + (qi[1][0] + qi[1][1]);
     }
     if (ROT) {
         after(a, b, r1, r2);
@@ -245,25 +254,25 @@ __device__ __forceinline__ void step2_pairs(Regs &X, float a, float b, float (&a
 }
 template <int IM, bool ROT, uint32_t PT>
 __device__ __forceinline__ void step2_diag(Regs &X, float a, float b, float (&acc)[4]) {
-    float pr[2] = {0.0f, 0.0f}, pi[2] = {0.0f, 0.0f}, qr[2] = {0.0f, 0.0f}, qi[2] = {0.0f, 0.0f};
+    float pr[4] = {}, pi[4] = {}, qr[4] = {}, qi[4] = {};
 #pragma unroll
     for (int m = 0; m < kA; ++m) {
         const bool sb = ((PT >> m) & 1u) != 0;
         const float2 av = X[1][m], bv = X[2][m], cv = X[0][m];
         const float2 af = sb ? make_float2(-av.x, -av.y) : av;
-        pr[m & 1] = fmaf(af.x, bv.x, fmaf(af.y, bv.y, pr[m & 1]));
-        qr[m & 1] = fmaf(af.x, cv.x, fmaf(af.y, cv.y, qr[m & 1]));
+        pr[m & 3] = fmaf(af.x, bv.x, fmaf(af.y, bv.y, pr[m & 3]));
+        qr[m & 3] = fmaf(af.x, cv.x, fmaf(af.y, cv.y, qr[m & 3]));
         if (IM == 2) {
-            pi[m & 1] = fmaf(af.x, bv.y, fmaf(-af.y, bv.x, pi[m & 1]));
-            qi[m & 1] = fmaf(af.x, cv.y, fmaf(-af.y, cv.x, qi[m & 1]));
+            pi[m & 3] = fmaf(af.x, bv.y, fmaf(-af.y, bv.x, pi[m & 3]));
+            qi[m & 3] = fmaf(af.x, cv.y, fmaf(-af.y, cv.x, qi[m & 3]));
         }
     }
-    const float r1 = pr[0] + pr[1], r2 = qr[0] + qr[1];
+    const float r1 = (pr[0] + pr[1]) + (pr[2] + pr[3]), r2 = (qr[0] + qr[1]) + (qr[2] + qr[3]);
     acc[0] += r1;
     acc[2] += r2;
     if (IM == 2) {
-        acc[1] += pi[0] + pi[1];
-        acc[3] += qi[0] + qi[1];
+        acc[1] += (pi[0] + pi[1]) + (pi[2] + pi[3]);
+        acc[3] += (qi[0] + qi[1]) + (qi[2] + qi[3]);
     }
     if (ROT) {
         after(a, b, r1, r2);

@@ -38,9 +38,11 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 HBM_PEAK_GBS = 6669.2  # measured copy bandwidth of this GPU pool
 # DRAM bytes (read + write) per launch of the timed kernel, from one ncu capture of this build's
-# kernel on the workload (profiles/rand12_p192_c128_step.md); None where no capture of the current
-# kernel exists. At 12 qubits only the first read of the checkpoints reaches DRAM.
-TRAFFIC = {"rand12_p192_c128": 12894976}
+# kernel on the workload; None where no capture of the current kernel exists. 12 qubits
+# (profiles/rand12_p192_c128_step.md): only the first read of the checkpoints reaches DRAM. 28 qubits
+# (profiles/rand28_p252_c64_step.md): mean over 30 consecutive metric passes, each reading the
+# registers it loads and writing the ones it stores.
+TRAFFIC = {"rand12_p192_c128": 12894976, "rand28_p252_c64": 11972552388}
 
 
 def workloads():
@@ -100,6 +102,31 @@ def column_flops(P: int, n: int) -> float:
     ips = P * (P - 1) / 2 + P + P
     rots = (P - 1) * (P - 2) / 2 + (P - 1)
     return N * 4.0 * (ips + rots)
+
+
+def stream_flops_per_amp(P: int) -> float:
+    """Float64 arithmetic of the streaming metric segment per amplitude, as the schedule runs it.
+
+    Columns l, l + 1 (l odd, l + 1 < P) walk together: column l + 1's first step alone, then one
+    paired step per i < l (two inner products, rotations of a, b and b2); other columns alone.
+    Per amplitude: an inner product's real part = 2 FMA = 4 flop; an adjoint rotation in scaled
+    form = 2 FMA = 4 flop per register; the step i = 0 has no rotation.
+    """
+    def single(i):
+        return 4.0 + (8.0 if i > 0 else 0.0)
+
+    def paired(i):
+        return 8.0 + (12.0 if i > 0 else 0.0)
+
+    total, j = 0.0, 1
+    while j < P:
+        if j % 2 == 1 and j + 1 < P:
+            total += single(j) + sum(paired(i) for i in range(j))
+            j += 2
+        else:
+            total += sum(single(i) for i in range(j))
+            j += 1
+    return total
 
 
 class ClockSampler:
@@ -444,8 +471,7 @@ def roofline(res, steps):
         p = problems[0]
         met_s = col_ms / steps / 1e3
         if prec64:
-            elems = p.P * (p.P - 1) / 2
-            flops = (1 << p.n) * 12.0 * elems  # inner product 2 FMA + two scaled rotations 2 FMA each, per amplitude
+            flops = (1 << p.n) * stream_flops_per_amp(p.P)  # paired columns share the rotation of a
             achieved = flops / met_s / 1e12
             return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
@@ -465,11 +491,19 @@ def roofline(res, steps):
     flops = flops_step / max(launches_per_step, 1)                # per launch, averaged
     peak = FP64_PEAK_TFLOPS if prec64 else FP32_PEAK_TFLOPS
     achieved = flops_step * steps / (col_ms / 1e3) / 1e12 if col_ms > 0 else 0.0
+    # complex128 batches run their launch groups side by side: the column launches overlap, and the
+    # sum of their durations overstates the time; the whole step's time bounds it from above
+    overlap = kind == "batch" and prec64
+    if overlap:
+        achieved = flops_step * steps / (res["ms_total"] / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": TRAFFIC.get(name), "kernel": "k_columns (recurrence + gradient sweep)",
             "peak_source": "derived: float64 2 FMA/clk/SM x 152 SMs x 2.07 GHz" if prec64 else
                            "derived: float32 128 FMA/clk/SM x 152 SMs x 2.07 GHz",
             "kernel_avg_ms": col_avg_s * 1e3, "flops_per_launch": flops, "launches_per_step": launches_per_step}
+    if overlap:
+        roof["note"] = ("launch groups side by side: achieved divides the step's column flops by the whole "
+                        "step's time (sweep and solve included), a lower bound")
     if res["pipeline"]:
         roof["note"] = ("pipelined sweep: the column launches overlap one another and the sweep; achieved divides "
                         "the step's column flops by the sum of their durations, a lower bound")

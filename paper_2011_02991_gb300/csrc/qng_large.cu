@@ -180,6 +180,118 @@ __device__ __forceinline__ Acc2<R> step_dispatch(const TileCtx &tc, typename CX2
     return step_dispatch_cb<R, IM, 0>(tc, A, B, ax, q, rot, c, s, t);
 }
 
+// The step of two columns that share a (kOpStep2): the inner products <A|sigma|B> into ab and
+// <A|sigma|C> into ac, then, when ROT, the adjoint rotation on A, B and C, in one sweep of the tile.
+template <typename R, int AX, int IM, bool ROT, int CB>
+__device__ __forceinline__ void step2_pairs(typename CX2<R>::T *A, typename CX2<R>::T *B, typename CX2<R>::T *C,
+                                           uint32_t T, int lb, R c, R s, R t, Acc2<R> &ab, Acc2<R> &ac) {
+    using cx = typename CX2<R>::T;
+    constexpr bool kScaled = std::is_same<R, double>::value;
+    const uint32_t bit = 1u << lb;
+    auto rot = [&](cx x, cx v) -> cx {
+        cx y;
+        if constexpr (kScaled) {
+            if constexpr (CB) { y.x = fma(t, x.x, v.x); y.y = fma(t, x.y, v.y); }
+            else              { y.x = fma(t, v.x, x.x); y.y = fma(t, v.y, x.y); }
+        } else {
+            y.x = fma(s, v.x, c * x.x); y.y = fma(s, v.y, c * x.y);
+        }
+        return y;
+    };
+    auto ip = [&](Acc2<R> &acc, cx a0, cx a1, cx s0, cx s1) {
+        if constexpr (IM != 0) acc.im = fma(a0.x, s0.y, fma(-a0.y, s0.x, fma(a1.x, s1.y, fma(-a1.y, s1.x, acc.im))));
+        if constexpr (IM != 1) acc.re = fma(a0.x, s0.x, fma(a0.y, s0.y, fma(a1.x, s1.x, fma(a1.y, s1.y, acc.re))));
+    };
+    for (uint32_t p = threadIdx.x; p < (T >> 1); p += blockDim.x) {
+        const uint32_t l0 = lins0(p, lb), l1 = l0 | bit;
+        const cx a0 = A[l0], a1 = A[l1], b0 = B[l0], b1 = B[l1], c0 = C[l0], c1 = C[l1];
+        if constexpr (AX == kAxisX) {
+            ip(ab, a0, a1, b1, b0);
+            ip(ac, a0, a1, c1, c0);
+        } else {
+            ip(ab, a0, a1, cx{b1.y, -b1.x}, cx{-b0.y, b0.x});
+            ip(ac, a0, a1, cx{c1.y, -c1.x}, cx{-c0.y, c0.x});
+        }
+        if constexpr (ROT) {
+            if constexpr (AX == kAxisX) {
+                A[l0] = rot(a0, cx{-a1.y, a1.x}); A[l1] = rot(a1, cx{-a0.y, a0.x});
+                B[l0] = rot(b0, cx{-b1.y, b1.x}); B[l1] = rot(b1, cx{-b0.y, b0.x});
+                C[l0] = rot(c0, cx{-c1.y, c1.x}); C[l1] = rot(c1, cx{-c0.y, c0.x});
+            } else {
+                A[l0] = rot(a0, a1); A[l1] = rot(a1, cx{-a0.x, -a0.y});
+                B[l0] = rot(b0, b1); B[l1] = rot(b1, cx{-b0.x, -b0.y});
+                C[l0] = rot(c0, c1); C[l1] = rot(c1, cx{-c0.x, -c0.y});
+            }
+        }
+    }
+}
+
+template <typename R, int IM, bool ROT, int CB>
+__device__ __forceinline__ void step2_diag(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B,
+                                           typename CX2<R>::T *C, int q, R c, R s, R t, Acc2<R> &ab, Acc2<R> &ac) {
+    using cx = typename CX2<R>::T;
+    constexpr bool kScaled = std::is_same<R, double>::value;
+    const uint32_t T = tc.T;
+    const int lb = tc.lbit[q];
+    const int bfix = lb < 0 ? (int)((tc.base >> q) & 1ull) : 0;
+    auto rotz = [&](cx x, int beta) -> cx {
+        const cx v = {lflip(x.y, beta ^ 1), lflip(x.x, beta)};  // (i Z x)
+        cx y;
+        if constexpr (kScaled) {
+            if constexpr (CB) { y.x = fma(t, x.x, v.x); y.y = fma(t, x.y, v.y); }
+            else              { y.x = fma(t, v.x, x.x); y.y = fma(t, v.y, x.y); }
+        } else {
+            y.x = fma(s, v.x, c * x.x); y.y = fma(s, v.y, c * x.y);
+        }
+        return y;
+    };
+    for (uint32_t l = threadIdx.x; l < T; l += blockDim.x) {
+        const int beta = lb >= 0 ? (int)((l >> lb) & 1u) : bfix;
+        const cx a = A[l], b = B[l], cc = C[l];
+        const cx af = lflip2(a, beta);  // (Z b)_beta = (-1)^beta b, folded into a
+        if constexpr (IM != 0) {
+            ab.im = fma(af.x, b.y, fma(-af.y, b.x, ab.im));
+            ac.im = fma(af.x, cc.y, fma(-af.y, cc.x, ac.im));
+        }
+        if constexpr (IM != 1) {
+            ab.re = fma(af.x, b.x, fma(af.y, b.y, ab.re));
+            ac.re = fma(af.x, cc.x, fma(af.y, cc.y, ac.re));
+        }
+        if constexpr (ROT) {
+            A[l] = rotz(a, beta);
+            B[l] = rotz(b, beta);
+            C[l] = rotz(cc, beta);
+        }
+    }
+}
+
+template <typename R, int IM, int CB>
+__device__ __forceinline__ void step2_dispatch_cb(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B,
+                                                  typename CX2<R>::T *C, int ax, int q, bool rot, R c, R s, R t,
+                                                  Acc2<R> &ab, Acc2<R> &ac) {
+    if (ax == kAxisZ) {
+        if (rot) step2_diag<R, IM, true, CB>(tc, A, B, C, q, c, s, t, ab, ac);
+        else step2_diag<R, IM, false, CB>(tc, A, B, C, q, c, s, t, ab, ac);
+        return;
+    }
+    const int lb = tc.lbit[q];
+    if (ax == kAxisX) {
+        if (rot) step2_pairs<R, kAxisX, IM, true, CB>(A, B, C, tc.T, lb, c, s, t, ab, ac);
+        else step2_pairs<R, kAxisX, IM, false, CB>(A, B, C, tc.T, lb, c, s, t, ab, ac);
+    } else {
+        if (rot) step2_pairs<R, kAxisY, IM, true, CB>(A, B, C, tc.T, lb, c, s, t, ab, ac);
+        else step2_pairs<R, kAxisY, IM, false, CB>(A, B, C, tc.T, lb, c, s, t, ab, ac);
+    }
+}
+
+template <typename R, int IM>
+__device__ __forceinline__ void step2_dispatch(const TileCtx &tc, typename CX2<R>::T *A, typename CX2<R>::T *B,
+                                               typename CX2<R>::T *C, int ax, int q, bool rot, R c, R s, R t, int caseB,
+                                               Acc2<R> &ab, Acc2<R> &ac) {
+    if (std::is_same<R, double>::value && caseB) step2_dispatch_cb<R, IM, 1>(tc, A, B, C, ax, q, rot, c, s, t, ab, ac);
+    else step2_dispatch_cb<R, IM, 0>(tc, A, B, C, ax, q, rot, c, s, t, ab, ac);
+}
+
 // MIM = 1: the pass may hold steps that take both parts of the inner product (adjoint = 2, slots
 // slot and slot + 1); a separate instantiation keeps the registers of the other passes unchanged.
 template <typename R, int MIM>
@@ -435,6 +547,41 @@ __global__ void __launch_bounds__(256) k_pass(PassArgs pa) {
                         pa.slotfac[pd.slot_base + op.slot] = sc[op.r0] * sc[op.r1];
                 }
                 if (kScaled && rot) { sc[op.r0] *= f; sc[op.r1] *= f; }
+                break;
+            }
+            case kOpStep2: {
+                const bool rot = op.param >= 0;
+                R c = 0, sv = 0, tv = 0;
+                int caseB = 0;
+                double f = 1.0;
+                if (rot) {
+                    const DevCoef co = pa.coef[op.param];  // adjoint rotation: s' = +s
+                    c = (R)co.c; sv = (R)co.s; tv = (R)co.t; caseB = co.caseB; f = co.f;
+                }
+                Acc2<R> ab = {0, 0}, ac = {0, 0};
+                const bool both = MIM && op.adjoint == 2;
+                if (both) step2_dispatch<R, 2>(tc, tile[kRegA], tile[kRegB], tile[kRegB2], op.axis, op.q0, rot, c, sv, tv, caseB, ab, ac);
+                else step2_dispatch<R, 0>(tc, tile[kRegA], tile[kRegB], tile[kRegB2], op.axis, op.q0, rot, c, sv, tv, caseB, ab, ac);
+                const double fb = sc[kRegA] * sc[kRegB], fc = sc[kRegA] * sc[kRegB2];
+                const bool rec = blockIdx.x == 0 && threadIdx.x == 0 && tile_id == 0;
+                if (both) {
+                    part[op.slot] += (double)ab.re;
+                    part[op.slot + 1] += (double)ab.im;
+                    part[op.slot + 2] += (double)ac.re;
+                    part[op.slot + 3] += (double)ac.im;
+                    if (rec) {
+                        pa.slotfac[pd.slot_base + op.slot] = pa.slotfac[pd.slot_base + op.slot + 1] = fb;
+                        pa.slotfac[pd.slot_base + op.slot + 2] = pa.slotfac[pd.slot_base + op.slot + 3] = fc;
+                    }
+                } else {
+                    part[op.slot] += (double)ab.re;
+                    part[op.slot + 1] += (double)ac.re;
+                    if (rec) {
+                        pa.slotfac[pd.slot_base + op.slot] = fb;
+                        pa.slotfac[pd.slot_base + op.slot + 1] = fc;
+                    }
+                }
+                if (kScaled && rot) { sc[kRegA] *= f; sc[kRegB] *= f; sc[kRegB2] *= f; }
                 break;
             }
             case kOpRecordFac: {

@@ -29,7 +29,7 @@ enum OpKind : int32_t {
     kOpStep2 = 9,      // the step of two columns that share a (registers a, b and b2): Re <a|sigma|b> into
                        // slot and Re <a|sigma|b2> into slot + 1 (adjoint 0), or Re, Im of the first into
                        // slot, slot + 1 and of the second into slot + 2, slot + 3 (adjoint 2); then the
-                       // adjoint rotation on a, b and b2 (register-phase kernel only)
+                       // adjoint rotation on a, b and b2
 };
 
 struct PassOp {

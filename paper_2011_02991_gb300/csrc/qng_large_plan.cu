@@ -396,8 +396,9 @@ struct Builder {
                 const Item &it = items[i1];
                 const bool new_q = it.need >= 0 && !win_set.count(it.need);
                 if (i1 > i0 && ((new_q && (int)win_set.size() >= win) || ((int)reds.size() + it.nred > kMaxSlots))) break;
-                // the register-phase kernel holds at most three registers in a pass (psi and b2 share a slot)
-                if (i1 > i0 && S.phased && __builtin_popcount(regs_used | it.regs) > 3) break;
+                // at most three registers in a pass: the register-phase kernel holds three slots (psi and b2
+                // share one), and the tile-program kernel keeps two CTAs per SM
+                if (i1 > i0 && (S.phased || S.pairs) && __builtin_popcount(regs_used | it.regs) > 3) break;
                 regs_used |= it.regs;
                 if (i1 > i0 && (i1 - i0 >= limit || (S.phased && i1 - i0 >= (size_t)kMaxPhaseOps))) break;
                 if (new_q) win_set.insert(it.need);
@@ -489,7 +490,7 @@ void build_schedule(const std::vector<qng_gate> &gates, int n, int P, int precis
     S.low = B.low;
     S.t = B.t;
     S.phased = precision == QNG_C64 && B.t == kPhaseTile;
-    S.pairs = S.phased;
+    S.pairs = true;
     const int PSI = 1 << kRegPsi, A = 1 << kRegA, Bm = 1 << kRegB;
 
     // forward: psi <- U_{P-1} ... U_0 |0>

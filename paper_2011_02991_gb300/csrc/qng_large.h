@@ -76,15 +76,18 @@ struct PassPhase {
     int8_t tbit[8];            // local bits of the thread index bits 0..7
     int32_t rmask;             // registers the phase reads or writes (gathered from the tile)
     int32_t wmask;             // registers the phase writes (scattered back)
-    int32_t macro;             // 0, or a straight-line form of the whole phase (kMacro* | axis << 4 | count)
+    int32_t macro;             // 0, or a straight-line form of the phase's last `count` operations
+                               // (kMacro* | axis << 4 | count, kMacroRev for descending targets); the
+                               // operations before them run one by one
 };
 // Straight-line phases: kMacroSteps, m recurrence steps (a, b, Re) on one axis with pair targets
 // at register bits 0..m-1 in order; kMacroCnot, m CNOTs on a and b with targets at register bits
 // 0..m-1 in order, the controls of the first m - 1 at register bits 1..m-1 and the last control a
 // thread-uniform bit.
 constexpr int32_t kMacroSteps = 1 << 8, kMacroCnot = 2 << 8;
-// kMacroSteps2: the same with steps of two columns (kOpStep2, Re).
-constexpr int32_t kMacroSteps2 = 3 << 8;
+// kMacroSteps2: the same with steps of two columns (kOpStep2, Re). kMacroRev (steps only): the
+// targets are register bits m-1, ..., 0 in order instead.
+constexpr int32_t kMacroSteps2 = 3 << 8, kMacroRev = 1 << 7;
 // Runs of diagonal operations (PassOp::zrun): Z-axis recurrence steps and CZ / Z gates, either all on
 // (a, b) or all on (a, b, b2) (kZrunDual), at least two steps, at most kMaxZrun operations, all steps
 // Re (adjoint 0) or all Re and Im (2, kZrunIm).

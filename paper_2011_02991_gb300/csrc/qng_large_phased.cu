@@ -525,24 +525,25 @@ __device__ __forceinline__ int axis_variant(int ax, int kt, int dk) {
 
 // Straight-line phases (PassPhase::macro): the whole phase is one basic block, so the compiler keeps
 // the amplitudes in place from step to step and nothing is decoded per operation.
-template <int AX, int K, int M>
+// Operation K of the run targets register bit K, or M - 1 - K when REV (targets in descending order).
+template <int AX, int K, int M, bool REV>
 __device__ __forceinline__ void steps_run(Regs &X, const OpD *d, float *part, int lane, int tid) {
     if constexpr (K < M) {
         const OpD o = d[K];
         float re = 0.0f, im = 0.0f;
-        step_pairs<1, 2, 0, true, K, AX>(X, o.a, o.b, re, im);
+        step_pairs<1, 2, 0, true, REV ? M - 1 - K : K, AX>(X, o.a, o.b, re, im);
         re += __shfl_xor_sync(0xffffffffu, re, 1);
         if (!(lane & 1)) part[o.slot * (kNT / 2) + (tid >> 1)] = re;
-        steps_run<AX, K + 1, M>(X, d, part, lane, tid);
+        steps_run<AX, K + 1, M, REV>(X, d, part, lane, tid);
     }
 }
-template <int AX>
+template <int AX, bool REV>
 __device__ __forceinline__ void macro_steps(Regs &X, int m, const OpD *d, float *part, int lane, int tid) {
     switch (m) {
-    case 1: steps_run<AX, 0, 1>(X, d, part, lane, tid); break;
-    case 2: steps_run<AX, 0, 2>(X, d, part, lane, tid); break;
-    case 3: steps_run<AX, 0, 3>(X, d, part, lane, tid); break;
-    default: steps_run<AX, 0, 4>(X, d, part, lane, tid); break;
+    case 1: steps_run<AX, 0, 1, REV>(X, d, part, lane, tid); break;
+    case 2: steps_run<AX, 0, 2, REV>(X, d, part, lane, tid); break;
+    case 3: steps_run<AX, 0, 3, REV>(X, d, part, lane, tid); break;
+    default: steps_run<AX, 0, 4, REV>(X, d, part, lane, tid); break;
     }
 }
 template <int K, int M> __device__ __forceinline__ void cnots_run(Regs &X, uint32_t ulast) {
@@ -566,28 +567,28 @@ __device__ __forceinline__ void macro_cnots(Regs &X, int m, uint32_t ulast) {
     }
 }
 // the same two forms for the steps of two columns and for CNOTs on b2 as well (slot 0)
-template <int AX, int K, int M>
+template <int AX, int K, int M, bool REV>
 __device__ __forceinline__ void steps2_run(Regs &X, const OpD *d, float *part, int lane, int tid) {
     if constexpr (K < M) {
         const OpD o = d[K];
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        step2_pairs<0, true, K, AX>(X, o.a, o.b, acc);
+        step2_pairs<0, true, REV ? M - 1 - K : K, AX>(X, o.a, o.b, acc);
         acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
         acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], 1);
         if (!(lane & 1)) {
             part[o.slot * (kNT / 2) + (tid >> 1)] = acc[0];
             part[(o.slot + 1) * (kNT / 2) + (tid >> 1)] = acc[2];
         }
-        steps2_run<AX, K + 1, M>(X, d, part, lane, tid);
+        steps2_run<AX, K + 1, M, REV>(X, d, part, lane, tid);
     }
 }
-template <int AX>
+template <int AX, bool REV>
 __device__ __forceinline__ void macro_steps2(Regs &X, int m, const OpD *d, float *part, int lane, int tid) {
     switch (m) {
-    case 1: steps2_run<AX, 0, 1>(X, d, part, lane, tid); break;
-    case 2: steps2_run<AX, 0, 2>(X, d, part, lane, tid); break;
-    case 3: steps2_run<AX, 0, 3>(X, d, part, lane, tid); break;
-    default: steps2_run<AX, 0, 4>(X, d, part, lane, tid); break;
+    case 1: steps2_run<AX, 0, 1, REV>(X, d, part, lane, tid); break;
+    case 2: steps2_run<AX, 0, 2, REV>(X, d, part, lane, tid); break;
+    case 3: steps2_run<AX, 0, 3, REV>(X, d, part, lane, tid); break;
+    default: steps2_run<AX, 0, 4, REV>(X, d, part, lane, tid); break;
     }
 }
 template <int K, int M> __device__ __forceinline__ void cnots3_run(Regs &X, uint32_t ulast) {
@@ -1017,27 +1018,10 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
             // global index of the thread's amplitude m = 0: the bit of every qubit that is not a
             // register bit is the same for the thread's 16 amplitudes
             const uint64_t gl = base | rowoff[tl >> 5] | (tl & 31u);
-            if (P.macro) {
-                const int m = P.macro & 15;
-                if ((P.macro & ~0xFF) == kMacroSteps) {
-                    if (((P.macro >> 4) & 15) == kAxisX) macro_steps<kAxisX>(X, m, opd + P.op_begin, part, lane, tid);
-                    else macro_steps<kAxisY>(X, m, opd + P.op_begin, part, lane, tid);
-                } else if ((P.macro & ~0xFF) == kMacroSteps2) {
-                    if constexpr (!PSI) {
-                        if (((P.macro >> 4) & 15) == kAxisX) macro_steps2<kAxisX>(X, m, opd + P.op_begin, part, lane, tid);
-                        else macro_steps2<kAxisY>(X, m, opd + P.op_begin, part, lane, tid);
-                    }
-                } else {
-                    const int q = opd[P.op_begin + m - 1].q0u;
-                    const uint32_t ul = q < 0 ? 1u : (uint32_t)(gl >> q) & 1u;
-                    if ((P.macro >> 4) & 1) {
-                        if constexpr (!PSI) macro_cnots3(X, m, ul);
-                    } else {
-                        macro_cnots(X, m, ul);
-                    }
-                }
-            }
-            for (int o = P.macro ? P.op_end : P.op_begin; o < P.op_end; ++o) {
+            // the phase's last m operations may form a straight-line block (PassPhase::macro); the
+            // operations before them run one by one
+            const int mb = P.op_end - (P.macro ? (P.macro & 15) : 0);
+            for (int o = P.op_begin; o < mb; ++o) {
                 const OpD d = opd[o];
                 if (d.pad) {  // a run of diagonal operations, composed
                     const int len = d.pad & kMaxZrun;
@@ -1138,6 +1122,38 @@ __global__ void __launch_bounds__(kNT, 1) k_pass_phased(PassArgs pa) {
                 }
                 default:
                     break;
+                }
+            }
+            if (P.macro) {
+                const int m = P.macro & 15;
+                const bool rev = (P.macro & kMacroRev) != 0;
+                const OpD *dm = opd + mb;
+                if ((P.macro & ~0xFF) == kMacroSteps) {
+                    if (((P.macro >> 4) & 7) == kAxisX) {
+                        if (rev) macro_steps<kAxisX, true>(X, m, dm, part, lane, tid);
+                        else macro_steps<kAxisX, false>(X, m, dm, part, lane, tid);
+                    } else {
+                        if (rev) macro_steps<kAxisY, true>(X, m, dm, part, lane, tid);
+                        else macro_steps<kAxisY, false>(X, m, dm, part, lane, tid);
+                    }
+                } else if ((P.macro & ~0xFF) == kMacroSteps2) {
+                    if constexpr (!PSI) {
+                        if (((P.macro >> 4) & 7) == kAxisX) {
+                            if (rev) macro_steps2<kAxisX, true>(X, m, dm, part, lane, tid);
+                            else macro_steps2<kAxisX, false>(X, m, dm, part, lane, tid);
+                        } else {
+                            if (rev) macro_steps2<kAxisY, true>(X, m, dm, part, lane, tid);
+                            else macro_steps2<kAxisY, false>(X, m, dm, part, lane, tid);
+                        }
+                    }
+                } else {
+                    const int q = dm[m - 1].q0u;
+                    const uint32_t ul = q < 0 ? 1u : (uint32_t)(gl >> q) & 1u;
+                    if ((P.macro >> 4) & 1) {
+                        if constexpr (!PSI) macro_cnots3(X, m, ul);
+                    } else {
+                        macro_cnots(X, m, ul);
+                    }
                 }
             }
             if (PSI && (wm & 1)) scatter<0>(X, reinterpret_cast<float2 *>(stage_reg(stage, 0)), ad, vm);

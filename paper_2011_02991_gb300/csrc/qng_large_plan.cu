@@ -94,19 +94,21 @@ int bank_class(int b) { return b == 0 ? 3 : (b - 1) % 3; }
 int32_t macro_form(const std::vector<PassOp> &ops, size_t i, size_t j) {
     const int m = (int)(j - i);
     if (m < 1 || m > 4) return 0;
-    bool steps = true, steps2 = true, cnots = true;
+    bool steps = true, steps2 = true, fwd = true, rev = true, cnots = true;
     const int ax = ops[i].axis, regs = ops[i].regs;
     const int ab = (1 << kRegA) | (1 << kRegB), abb = ab | (1 << kRegB2);
     for (int k = 0; k < m; ++k) {
         const PassOp &o = ops[i + k];
-        const bool xy_k = o.adjoint == 0 && o.axis == ax && (ax == kAxisX || ax == kAxisY) && o.kt == k;
-        steps = steps && o.kind == kOpStep && o.r0 == kRegA && o.r1 == kRegB && xy_k;
-        steps2 = steps2 && o.kind == kOpStep2 && xy_k;
+        const bool xy = o.adjoint == 0 && o.axis == ax && (ax == kAxisX || ax == kAxisY);
+        steps = steps && o.kind == kOpStep && o.r0 == kRegA && o.r1 == kRegB && xy;
+        steps2 = steps2 && o.kind == kOpStep2 && xy;
+        fwd = fwd && o.kt == k;
+        rev = rev && o.kt == m - 1 - k;
         cnots = cnots && o.kind == kOpFixed && o.fixed_kind == QNG_GATE_CNOT && (regs == ab || regs == abb) &&
                 o.regs == regs && o.kt == k && (k < m - 1 ? o.dk0 == k + 1 : o.dk0 < 0);
     }
-    if (steps) return kMacroSteps | (ax << 4) | m;
-    if (steps2) return kMacroSteps2 | (ax << 4) | m;
+    if ((steps || steps2) && (fwd || rev))
+        return (steps ? kMacroSteps : kMacroSteps2) | (fwd ? 0 : kMacroRev) | (ax << 4) | m;
     if (cnots) return kMacroCnot | (regs == abb ? 1 << 4 : 0) | m;
     return 0;
 }
@@ -225,8 +227,15 @@ bool make_phases(const PassDesc &pd, std::vector<PassOp> &ops, std::vector<PassP
         }
         p.rmask = rm;
         p.wmask = wm;
-        p.macro = macro_form(ops, i, j);
-        if (!p.macro) mark_zruns(ops, i, j);
+        // the longest suffix of the phase's operations with a straight-line form; runs of diagonal
+        // operations among the rest
+        p.macro = 0;
+        size_t mstart = j;
+        for (size_t k = j >= 4 ? std::max(i, j - 4) : i; k < j && !p.macro; ++k) {
+            p.macro = macro_form(ops, k, j);
+            if (p.macro) mstart = k;
+        }
+        mark_zruns(ops, i, mstart);
         ph.push_back(p);
         if ((int)ph.size() > kMaxPhases) {
             *fit_ops = (size_t)ph[kMaxPhases].op_begin;

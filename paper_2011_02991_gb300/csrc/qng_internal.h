@@ -29,7 +29,7 @@ struct DevParam {
     int32_t diag_count; //   of the diag table, plus zmask; diag_count = -1 when F_k is not all diagonal
     uint64_t zmask;     //   single-qubit Z factors of F_k
     int32_t zrun;       // Z rotations with diagonal F from k on (this one included, at most kZRunMax); 0 if k is not one
-    int32_t pad;
+    int32_t zdown;      // Z rotations without fixed gates from k down (this one included); 0 if k is not one
 };
 
 // Generator of a kAxisGen parameter (same index as its DevParam): K = C (x) S with C the projector
@@ -45,11 +45,18 @@ constexpr int kZRunMax = 16;
 constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA (opt-in maximum)
 
 // Fill DevParam::zrun over the parameters [p, p + P) of one instance.
+// zdown: the runs the complex64 column walk of a single instance composes (its own kernel
+// instantiation; batches launch the column kernel without that code).
 inline void set_zruns(DevParam *p, int P) {
     int run = 0;
     for (int k = P - 1; k >= 0; --k) {
         run = (p[k].axis == kAxisZ && p[k].diag_count >= 0) ? run + 1 : 0;
         p[k].zrun = run < kZRunMax ? run : kZRunMax;
+    }
+    int down = 0;
+    for (int k = 0; k < P; ++k) {
+        down = (p[k].axis == kAxisZ && p[k].fix_count == 0) ? down + 1 : 0;
+        p[k].zdown = down;
     }
 }
 

@@ -892,21 +892,125 @@ __global__ void __launch_bounds__(512) k_forward(Work w, int group_first, int cl
 }
 
 // ------------------------------------------------------------------------------------------
+// complex64 column walk through a run of L Z rotations without fixed gates, from parameter i down.
+// Diagonal operators commute: Psi[i'+1] and b at step i' of the run are Psi[i+1] and the run's
+// starting b times the same diagonal unitary D, so <Psi[i'+1]|Z_q|b> = <Psi[i+1]|Z_q|b_start>. Every
+// inner product of the run therefore comes from the one checkpoint Psi[i+1], and the run's adjoint
+// rotations (cos + i sin Z) compose into one factor per amplitude: one checkpoint read and one
+// barrier for the run instead of one per step.
+constexpr int kColRun = 4;  // steps per run at most (a longer run is taken in pieces)
+template <typename R, int AMPS, int MODE>
+__device__ __forceinline__ void col_zrun_t(Eng<R> &e, const typename CX<R>::T *__restrict__ a,
+                                           const DevParam *__restrict__ params, const DevCoef *__restrict__ coefs,
+                                           int i, int L, RI<R> (&parts)[kColRun]) {
+    using cx = typename CX<R>::T;
+    // per amplitude only the products and the composed factor stay in registers; b is read again
+    // from shared memory at the end (the run does not write it before then)
+    cx ph[AMPS];
+    R pr[AMPS], pm[AMPS];
+#pragma unroll
+    for (int u = 0; u < AMPS; ++u) {
+        const uint32_t l = threadIdx.x + u * blockDim.x;
+        const cx xv = e.buf[l];
+        const cx av = a[e.base | l];
+        pr[u] = av.x * xv.x + av.y * xv.y;  // Re conj(a) b
+        pm[u] = av.x * xv.y - av.y * xv.x;  // Im conj(a) b
+        ph[u] = cx{(R)1, (R)0};
+    }
+#pragma unroll
+    for (int r = 0; r < kColRun; ++r) {
+        if (r >= L) break;
+        const int ii = i - r;
+        const DevParam pk = params[ii];
+        RI<R> pt = {0, 0};
+#pragma unroll
+        for (int u = 0; u < AMPS; ++u) {
+            const bool beta = ((e.base | (threadIdx.x + u * blockDim.x)) >> pk.q) & 1;  // (Z b)_beta = (-1)^beta b
+            if (MODE != 1) pt.re += beta ? -pr[u] : pr[u];
+            if (MODE != 0) pt.im += beta ? -pm[u] : pm[u];
+        }
+        parts[r] = pt;
+        if (ii > 0) {  // the last step of a column (i = 0) takes no rotation
+            const DevCoef co = coefs[ii];
+            const R c = co.cf, sn = co.sf;
+#pragma unroll
+            for (int u = 0; u < AMPS; ++u) {
+                const R sv = (((e.base | (threadIdx.x + u * blockDim.x)) >> pk.q) & 1) ? -sn : sn;
+                ph[u] = cx{fma(c, ph[u].x, -sv * ph[u].y), fma(c, ph[u].y, sv * ph[u].x)};
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < AMPS; ++u) {
+        const uint32_t l = threadIdx.x + u * blockDim.x;
+        const cx x = e.buf[l];
+        const cx y = {fma(x.x, ph[u].x, -x.y * ph[u].y), fma(x.x, ph[u].y, x.y * ph[u].x)};
+        e.buf[l] = y;
+    }
+}
+// false (nothing done) when the CTA shape has no compiled amplitude count
+template <typename R, int MODE>
+__device__ __forceinline__ bool col_zrun(Eng<R> &e, const typename CX<R>::T *a, const DevParam *params,
+                                         const DevCoef *coefs, int i, int L, RI<R> (&parts)[kColRun]) {
+    if (e.Nl % blockDim.x) return false;
+    switch (e.Nl / blockDim.x) {
+    case 1: col_zrun_t<R, 1, MODE>(e, a, params, coefs, i, L, parts); return true;
+    case 2: col_zrun_t<R, 2, MODE>(e, a, params, coefs, i, L, parts); return true;
+    case 4: col_zrun_t<R, 4, MODE>(e, a, params, coefs, i, L, parts); return true;
+    default: return false;
+    }
+}
+// The partial sums of step sx into the warp's shift register acc, flushed to red every 8 steps (4
+// with both parts, mode 2) and at the last step.
+template <typename RA, int MIM>
+__device__ __forceinline__ void push_part(RA (&acc)[8], int &cnt, int mode, int sx, int nsteps, RI<RA> part,
+                                          double *red, double *red_im, int lane, int nw, int wid) {
+    if (!MIM || mode != 2) {
+#pragma unroll
+        for (int k = 7; k > 0; --k) acc[k] = acc[k - 1];
+        acc[0] = mode ? part.im : part.re;
+        if (++cnt == 8 || sx == nsteps - 1) {
+            const int idx = (lane >> 2) & 7;
+            const double pw = (double)warp_sum8(acc, lane);
+            if ((lane & 3) == 0 && idx < cnt) red[(size_t)(sx - idx) * nw + wid] = pw;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = 0;
+            cnt = 0;
+        }
+    } else {
+#pragma unroll
+        for (int k = 7; k > 1; --k) acc[k] = acc[k - 2];
+        acc[0] = part.re;
+        acc[1] = part.im;
+        if (++cnt == 4 || sx == nsteps - 1) {
+            const int idx = (lane >> 2) & 7, off = idx >> 1;
+            const double pw = (double)warp_sum8(acc, lane);
+            if ((lane & 3) == 0 && off < cnt) ((idx & 1) ? red_im : red)[(size_t)(sx - off) * nw + wid] = pw;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = 0;
+            cnt = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // k_columns: one cluster per work item (instance, column).
-template <typename R, int MIM, int GEN>
+template <typename R, int MIM, int GEN, int ZR>
 __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int cl, int max_P, unsigned char *smem);
 
 // One cluster per work item, or (queue != nullptr) a persistent grid of clusters that take work
 // items, longest first, from a device counter until all num_work are done. MIM = 1: metric
 // columns take Im L_ij as well (into w.Lim); their partial sums need Group::smem_col_im bytes.
-// GEN = 1: the group has generalised rotations.
-template <typename R, int MIM, int GEN>
+// GEN = 1: the group has generalised rotations. ZR = 1 (complex64, a group of one instance): runs
+// of Z rotations are composed (col_zrun_t); a separate instantiation, so that the batches' column
+// kernel stays as it was (with the run code compiled in, a 256-instance batch measured slower).
+template <typename R, int MIM, int GEN, int ZR = 0>
 __global__ void __launch_bounds__(256, (MIM || GEN) ? 2 : 3) k_columns(Work w, int work_first, int cl, int max_P, int *queue,
                                                                        int num_work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int item_sh;
     if (!queue) {
-        column_item<R, MIM, GEN>(w, w.work[work_first + (blockIdx.x >> cl)], cl, max_P, smem);
+        column_item<R, MIM, GEN, ZR>(w, w.work[work_first + (blockIdx.x >> cl)], cl, max_P, smem);
         return;
     }
     for (;;) {
@@ -916,18 +1020,18 @@ __global__ void __launch_bounds__(256, (MIM || GEN) ? 2 : 3) k_columns(Work w, i
             const int item = *cg::this_cluster().map_shared_rank(&item_sh, 0);
             cg::this_cluster().sync();  // rank 0 keeps item_sh until every CTA has read it
             if (item >= num_work) return;
-            column_item<R, MIM, GEN>(w, w.work[work_first + item], cl, max_P, smem);
+            column_item<R, MIM, GEN, ZR>(w, w.work[work_first + item], cl, max_P, smem);
         } else {
             __syncthreads();
             const int item = item_sh;
             __syncthreads();
             if (item >= num_work) return;
-            column_item<R, MIM, GEN>(w, w.work[work_first + item], cl, max_P, smem);
+            column_item<R, MIM, GEN, ZR>(w, w.work[work_first + item], cl, max_P, smem);
         }
     }
 }
 
-template <typename R, int MIM, int GEN>
+template <typename R, int MIM, int GEN, int ZR>
 __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int cl, int max_P, unsigned char *smem) {
     using cx = typename CX<R>::T;
     using RA = R;  // per-thread partial sums; float64 from the warp level on
@@ -1040,6 +1144,35 @@ __device__ __forceinline__ void column_item(const Work &w, const DevWork wk, int
         const DevParam pi = w.param[in.param_tab + i];
         const double sci = scales[i + 1];
         const cx *a = ckpt + (uint64_t)(i + 1) * N;
+        if constexpr (!kScaled && !GEN && ZR) {
+            // complex64: a run of Z rotations without fixed gates in one pass (col_zrun_t)
+            const int L = min(min(pi.zdown, nsteps - s), kColRun);
+            if (L >= 2) {
+                RI<RA> zp[kColRun];
+                const DevParam *pt = w.param + in.param_tab;
+                const DevCoef *ct = w.coef + in.param_off;
+                bool done = false;
+                if (mode == 0) done = col_zrun<R, 0>(e, a, pt, ct, i, L, zp);
+                else if (mode == 1) done = col_zrun<R, 1>(e, a, pt, ct, i, L, zp);
+                else if constexpr (MIM) done = col_zrun<R, 2>(e, a, pt, ct, i, L, zp);
+                if (done) {
+                    if (s + L < nsteps) {  // the step after the run reads checkpoint i - L + 1
+                        const char *nxt = reinterpret_cast<const char *>(ckpt + (uint64_t)(i - L + 1) * N + e.base);
+                        for (uint32_t off = threadIdx.x * 128u; off < slice_bytes; off += blockDim.x * 128u)
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + off));
+                    }
+                    if (threadIdx.x == 0)  // every inner product of the run is taken on checkpoint i + 1
+                        for (int r = 0; r < L; ++r) fac[s + r] = sci * scale_b;
+#pragma unroll
+                    for (int r = 0; r < kColRun; ++r)
+                        if (r < L) push_part<RA, MIM>(acc, cnt, mode, s + r, nsteps, zp[r], red, red_im, lane, nw, wid);
+                    __syncthreads();
+                    s += L - 1;
+                    continue;
+                }
+            }
+        }
+
         // the next step reads this CTA's slice of checkpoint i: start it towards L1 now, so the
         // step after this one does not wait on L2
         if (s + 1 < nsteps) {
@@ -1527,6 +1660,8 @@ cudaError_t prepare_kernels(int precision, size_t smem_fwd, size_t smem_col, siz
     if ((e = set_attrs(k_forward<float, 0>, smem_fwd)) != cudaSuccess) return e;
     if ((e = set_attrs(k_forward<float, 1>, smem_fwd)) != cudaSuccess) return e;
     if ((e = set_attrs(k_columns<float, 0, 0>, smem_col)) != cudaSuccess) return e;
+    if ((e = set_attrs(k_columns<float, 0, 0, 1>, smem_col)) != cudaSuccess) return e;
+    if ((e = set_attrs(k_columns<float, 1, 0, 1>, smem_col_im)) != cudaSuccess) return e;
     if ((e = set_attrs(k_columns<float, 0, 1>, smem_col)) != cudaSuccess) return e;
     if ((e = set_attrs(k_columns<float, 1, 0>, smem_col_im)) != cudaSuccess) return e;
     return set_attrs(k_columns<float, 1, 1>, smem_col_im);
@@ -1591,6 +1726,10 @@ cudaError_t launch_columns_range(const Work &w, const Group &g, int precision, i
     if (precision == QNG_C128) {
         if (metric_im) return g.general ? QNG_COLS(double, 1, 1) : QNG_COLS(double, 1, 0);
         return g.general ? QNG_COLS(double, 0, 1) : QNG_COLS(double, 0, 0);
+    }
+    if (g.num_inst == 1 && !g.general) {  // a single instance: the instantiation with composed Z runs
+        if (metric_im) return launch_cluster(k_columns<float, 1, 0, 1>, grid, g.threads, smem, g.cl, st, w, first, g.cl, g.max_P, queue, num);
+        return launch_cluster(k_columns<float, 0, 0, 1>, grid, g.threads, smem, g.cl, st, w, first, g.cl, g.max_P, queue, num);
     }
     if (metric_im) return g.general ? QNG_COLS(float, 1, 1) : QNG_COLS(float, 1, 0);
     return g.general ? QNG_COLS(float, 0, 1) : QNG_COLS(float, 0, 0);

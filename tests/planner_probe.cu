@@ -3,6 +3,8 @@
 // passes) or complex128 (tile-program passes), optionally for a column subset, checks the
 // schedule's structural invariants and prints what the test compares:
 //   red <segment> <region> <index>   one line per inner-product destination
+//   step <segment> <kind> <rot>       one line per recurrence step (kOpStep 8 / kOpStep2 9; rot 1 if it
+//                                     rotates its registers)
 //   ok                                every invariant held (else a line "bad <what>" and exit 1)
 // Input (stdin): n P G precision nwant, then G lines "kind q0 q1 param", then nwant column indices.
 #include <cstdio>
@@ -64,6 +66,8 @@ int main() {
         if (pd.nslots > kMaxSlots) return bad("slots", L.pass, pd.nslots);
         for (int o = 0; o < pd.nops; ++o) {
             const PassOp &op = S.ops[pd.op_begin + o];
+            if (op.kind == kOpStep || op.kind == kOpStep2)
+                std::printf("step %d %d %d\n", L.segment, op.kind, op.param >= 0 ? 1 : 0);
             if (op.kind == kOpStep2) {
                 // a paired step serves columns u = l + 1 and l, l odd: its two L destinations
                 const int nv = op.adjoint == 2 ? 2 : 1;

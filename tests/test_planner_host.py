@@ -8,6 +8,7 @@ passes):
   <sigma_j> for every computed column j, Im L_ij as well in the complex-metric segment, every
   gradient entry (Eq. 2) and the energy;
 - a column subset computes exactly its own columns;
+- the bench's float64 flop count of the streaming metric segment equals the schedule's steps;
 - the probe's structural invariants: two columns walk together only as (l, l + 1) with l odd, a pass
   holds at most three registers and never psi with b2, every non-diagonal target of a register
   phase is a register bit, a composed run holds only diagonal operations, and a straight-line block
@@ -40,7 +41,9 @@ def probe(tmp_path_factory):
     return exe
 
 
-def run_probe(exe, circuit, precision, want=None):
+def run_probe(exe, circuit, precision, want=None, with_steps=False):
+    """The schedule's reduction destinations {(segment, region): [index]}, and with with_steps its
+    recurrence steps [(segment, kind, rotates)] as well."""
     g = np.asarray(circuit.gates, dtype=np.int64)
     lines = [f"{circuit.n} {circuit.num_params} {len(g)} {precision} {-1 if want is None else len(want)}"]
     lines += [" ".join(str(int(v)) for v in row) for row in g]
@@ -50,11 +53,14 @@ def run_probe(exe, circuit, precision, want=None):
     out = r.stdout.split("\n")
     assert r.returncode == 0 and "ok" in out, f"probe: {[x for x in out if x.startswith('bad')]} {r.stderr}"
     reds = {}
+    steps = []
     for x in out:
         if x.startswith("red "):
             _, seg, region, idx = x.split()
             reds.setdefault((int(seg), int(region)), []).append(int(idx))
-    return reds
+        elif x.startswith("step "):
+            steps.append(tuple(int(v) for v in x.split()[1:]))
+    return (reds, steps) if with_steps else reds
 
 
 def check_coverage(reds, P, cols):
@@ -110,3 +116,20 @@ def test_subset_breaking_pairs(probe):
     cols = [0, 1, 4, 7, 8, P - 2]
     for precision in (W.C64, W.C128):
         check_coverage(run_probe(probe, c, precision, cols), P, cols)
+
+
+@pytest.mark.parametrize("P_layers", [1, 2, 3])
+def test_bench_flop_count_matches_schedule(probe, P_layers):
+    """The roofline's float64 work of the streaming metric segment (bench.stream_flops_per_amp) is
+    what the paired schedule runs: per amplitude, 4 flop per inner product and 4 per register
+    rotated (scaled form), a single step rotating a and b, a paired one a, b and b2."""
+    import bench
+    c = W.layered_ansatz(12, P_layers, rotation_kinds=(W.RY, W.RX, W.RZ), entangler=W.CNOT)
+    _, steps = run_probe(probe, c, W.C128, with_steps=True)
+    flops = 0.0
+    for seg, kind, rot in steps:
+        if seg != SEG_METRIC:
+            continue
+        ips, regs = (1, 2) if kind == 8 else (2, 3)
+        flops += 4.0 * ips + (4.0 * regs if rot else 0.0)
+    assert flops == bench.stream_flops_per_amp(c.num_params)
